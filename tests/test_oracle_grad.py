@@ -1,0 +1,138 @@
+"""Pin the oracle's hand-derived backward with FP64 central finite differences.
+
+Loss = sum(dimg * image) for a fixed seeded dimg, so d(loss)/d(theta) is the
+oracle's analytic gradient. Central differences with h = 1e-6 max(1, |theta|)
+in FP64 are independent of that derivation. A sample whose +-h evaluation
+changes a discrete decision (which Gaussians contribute at a pixel, or which
+contributions are clamped at alpha_max) straddles a jump and is skipped; the
+test requires that most samples are usable.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenegen as sg
+
+
+def _tiny(seed, N=24, kind="basic", widths=(16, 16), log_s_mean=-1.8, res=32, metal_zero=False):
+    sc = sg.shell_scene(seed, N)
+    rng = np.random.default_rng(seed + 100)
+    sc.log_s = sg.f32(rng.normal(log_s_mean, 0.25, (N, 3)))
+    sc.normal = sg.f32(sc.normal + rng.normal(0, 0.3, (N, 3)))
+    if not metal_zero:
+        sc.metal = sg.f32(rng.uniform(0, 1, N))
+    sc.vis = sg.f32(rng.uniform(0, 1, N))
+    cam = 3.0 * np.array([1.0, 0.2, 1.0]) / np.linalg.norm([1.0, 0.2, 1.0])
+    pair = sg._make_pair(cam, [1.5, -2.0, 3.0], res, res)
+    spec = sg.mlp_spec(seed + 7, kind, list(widths))
+    return sc, pair, spec
+
+
+def _loss(sc, pair, spec, dimg):
+    r = O.render_pair(sc, pair, spec)
+    return float((r["img"] * dimg).sum()), r["ncontrib"].copy(), r["margin"][:, 2].copy()
+
+
+def _fd_check(sc, pair, spec, picks, dimg, rtol=2e-5):
+    r = O.render_pair(sc, pair, spec, dimg=dimg)
+    _, nc0, cl0 = _loss(sc, pair, spec, dimg)
+    used, bad = 0, []
+    for name, idx in picks:
+        if name[0] in "Wb" and name[1:].isdigit():
+            l = int(name[1:])
+            arr = (spec.weights if name[0] == "W" else spec.biases)[l]
+            ana = (r["dW"] if name[0] == "W" else r["db"])[l][idx]
+        else:
+            arr = getattr(sc, name)
+            ana = r["grads"][name][idx]
+        x0 = float(arr[idx])
+        h = 1e-6 * max(1.0, abs(x0))
+        arr[idx] = x0 + h
+        lp, ncp, clp = _loss(sc, pair, spec, dimg)
+        arr[idx] = x0 - h
+        lm, ncm, clm = _loss(sc, pair, spec, dimg)
+        arr[idx] = x0
+        if not (np.array_equal(ncp, nc0) and np.array_equal(ncm, nc0)
+                and np.array_equal(clp, cl0) and np.array_equal(clm, cl0)):
+            continue
+        fd = (lp - lm) / (2 * h)
+        used += 1
+        scale = max(abs(fd), abs(ana), 1e-3)
+        if abs(fd - ana) > rtol * scale:
+            bad.append((name, idx, fd, ana))
+    return used, bad
+
+
+PARAMS = ["mu", "log_s", "quat", "logit_o", "normal", "base", "rough", "metal", "sss", "vis"]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fd_scene_parameters_basic_mlp(seed):
+    sc, pair, spec = _tiny(seed)
+    dimg = sg.random_dimg(seed + 50, pair.W * pair.H)
+    r = O.render_pair(sc, pair, spec)
+    live = np.flatnonzero(r["rect"][:, 0] <= r["rect"][:, 1])
+    rng = np.random.default_rng(seed)
+    picks = []
+    for name in PARAMS:
+        arr = getattr(sc, name)
+        for _ in range(6):
+            g = int(rng.choice(live))
+            idx = (g,) if arr.ndim == 1 else (g, int(rng.integers(arr.shape[1])))
+            picks.append((name, idx))
+    used, bad = _fd_check(sc, pair, spec, picks, dimg)
+    assert used >= 0.8 * len(picks), used
+    assert not bad, bad[:5]
+
+
+def test_fd_mlp_weights_basic():
+    sc, pair, spec = _tiny(3)
+    dimg = sg.random_dimg(53, pair.W * pair.H)
+    rng = np.random.default_rng(3)
+    picks = []
+    for l, W in enumerate(spec.weights):
+        for _ in range(5):
+            picks.append((f"W{l}", (int(rng.integers(W.shape[0])), int(rng.integers(W.shape[1])))))
+        picks.append((f"b{l}", (int(rng.integers(W.shape[0])),)))
+    used, bad = _fd_check(sc, pair, spec, picks, dimg)
+    assert used >= 0.8 * len(picks)
+    assert not bad, bad[:5]
+
+
+def test_fd_pe6_mlp_inputs_and_weights():
+    """The Fourier-encoded network of the 300K configuration (FP64 mode)."""
+    sc, pair, _ = _tiny(4)
+    spec = sg.mlp_spec(9, "pe6", [32, 32])
+    dimg = sg.random_dimg(54, pair.W * pair.H)
+    r = O.render_pair(sc, pair, spec)
+    live = np.flatnonzero(r["rect"][:, 0] <= r["rect"][:, 1])
+    rng = np.random.default_rng(4)
+    picks = [("mu", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(10)]
+    picks += [("normal", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(5)]
+    picks += [("vis", (int(rng.choice(live)),)) for _ in range(5)]
+    picks += [("W0", (int(rng.integers(32)), int(rng.integers(50)))) for _ in range(5)]
+    picks += [("W2", (int(rng.integers(4)), int(rng.integers(32)))) for _ in range(4)]
+    used, bad = _fd_check(sc, pair, spec, picks, dimg)
+    assert used >= 0.8 * len(picks)
+    assert not bad, bad[:5]
+
+
+def test_fd_with_clamped_alpha_and_stop():
+    """Dense, opaque Gaussians: alpha clamps at 0.99 and T-stops are common."""
+    sc, pair, spec = _tiny(5, N=40, log_s_mean=-1.6)
+    sc.logit_o = sg.f32(np.random.default_rng(8).normal(3.0, 2.0, sc.N))
+    dimg = sg.random_dimg(55, pair.W * pair.H)
+    r = O.render_pair(sc, pair, spec)
+    assert r["margin"][:, 2].sum() > 0          # some clamped contributions exist
+    live = np.flatnonzero(r["rect"][:, 0] <= r["rect"][:, 1])
+    rng = np.random.default_rng(5)
+    picks = []
+    for name in ["mu", "log_s", "quat", "logit_o", "base", "rough"]:
+        arr = getattr(sc, name)
+        for _ in range(6):
+            g = int(rng.choice(live))
+            idx = (g,) if arr.ndim == 1 else (g, int(rng.integers(arr.shape[1])))
+            picks.append((name, idx))
+    used, bad = _fd_check(sc, pair, spec, picks, dimg)
+    assert used >= 0.7 * len(picks)
+    assert not bad, bad[:5]
