@@ -1,0 +1,456 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable OLAT render (forward + backward).
+
+Default workload: the 300K-Gaussian blob scene with 64 view/light pairs at
+800x800 (cameras on a radius-3 hemisphere, lights on a radius-4 sphere, both
+Fibonacci lattices), 16x16 tiles, PE6 network with four 128-wide layers. One
+step = network forward, projection, bin + sort, fused composite + shade, L1
+loss gradient against a target image, fused shade + composite backward,
+network backward and projection backward, for all 64 pairs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank renders its own
+64-pair batch (weak scaling) and the parameter gradients are summed with one
+NCCL all-reduce per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd view-light renders/sec and % HBM roofline vs plain FP32 path at ≤1e-4 err"
+UNIT = "renders/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.lines = []
+        self.proc = None
+        self.uuid = uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle sample
+
+_CPU_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, ROOT)
+import numpy as np
+import scenegen as sg, oracle as O
+wl = sg.make_workload(WORKLOAD)
+pair = wl.pairs[0]
+sc = wl.scenes[pair.scene]
+stride = STRIDE
+pix = O.all_pixels(pair.W, pair.H)
+sel = pix[(pix[:, 1] % stride == 0)]
+dimg = sg.random_dimg(7, sel.shape[0])
+O.lib()
+t0 = time.perf_counter()
+X = O.mlp_inputs(wl.mlp.kind, sc.mu, sc.normal, sc.vis, pair.center, pair.light)
+acts, y, Ls, Lin = O.mlp_forward(wl.mlp, X)
+dW = O.mlp_backward(wl.mlp, acts, y, Ls, np.ones_like(Ls), np.ones_like(Lin))
+t_mlp = time.perf_counter() - t0
+t0 = time.perf_counter()
+r = O.render_pair(sc, pair, wl.mlp, pixels=sel.astype(np.int32), dimg=dimg)
+t_all = time.perf_counter() - t0
+t_raster = max(t_all - t_mlp, 1e-9)
+full = t_mlp + t_raster * stride
+print(json.dumps({"t_mlp": t_mlp, "t_sample": t_all, "t_full_est": full, "pixels": int(sel.shape[0])}))
+"""
+
+
+def cpu_oracle_sample(workload: str, stride: int, threads: int):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = _CPU_SAMPLE.replace("ROOT", repr(ROOT)).replace("WORKLOAD", repr(workload)).replace("STRIDE", str(stride))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    stride = 16
+    times = []
+    for i in range(args.warmup + args.steps):
+        d = cpu_oracle_sample(args.workload, stride, threads)
+        if i >= args.warmup:
+            times.append(d["t_full_est"])
+    t = sum(times) / len(times)
+    value = 1.0 / t
+    sample = (f"one view/light pair of workload {args.workload}: full network fwd+bwd over all Gaussians, "
+              f"raster fwd+bwd on every {stride}th pixel row, raster time scaled by {stride}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(args):
+    desc = {
+        "c4": "300K Gaussians on a seeded SH blob, 64 view/light pairs at 800x800 (Fibonacci cameras r=3 "
+              "hemisphere, lights r=4 sphere), PE6 MLP 64-128x4-4",
+        "c3": "300K Gaussians on a seeded SH blob, 1 view/light pair at 800x800, PE6 MLP 64-128x4-4",
+        "c2": "100K Gaussians on a seeded SH blob, 1 pair at 512x512, MLP 9-64x3-4",
+        "c1": "1,024 Gaussians in a shell, 1 pair at 128x128, MLP 9-32x2-4",
+    }
+    return {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
+            "loss": "L1 vs target rendered from perturbed parameters",
+            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
+
+
+# ---------------------------------------------------------------------------- our arm
+
+STAGES = ("mlp_fwd", "project_fwd", "bin_sort", "render_fwd", "render_bwd", "mlp_bwd", "project_bwd")
+
+
+def algorithmic_bytes(stage, n_items, n_pixels, n_inst, n_gauss, n_pairs):
+    """Compulsory (algorithmic) bytes per launch of each stage."""
+    if stage == "render_fwd":          # gbuf 64 + last 4 + img 12 per pixel; id 4 per instance; record 96 per item
+        return 80 * n_pixels + 4 * n_inst + 96 * n_items
+    if stage == "render_bwd":          # gbuf 64 + last 4 + img 12 + target 12 per pixel; id 4; record 96 + grad 84
+        return 92 * n_pixels + 4 * n_inst + 180 * n_items
+    if stage == "project_fwd":         # params 84 + net out 16 -> record 96 + rect 16
+        return 212 * n_items
+    if stage == "project_bwd":         # grad record 96 + net-input grad 28 per item; params 84 + grads 84 rw
+        return 124 * n_items + 252 * n_gauss
+    if stage == "bin_sort":            # key+id write 12, one read+write pass 24, per instance; depth keys per item
+        return 36 * n_inst + 32 * n_items
+    if stage == "mlp_fwd":
+        return 44 * n_items
+    if stage == "mlp_bwd":
+        return 72 * n_items
+    return 0
+
+
+def mlp_flops(widths, rows):
+    f = 0
+    for a, b in zip(widths[:-1], widths[1:]):
+        f += 2 * a * b
+    return f * rows
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import scenegen as sg
+    from paper_2408_12282_gb300 import binding as B
+    from paper_2408_12282_gb300 import pipeline as PL
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    B.load_library()
+    hbm, bf16_burst, bf16_sus, peak_src = _peaks()
+
+    wl = sg.make_workload(args.workload, seed_offset=rank)
+    precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
+    try:
+        r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
+        r.forward_front()
+    except B.SSSGSError:
+        precision = B.FP32
+        r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
+    n_inst = r.fit_capacity()
+    table = r.table
+    n_pairs = table.n
+    # target images from the perturbed scene (untimed set-up)
+    tgt_scene = wl.target_scene or sg.perturbed(wl.scenes[0], 4242 + rank)
+    wl_t = sg.Workload(wl.name, [tgt_scene], wl.pairs, wl.mlp, wl.tile)
+    rt = PL.renderer_for_workload(wl_t, precision=precision, tile=args.tile)
+    rt.fit_capacity()
+    rt.forward()
+    target = rt.img.clone()
+    del rt
+    torch.cuda.empty_cache()
+    l1_scale = 1.0 / (3.0 * table.n_pixels)
+    grads_flat = [g for g in r.grads.values()] + r.dW + r.db
+
+    def step():
+        r.forward()
+        r.backward(target=target, l1_scale=l1_scale)
+        if world > 1:
+            for g in grads_flat:
+                dist.all_reduce(g)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    r.check_status()
+
+    # ---------------- timed region (device events on the launching stream)
+    st = torch.cuda.current_stream()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    l0 = B.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    launches = (B.launch_count() - l0) // args.steps
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * n_pairs * 1000.0 / ms_max
+
+    # ---------------- per-stage timing (separate pass, events between calls)
+    stage_ms = {s: 0.0 for s in STAGES}
+    reps = max(2, min(args.steps, 5))
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+        ev[0].record(st)
+        B.mlp_fwd(r._mlp_s, table.h, table.d, r._scene_s, r.mlp_out)
+        ev[1].record(st)
+        B.project_fwd(r.cfg, table.h, table.d, r._scene_s, r.mlp_out, r.rec, r.rect)
+        ev[2].record(st)
+        B.bin_sort(r.cfg, table.h, table.d, r.rec, r.rect, r.capacity, r.vals, r.ranges, r.count, r.status, r.ws_bin)
+        ev[3].record(st)
+        B.render_fwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img)
+        ev[4].record(st)
+        r.zero_grads()
+        e_z = torch.cuda.Event(enable_timing=True)
+        e_z.record(st)
+        B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, None, target, None,
+                     l1_scale, r.drec)
+        ev[5].record(st)
+        B.mlp_bwd(r._mlp_s, table.h, table.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp)
+        ev[6].record(st)
+        B.project_bwd(r.cfg, table.h, table.d, r._scene_s, r.drec, r.dx_items, r._grad_s)
+        ev[7].record(st)
+        torch.cuda.synchronize()
+        for i, s in enumerate(STAGES):
+            a = e_z if s == "render_bwd" else ev[i]
+            stage_ms[s] += a.elapsed_time(ev[i + 1]) / reps
+    n_items, n_pixels = table.n_items, table.n_pixels
+    n_gauss = wl.scenes[0].N
+    dom = max(STAGES, key=lambda s: stage_ms[s])
+    widths = [int(r._mlp_s.width[i]) for i in range(r._mlp_s.n_layers + 1)]
+    if dom in ("mlp_fwd", "mlp_bwd") and precision == B.BF16:
+        fl = mlp_flops(widths, n_items) * (1 if dom == "mlp_fwd" else 2)
+        ach = fl / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
+                "frac": ach / bf16_sus, "traffic": None, "peak_source": peak_src + " (bf16 sustained)"}
+    else:
+        by = algorithmic_bytes(dom, n_items, n_pixels, n_inst, n_gauss, n_pairs)
+        ach = by / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": peak_src + " (hbm copy)"}
+    total_bytes = sum(algorithmic_bytes(s, n_items, n_pixels, n_inst, n_gauss, n_pairs) for s in STAGES)
+    step_hbm_frac = total_bytes / (ms_max * 1e-3) / 1e9 / hbm
+
+    # ---------------- plain unbatched FP32 path (per-pair launches, unfused, CUDA-core network)
+    plain = None
+    if not args.skip_plain:
+        k = min(args.plain_pairs, n_pairs)
+        rp = PL.renderer_for_workload(wl, precision=B.FP32, fused=False, tile=args.tile, pair_slice=slice(0, 1))
+        rp.fit_capacity()
+        rp.set_capacity(int(1.5 * n_inst / n_pairs) + 4096)
+        tables = [PL.PairTable([wl.pairs[i]], rp.cfg, [0], [n_gauss]) for i in range(k)]
+        dimg_p = torch.full((rp.table.n_pixels, 3), l1_scale, device="cuda")
+
+        def plain_step():
+            for tb in tables:
+                rp.table = tb
+                rp.forward()
+                rp.backward(dimg=dimg_p)
+        plain_step()
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(st)
+        plain_step()
+        p1.record(st)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        plain = {"renders_per_s": k * 1000.0 / pms, "pairs_timed": k,
+                 "what": "per-pair launches, unfused composite and shade, FP32 CUDA-core network",
+                 "speedup_of_batched": value / world / (k * 1000.0 / pms)}
+        del rp
+        torch.cuda.empty_cache()
+
+    # ---------------- end to end through the public API with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        host_in = {k: v.detach().cpu().pin_memory() for k, v in r.scene.items()}
+        host_tgt = target.cpu().pin_memory()
+        host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in r.grads.items()}
+        h2d = sum(v.numel() * 4 for v in host_in.values()) + host_tgt.numel() * 4
+        d2h = sum(v.numel() * 4 for v in host_out.values())
+
+        def e2e_step():
+            for k2, v in host_in.items():
+                r.scene[k2].copy_(v, non_blocking=True)
+            target.copy_(host_tgt, non_blocking=True)
+            r.forward()
+            r.backward(target=target, l1_scale=l1_scale)
+            if world > 1:
+                for g in grads_flat:
+                    dist.all_reduce(g)
+            for k2, v in host_out.items():
+                v.copy_(r.grads[k2], non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(st)
+        for _ in range(args.steps):
+            e2e_step()
+        q1.record(st)
+        torch.cuda.synchronize()
+        ems = q0.elapsed_time(q1) / args.steps
+        e2e = {"value": world * n_pairs * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # ---------------- CPU oracle baseline (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        try:
+            d = cpu_oracle_sample(args.workload, 16, 1)
+            cpu = {"value": 1.0 / d["t_full_est"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": (f"one pair of {args.workload}: network fwd+bwd over all {n_gauss} Gaussians "
+                              f"({d['t_mlp']:.1f} s) + raster fwd+bwd on every 16th pixel row "
+                              f"({d['t_sample'] - d['t_mlp']:.1f} s) scaled by 16; single thread")}
+        except Exception as ex:  # report, do not hide
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16+f32" if precision == B.BF16 else "f32",
+                "data": "synthetic", "config": _config(args),
+                "roofline": roof, "step_hbm_frac_of_algorithmic": step_hbm_frac,
+                "stage_ms": stage_ms, "instances": n_inst, "items": n_items, "pixels": n_pixels,
+                "plain_fp32": plain, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--fp32-mlp", action="store_true")
+    ap.add_argument("--plain-pairs", type=int, default=4)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

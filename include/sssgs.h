@@ -1,0 +1,252 @@
+/*
+ * libsssgs -- differentiable OLAT render of relightable 3D Gaussians with a
+ * learned subsurface-scattering residual, for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: "Subsurface Scattering for 3D Gaussian Splatting" (arXiv 2408.12282).
+ * One view/light pair ("pair") is rendered per camera + OLAT point light
+ * (Section 3.2, "Incident Light"). The stages of the forward pass are
+ *
+ *   mlp      (L_SSS, L_in) = f_Theta(mu, Sigma, n, w_in, w_out, v)        Eq. 6
+ *   project  EWA splat: Sigma' = J W Sigma W^T J^T, conic, mean, depth    Eq. 1, Eq. 2
+ *   bin_sort tile binning + stable radix sort by (tile, depth)            Eq. 3 ordering
+ *   composite front-to-back alpha compositing of 15 features             Eq. 3, Fig. 2
+ *   shade    per-pixel Cook-Torrance/Lambert BRDF + SSS blend             Eq. 4, Eq. 7
+ *
+ * and the backward of each (gradients accumulate, "+=", into caller-zeroed
+ * buffers).
+ *
+ * Conventions (the paper is silent on each; both this library and its test
+ * oracle use them):
+ *   camera  OpenCV pinhole, x_cam = R x_world + t, +z forward, pixel (i, j)
+ *           sampled at (i + 0.5, j + 0.5);
+ *   alpha   = min(alpha_max, o exp(-p)), p = 0.5 (ca dx^2 + cc dy^2) + cb dx dy,
+ *           skipped if p < 0 or alpha < alpha_min; compositing stops before the
+ *           Gaussian that would take T below T_min;
+ *   order   float32 view depth z = fmaf(R20, mx, fmaf(R21, my, fmaf(R22, mz, t2))),
+ *           ties by item index;
+ *   BRDF    GGX D, Schlick F (F0 = 0.04 (1 - m) + b m), separable Smith-GGX as
+ *           V = G / (4 n.wo n.wi), alpha_r = roughness^2; Lambert (1 - m) b / pi;
+ *   output  image = A * L_out(G / A), A = 1 - T (black background).
+ *
+ * Ownership: the caller allocates every buffer (device memory unless stated)
+ * and the workspace; the library never allocates or frees. All calls enqueue
+ * asynchronous work on `stream` and return immediately.
+ *
+ * Errors: each entry point returns SSSGS_OK (0) or a negative code detected on
+ * the host before any launch (bad argument, launch failure). Conditions found
+ * on the device (instance capacity overflow) are written to the caller's
+ * device status word and never trap; read it after the stream synchronises.
+ */
+#ifndef SSSGS_H
+#define SSSGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sssgs_stream;   /* == cudaStream_t; NULL = legacy default stream */
+
+enum {
+    SSSGS_OK = 0,
+    SSSGS_ERR_INVALID_ARG = -1,   /* host-side argument check failed; nothing launched */
+    SSSGS_ERR_CUDA = -2,          /* a CUDA launch or API call failed */
+    SSSGS_ERR_UNSUPPORTED = -3,   /* configuration not compiled in (tile size, MLP shape) */
+    SSSGS_ERR_WORKSPACE = -4      /* workspace smaller than sssgs_*_workspace_bytes */
+};
+
+/* Device status bits (written with atomicOr into the caller's int32 word). */
+enum {
+    SSSGS_STATUS_CAPACITY = 1     /* more tile instances than `capacity`; lists truncated */
+};
+
+#define SSSGS_NF 15          /* composited features: depth, n3, base3, rough, metal, sss, Lsss3, Lin, vis */
+#define SSSGS_REC 24         /* floats per packed (pair, Gaussian) record (96 B, 16-B aligned) */
+#define SSSGS_GBUF 16        /* floats per G-buffer pixel: 15 features + final transmittance T */
+#define SSSGS_MAX_LAYERS 8
+
+/* Record layout (floats): 0 mx, 1 my, 2 ca, 3 cb, 4 cc, 5 opacity,
+ * 6..20 features (6 depth, 7-9 n, 10-12 base, 13 rough, 14 metal, 15 sss,
+ * 16-18 L_SSS, 19 L_in, 20 vis), 21..23 zero. The gradient record has the
+ * same layout (d/dmx ... d/dvis). */
+
+/* Render conventions. Defaults (sssgs_cfg_default): tile 16, dilation 0.3 px^2,
+ * det_eps 1e-6 px^4, z_near 0.2, alpha_min 1/255, alpha_max 0.99, T_min 1e-4,
+ * A_eps 1e-6. All values are float32. */
+typedef struct sssgs_cfg {
+    int32_t tile;        /* tile edge in pixels: 8, 16 or 32 */
+    int32_t reserved;    /* must be 0 */
+    float dilation;      /* low-pass dilation added to the 2D covariance diagonal */
+    float det_eps;       /* cull if det(Sigma') <= det_eps (guards the conic inverse) */
+    float z_near;        /* cull if view depth < z_near */
+    float alpha_min;     /* skip contributions below this alpha */
+    float alpha_max;     /* clamp alpha */
+    float T_min;         /* stop before transmittance falls below T_min */
+    float A_eps;         /* shading normalises by max(A, A_eps) */
+} sssgs_cfg;
+
+/* One view/light pair. The caller fills the first block; sssgs_plan fills
+ * the layout block. The same array must be passed as host copy (h_pairs) and
+ * device copy (d_pairs, 16-byte aligned) to every call. 128 bytes. */
+typedef struct sssgs_pair {
+    float R[9];          /* world->camera rotation, row-major */
+    float t[3];          /* x_cam = R x_world + t */
+    float fx, fy, cx, cy;
+    float light[3];      /* OLAT point-light position (world) */
+    int32_t W, H;        /* image size in pixels */
+    int32_t g_begin;     /* this pair renders Gaussians [g_begin, g_begin + g_count) */
+    int32_t g_count;     /*   of the scene arrays */
+    /* --- filled by sssgs_plan --- */
+    int32_t tiles_x, tiles_y;
+    int32_t tile_offset;   /* first global tile id of this pair */
+    int32_t pad0, pad1;
+    int64_t pixel_offset;  /* first global pixel of this pair (row-major within the pair) */
+    int64_t item_offset;   /* first (pair, Gaussian) item row of this pair */
+} sssgs_pair;
+
+/* Totals of a planned batch. */
+typedef struct sssgs_plan_info {
+    int64_t n_items;       /* sum of g_count */
+    int64_t n_pixels;      /* sum of W*H */
+    int32_t n_tiles;       /* sum of tiles_x*tiles_y */
+    int32_t tile_bits;     /* bits needed for a global tile id */
+} sssgs_plan_info;
+
+/* Per-Gaussian parameters (float32 device arrays, concatenated over scenes):
+ * mu N*3, log_s N*3, quat N*4 (w,x,y,z; normalised inside), logit_o N,
+ * normal N*3, base N*3, rough N, metal N, sss N, vis N. */
+typedef struct sssgs_scene {
+    const float *mu, *log_s, *quat, *logit_o, *normal, *base, *rough, *metal, *sss, *vis;
+    int64_t n;
+} sssgs_scene;
+
+/* Gradients of the same shapes (accumulated). Any pointer may be NULL to skip. */
+typedef struct sssgs_scene_grad {
+    float *mu, *log_s, *quat, *logit_o, *normal, *base, *rough, *metal, *sss, *vis;
+} sssgs_scene_grad;
+
+enum { SSSGS_MLP_BASIC = 0, SSSGS_MLP_PE6 = 1 };
+enum { SSSGS_FP32 = 0, SSSGS_BF16 = 1 };
+
+/* Residual / incident-light MLP (Eq. 6; Appendix E "Network"). Input per
+ * (pair, Gaussian), with w_out = unit(camera - mu), w_in = unit(light - mu):
+ *   BASIC: [mu, w_out, w_in] (width[0] = 9)
+ *   PE6:   [sin(2^k pi mu), cos(2^k pi mu) (k<6, 36), mu, w_out, w_in, n,
+ *           |light - mu|, v] = 50, zero-padded (width[0] = 64)
+ * Linear layers W[l] (width[l+1] x width[l], row-major, float32) + b[l], ReLU
+ * between layers; width[n_layers] = 4: sigmoid -> L_SSS (3), ReLU -> L_in. */
+typedef struct sssgs_mlp {
+    int32_t kind;        /* SSSGS_MLP_BASIC or SSSGS_MLP_PE6 */
+    int32_t n_layers;    /* 2 .. SSSGS_MAX_LAYERS */
+    int32_t precision;   /* SSSGS_FP32 (CUDA cores) or SSSGS_BF16 (tensor cores, FP32 accumulate) */
+    int32_t width[SSSGS_MAX_LAYERS + 1];
+    const float* W[SSSGS_MAX_LAYERS];
+    const float* b[SSSGS_MAX_LAYERS];
+} sssgs_mlp;
+
+typedef struct sssgs_mlp_grad {
+    float* W[SSSGS_MAX_LAYERS];
+    float* b[SSSGS_MAX_LAYERS];
+} sssgs_mlp_grad;
+
+/* ---------------------------------------------------------------------- */
+
+const char* sssgs_version(void);
+
+/* Number of kernels libsssgs has launched in this process (host-side counter,
+ * incremented at every launch site; for accounting in benchmarks). */
+uint64_t sssgs_launch_count(void);
+const char* sssgs_strerror(int code);
+void sssgs_cfg_default(sssgs_cfg* cfg);
+
+/* Fill the layout fields of pairs[0..n_pairs) (host memory) and the totals.
+ * Pairs must have W, H in 1..16384 and g_count >= 0. Host only. */
+int sssgs_plan(sssgs_pair* pairs, int n_pairs, const sssgs_cfg* cfg, sssgs_plan_info* info);
+
+/* a0 -- network forward (Eq. 6). out[n_items*4] = (L_SSS rgb, L_in) per item. */
+int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                  int n_pairs, const sssgs_scene* scene, float* out, sssgs_stream stream);
+
+/* a5 -- network backward. Reads dL/d(L_SSS, L_in) from the gradient records
+ * drec (fields 16..19) and accumulates weight/bias gradients into grad and
+ * per-item input gradients into dx_items[n_items*7] = (dmu 3, dn 3, dv 1).
+ * workspace: sssgs_mlp_workspace_bytes(mlp, n_items) bytes (any alignment >= 256). */
+size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_items);
+int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                  int n_pairs, const sssgs_scene* scene, const float* drec,
+                  const sssgs_mlp_grad* grad, float* dx_items,
+                  void* workspace, size_t workspace_bytes, sssgs_stream stream);
+
+/* a1 -- EWA projection (Eq. 1, Eq. 2). Per item writes the packed record
+ * (rec[n_items*24], features copied from the scene and from mlp_out[n_items*4])
+ * and the inclusive tile rectangle rect[n_items*4] = (tx0, tx1, ty0, ty1) of
+ * the ellipse {p <= ln(o / alpha_min)}; tx0 > tx1 marks a culled item. */
+int sssgs_project_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                      int n_pairs, const sssgs_scene* scene, const float* mlp_out,
+                      float* rec, int32_t* rect, sssgs_stream stream);
+
+/* a2 -- tile binning + stable radix sort. Orders the items of each pair by
+ * (float32 depth bits of rec[6], item), emits one instance per tile of each
+ * rectangle, and stably sorts instances by global tile id, giving the order
+ * (tile, depth, item). Outputs: vals[capacity] item id per instance,
+ * ranges[n_tiles*2] = [start, end) per global tile, d_count = number of
+ * instances (device int64). If more than `capacity` instances arise,
+ * SSSGS_STATUS_CAPACITY is set in *d_status and lists are truncated.
+ * workspace: sssgs_bin_workspace_bytes(n_items, capacity, n_tiles). */
+size_t sssgs_bin_workspace_bytes(int64_t n_items, int64_t capacity, int32_t n_tiles);
+int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                   int n_pairs, const float* rec, const int32_t* rect, int64_t capacity,
+                   uint32_t* vals, uint32_t* ranges, int64_t* d_count, int32_t* d_status,
+                   void* workspace, size_t workspace_bytes, sssgs_stream stream);
+
+/* a3 -- front-to-back compositing (Eq. 3) into gbuf[n_pixels*16] (15 features
+ * weighted by w_i = T_i alpha_i, then the final T) and last[n_pixels] (one past
+ * the list position of the last contribution). */
+int sssgs_composite_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                        int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                        float* gbuf, uint32_t* last, sssgs_stream stream);
+
+/* a4 -- deferred shading (Eq. 4, Eq. 7): img[n_pixels*3] from gbuf. */
+int sssgs_shade_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                    int n_pairs, const float* gbuf, float* img, sssgs_stream stream);
+
+/* a4 backward: dgbuf[n_pixels*16] (written, not accumulated) from dimg. */
+int sssgs_shade_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                    int n_pairs, const float* gbuf, const float* dimg, float* dgbuf,
+                    sssgs_stream stream);
+
+/* a3 backward: back-to-front replay from the stored final T (no per-pixel
+ * lists kept). Accumulates per-item gradient records into drec[n_items*24]. */
+int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                        int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                        const float* gbuf, const uint32_t* last, const float* dgbuf,
+                        float* drec, sssgs_stream stream);
+
+/* Fused a3+a4 forward: composite then shade in one pass; writes gbuf, last, img. */
+int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                     int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                     float* gbuf, uint32_t* last, float* img, sssgs_stream stream);
+
+/* Fused a4+a3 backward. Upstream gradient either dimg[n_pixels*3], or (dimg ==
+ * NULL) the L1 loss  l1_scale * sum |img - target|  with optional per-pixel
+ * weights (NULL = 1): dimg = l1_scale * w * sign(img - target). Accumulates drec. */
+int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                     int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                     const float* gbuf, const uint32_t* last, const float* img,
+                     const float* dimg, const float* target, const float* weight, float l1_scale,
+                     float* drec, sssgs_stream stream);
+
+/* a5 -- projection backward. For every Gaussian of the scene, sums over the
+ * pairs that render it: the gradient records drec (geometry via Eq. 2 and the
+ * covariance parameterisation, features directly) and, if dx_items != NULL,
+ * the network-input gradients from sssgs_mlp_bwd. Accumulates into grad. */
+int sssgs_project_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                      int n_pairs, const sssgs_scene* scene, const float* drec,
+                      const float* dx_items, const sssgs_scene_grad* grad, sssgs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSSGS_H */

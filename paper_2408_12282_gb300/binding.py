@@ -1,0 +1,278 @@
+"""ctypes binding of libsssgs (include/sssgs.h): argument marshalling only.
+
+Every function here has the name of the C entry point without the `sssgs_`
+prefix, takes torch tensors (or None) for device pointers, and raises
+SSSGSError on a non-zero return code. No compute happens in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+c_i32, c_i64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
+MAX_LAYERS = 8
+NF, REC, GBUF = 15, 24, 16
+MLP_BASIC, MLP_PE6 = 0, 1
+FP32, BF16 = 0, 1
+STATUS_CAPACITY = 1
+
+
+class SSSGSError(RuntimeError):
+    pass
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("tile", c_i32), ("reserved", c_i32), ("dilation", c_f32), ("det_eps", c_f32),
+                ("z_near", c_f32), ("alpha_min", c_f32), ("alpha_max", c_f32), ("T_min", c_f32),
+                ("A_eps", c_f32)]
+
+
+class Pair(ctypes.Structure):
+    _fields_ = [("R", c_f32 * 9), ("t", c_f32 * 3), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32),
+                ("cy", c_f32), ("light", c_f32 * 3), ("W", c_i32), ("H", c_i32), ("g_begin", c_i32),
+                ("g_count", c_i32), ("tiles_x", c_i32), ("tiles_y", c_i32), ("tile_offset", c_i32),
+                ("pad0", c_i32), ("pad1", c_i32), ("pixel_offset", c_i64), ("item_offset", c_i64)]
+
+
+assert ctypes.sizeof(Pair) == 128
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_items", c_i64), ("n_pixels", c_i64), ("n_tiles", c_i32), ("tile_bits", c_i32)]
+
+
+_SCENE_FIELDS = ("mu", "log_s", "quat", "logit_o", "normal", "base", "rough", "metal", "sss", "vis")
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [(k, c_vp) for k in _SCENE_FIELDS] + [("n", c_i64)]
+
+
+class SceneGrad(ctypes.Structure):
+    _fields_ = [(k, c_vp) for k in _SCENE_FIELDS]
+
+
+class MLP(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("n_layers", c_i32), ("precision", c_i32),
+                ("width", c_i32 * (MAX_LAYERS + 1)), ("W", c_vp * MAX_LAYERS), ("b", c_vp * MAX_LAYERS)]
+
+
+class MLPGrad(ctypes.Structure):
+    _fields_ = [("W", c_vp * MAX_LAYERS), ("b", c_vp * MAX_LAYERS)]
+
+
+_LIB = None
+
+_SIGS = {
+    "sssgs_version": ([], ctypes.c_char_p),
+    "sssgs_launch_count": ([], ctypes.c_uint64),
+    "sssgs_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "sssgs_cfg_default": ([ctypes.POINTER(Cfg)], None),
+    "sssgs_plan": ([ctypes.POINTER(Pair), ctypes.c_int, ctypes.POINTER(Cfg), ctypes.POINTER(PlanInfo)], ctypes.c_int),
+    "sssgs_mlp_fwd": ([ctypes.POINTER(MLP), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp,
+                       c_vp], ctypes.c_int),
+    "sssgs_mlp_workspace_bytes": ([ctypes.POINTER(MLP), c_i64], ctypes.c_size_t),
+    "sssgs_mlp_bwd": ([ctypes.POINTER(MLP), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp,
+                       ctypes.POINTER(MLPGrad), c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
+    "sssgs_project_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
+                           c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_bin_workspace_bytes": ([c_i64, c_i64, c_i32], ctypes.c_size_t),
+    "sssgs_bin_sort": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_i64, c_vp,
+                        c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
+    "sssgs_composite_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
+                             c_vp, c_vp], ctypes.c_int),
+    "sssgs_shade_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp],
+                        ctypes.c_int),
+    "sssgs_shade_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp],
+                        ctypes.c_int),
+    "sssgs_composite_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
+                             c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_render_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
+                          c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_render_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
+                          c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp], ctypes.c_int),
+    "sssgs_project_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
+                           c_vp, c_vp, ctypes.POINTER(SceneGrad), c_vp], ctypes.c_int),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libsssgs.so; raise if it is missing (there is no fallback path)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise SSSGSError(f"CUDA library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def _p(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(rc, name):
+    if rc != 0:
+        msg = load_library().sssgs_strerror(rc).decode()
+        raise SSSGSError(f"{name} failed: {rc} ({msg})")
+
+
+# --------------------------------------------------------------------------- structs
+
+def cfg_default() -> Cfg:
+    c = Cfg()
+    load_library().sssgs_cfg_default(ctypes.byref(c))
+    return c
+
+
+def version() -> str:
+    return load_library().sssgs_version().decode()
+
+
+def launch_count() -> int:
+    return int(load_library().sssgs_launch_count())
+
+
+def strerror(code: int) -> str:
+    return load_library().sssgs_strerror(code).decode()
+
+
+def plan(pairs_arr, cfg: Cfg) -> PlanInfo:
+    info = PlanInfo()
+    _check(load_library().sssgs_plan(pairs_arr, len(pairs_arr), ctypes.byref(cfg), ctypes.byref(info)), "sssgs_plan")
+    return info
+
+
+def scene_struct(t: dict) -> Scene:
+    s = Scene(*[_p(t[k]) for k in _SCENE_FIELDS], t["mu"].shape[0])
+    return s
+
+
+def scene_grad_struct(t: dict) -> SceneGrad:
+    return SceneGrad(*[_p(t.get(k)) for k in _SCENE_FIELDS])
+
+
+def mlp_struct(kind: int, precision: int, Ws, bs) -> MLP:
+    m = MLP()
+    m.kind = kind
+    m.precision = precision
+    m.n_layers = len(Ws)
+    m.width[0] = Ws[0].shape[1]
+    for l, W in enumerate(Ws):
+        m.width[l + 1] = W.shape[0]
+        m.W[l] = _p(W)
+        m.b[l] = _p(bs[l])
+    return m
+
+
+def mlp_grad_struct(dWs, dbs) -> MLPGrad:
+    g = MLPGrad()
+    for l, W in enumerate(dWs):
+        g.W[l] = _p(W)
+        g.b[l] = _p(dbs[l]) if dbs is not None else None
+    return g
+
+
+# --------------------------------------------------------------------------- entry points
+
+def mlp_fwd(mlp: MLP, pairs, d_pairs, scene: Scene, out, stream=None):
+    _check(load_library().sssgs_mlp_fwd(ctypes.byref(mlp), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
+                                        _p(out), _stream(stream)), "sssgs_mlp_fwd")
+
+
+def mlp_workspace_bytes(mlp: MLP, n_items: int) -> int:
+    return int(load_library().sssgs_mlp_workspace_bytes(ctypes.byref(mlp), n_items))
+
+
+def mlp_bwd(mlp: MLP, pairs, d_pairs, scene: Scene, drec, grad: MLPGrad, dx_items, workspace, stream=None):
+    _check(load_library().sssgs_mlp_bwd(ctypes.byref(mlp), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
+                                        _p(drec), ctypes.byref(grad), _p(dx_items), _p(workspace),
+                                        workspace.numel() * workspace.element_size() if workspace is not None else 0,
+                                        _stream(stream)), "sssgs_mlp_bwd")
+
+
+def project_fwd(cfg: Cfg, pairs, d_pairs, scene: Scene, mlp_out, rec, rect, stream=None):
+    _check(load_library().sssgs_project_fwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
+                                            _p(mlp_out), _p(rec), _p(rect), _stream(stream)), "sssgs_project_fwd")
+
+
+def bin_workspace_bytes(n_items: int, capacity: int, n_tiles: int) -> int:
+    return int(load_library().sssgs_bin_workspace_bytes(n_items, capacity, n_tiles))
+
+
+def bin_sort(cfg: Cfg, pairs, d_pairs, rec, rect, capacity: int, vals, ranges, d_count, d_status, workspace,
+             stream=None):
+    _check(load_library().sssgs_bin_sort(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(rect),
+                                         capacity, _p(vals), _p(ranges), _p(d_count), _p(d_status), _p(workspace),
+                                         workspace.numel() * workspace.element_size(), _stream(stream)),
+           "sssgs_bin_sort")
+
+
+def composite_fwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, stream=None):
+    _check(load_library().sssgs_composite_fwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(vals),
+                                              _p(ranges), _p(gbuf), _p(last), _stream(stream)),
+           "sssgs_composite_fwd")
+
+
+def shade_fwd(cfg: Cfg, pairs, d_pairs, gbuf, img, stream=None):
+    _check(load_library().sssgs_shade_fwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(gbuf), _p(img),
+                                          _stream(stream)), "sssgs_shade_fwd")
+
+
+def shade_bwd(cfg: Cfg, pairs, d_pairs, gbuf, dimg, dgbuf, stream=None):
+    _check(load_library().sssgs_shade_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(gbuf), _p(dimg),
+                                          _p(dgbuf), _stream(stream)), "sssgs_shade_bwd")
+
+
+def composite_bwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, dgbuf, drec, stream=None):
+    _check(load_library().sssgs_composite_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(vals),
+                                              _p(ranges), _p(gbuf), _p(last), _p(dgbuf), _p(drec),
+                                              _stream(stream)), "sssgs_composite_bwd")
+
+
+def render_fwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, stream=None):
+    _check(load_library().sssgs_render_fwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(vals),
+                                           _p(ranges), _p(gbuf), _p(last), _p(img), _stream(stream)),
+           "sssgs_render_fwd")
+
+
+def render_bwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, dimg, target, weight, l1_scale,
+               drec, stream=None):
+    _check(load_library().sssgs_render_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(vals),
+                                           _p(ranges), _p(gbuf), _p(last), _p(img), _p(dimg), _p(target),
+                                           _p(weight), float(l1_scale), _p(drec), _stream(stream)),
+           "sssgs_render_bwd")
+
+
+def project_bwd(cfg: Cfg, pairs, d_pairs, scene: Scene, drec, dx_items, grad: SceneGrad, stream=None):
+    _check(load_library().sssgs_project_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
+                                            _p(drec), _p(dx_items), ctypes.byref(grad), _stream(stream)),
+           "sssgs_project_bwd")

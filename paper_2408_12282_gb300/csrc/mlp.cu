@@ -1,0 +1,532 @@
+// Joint SSS-residual / incident-light network f_Theta (Eq. 6) on CUDA cores, FP32.
+//
+// Every (pair, Gaussian) item is one row. Its input is built in the kernel
+// from the Gaussian's mean (Fourier-encoded in the PE6 form, as the paper
+// does for mu), normal and visibility, and the pair's camera and light
+// (w_out, w_in, light distance). A CTA runs a 64-row tile through all layers
+// with activations and the current layer's weights in shared memory and a
+// 4 x (N/16) register micro-tile per thread. Heads: sigmoid -> L_SSS (rgb),
+// ReLU -> L_in (Appendix E "Network").
+//
+// Backward, per chunk of rows: phase A recomputes the forward of a 32-row tile,
+// back-propagates to every layer's pre-activation gradient dZ and to the
+// network input (mapped to d mu, d n, d v per item), storing H and dZ in the
+// workspace; phase B reduces dW = sum_rows dZ^T H and db = sum_rows dZ with a
+// register micro-tile per thread and one atomic per weight per CTA.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace sssgs {
+
+constexpr int MLP_THREADS = 256;
+constexpr int MLP_MAXW = 128;
+constexpr int MLP_LDA = MLP_MAXW + 4;
+constexpr int FWD_ROWS = 64;
+constexpr int BWD_ROWS = 32;
+constexpr int64_t MLP_CHUNK = 131072;
+
+struct MlpDev {
+    int kind, L;
+    int w[SSSGS_MAX_LAYERS + 1];
+    const float* W[SSSGS_MAX_LAYERS];
+    const float* b[SSSGS_MAX_LAYERS];
+};
+
+// Network input of item m (row of width w[0]) written to x.
+__device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
+                                            int64_t g, float* x) {
+    const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
+    const float3 C = cam_center(P);
+    float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
+    float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    if (net.kind == SSSGS_MLP_BASIC) {
+        x[0] = m0; x[1] = m1; x[2] = m2;
+        x[3] = wo.x; x[4] = wo.y; x[5] = wo.z;
+        x[6] = wi.x; x[7] = wi.y; x[8] = wi.z;
+        return;
+    }
+    const float mm[3] = {m0, m1, m2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float f = ldexpf(kPi, k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s, co;
+            sincosf(f * mm[c], &s, &co);
+            x[6 * k + c] = s;
+            x[6 * k + 3 + c] = co;
+        }
+    }
+    x[36] = m0; x[37] = m1; x[38] = m2;
+    x[39] = wo.x; x[40] = wo.y; x[41] = wo.z;
+    x[42] = wi.x; x[43] = wi.y; x[44] = wi.z;
+    x[45] = sc.normal[3 * g]; x[46] = sc.normal[3 * g + 1]; x[47] = sc.normal[3 * g + 2];
+    x[48] = li;
+    x[49] = sc.vis[g];
+    for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
+}
+
+// Input gradient dX (row) -> (dmu, dn, dv) of item m, written to dx[7].
+__device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
+                                               int64_t g, const float* dX, float* dx) {
+    const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
+    const float3 C = cam_center(P);
+    float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
+    float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    int o_mu, o_wo, o_wi;
+    float dmu[3] = {0.f, 0.f, 0.f};
+    if (net.kind == SSSGS_MLP_BASIC) {
+        o_mu = 0; o_wo = 3; o_wi = 6;
+        dx[3] = dx[4] = dx[5] = dx[6] = 0.f;
+    } else {
+        o_mu = 36; o_wo = 39; o_wi = 42;
+        const float mm[3] = {m0, m1, m2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float f = ldexpf(kPi, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s, co;
+                sincosf(f * mm[c], &s, &co);
+                dmu[c] += f * (dX[6 * k + c] * co - dX[6 * k + 3 + c] * s);
+            }
+        }
+        dx[3] = dX[45]; dx[4] = dX[46]; dx[5] = dX[47];
+        dx[6] = dX[49];
+        dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
+    }
+    dmu[0] += dX[o_mu]; dmu[1] += dX[o_mu + 1]; dmu[2] += dX[o_mu + 2];
+    // d unit(P - mu) / d mu applied to g:  -(g - w (w.g)) / |P - mu|
+    const float3 go = make_float3(dX[o_wo], dX[o_wo + 1], dX[o_wo + 2]);
+    const float3 gi = make_float3(dX[o_wi], dX[o_wi + 1], dX[o_wi + 2]);
+    const float3 bo = (-1.f / lo) * (go - dot3(wo, go) * wo);
+    const float3 bi = (-1.f / li) * (gi - dot3(wi, gi) * wi);
+    dx[0] = dmu[0] + bo.x + bi.x;
+    dx[1] = dmu[1] + bo.y + bi.y;
+    dx[2] = dmu[2] + bo.z + bi.z;
+}
+
+// out[r][j] = bias[j] + sum_i in[r][i] * M[i*J + j] over a ROWS-row tile
+// (act 1: ReLU; mask != null: out *= (mask[r][j] > 0)). J multiple of 16.
+template <int ROWS, int CJ>
+__device__ __forceinline__ void tile_gemm16(const float* in, int I, const float* M, const float* bias, float* out,
+                                            int act, const float* mask) {
+    constexpr int J = 16 * CJ;
+    constexpr int RR = ROWS / 16;
+    const int t = threadIdx.x, rg = t >> 4, cg = t & 15;
+    float acc[RR][CJ];
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+        for (int c = 0; c < CJ; ++c) acc[r][c] = bias ? bias[cg * CJ + c] : 0.f;
+    for (int i = 0; i < I; ++i) {
+        float a[RR], w[CJ];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) a[r] = in[(rg * RR + r) * MLP_LDA + i];
+#pragma unroll
+        for (int c = 0; c < CJ; ++c) w[c] = M[i * J + cg * CJ + c];
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+#pragma unroll
+            for (int c = 0; c < CJ; ++c) acc[r][c] = fmaf(a[r], w[c], acc[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+        for (int c = 0; c < CJ; ++c) {
+            const int row = rg * RR + r, col = cg * CJ + c;
+            float v = acc[r][c];
+            if (act == 1) v = fmaxf(v, 0.f);
+            if (mask && !(mask[row * MLP_LDA + col] > 0.f)) v = 0.f;
+            out[row * MLP_LDA + col] = v;
+        }
+}
+
+// Generic (any J) variant: one output per thread-iteration.
+template <int ROWS>
+__device__ __forceinline__ void tile_gemm_any(const float* in, int I, const float* M, int J, const float* bias,
+                                              float* out, int act, const float* mask) {
+    for (int o = threadIdx.x; o < ROWS * J; o += MLP_THREADS) {
+        const int row = o / J, col = o % J;
+        float v = bias ? bias[col] : 0.f;
+        for (int i = 0; i < I; ++i) v = fmaf(in[row * MLP_LDA + i], M[i * J + col], v);
+        if (act == 1) v = fmaxf(v, 0.f);
+        if (mask && !(mask[row * MLP_LDA + col] > 0.f)) v = 0.f;
+        out[row * MLP_LDA + col] = v;
+    }
+}
+
+template <int ROWS>
+__device__ __forceinline__ void tile_gemm(const float* in, int I, const float* M, int J, const float* bias,
+                                          float* out, int act, const float* mask) {
+    switch (J) {
+        case 16: tile_gemm16<ROWS, 1>(in, I, M, bias, out, act, mask); break;
+        case 32: tile_gemm16<ROWS, 2>(in, I, M, bias, out, act, mask); break;
+        case 64: tile_gemm16<ROWS, 4>(in, I, M, bias, out, act, mask); break;
+        case 128: tile_gemm16<ROWS, 8>(in, I, M, bias, out, act, mask); break;
+        default: tile_gemm_any<ROWS>(in, I, M, J, bias, out, act, mask); break;
+    }
+}
+
+// Stage layer weights in shared memory: transposed (K x N, for H W^T) or
+// as stored (N x K, for dZ W).
+__device__ __forceinline__ void stage_weights(const float* __restrict__ W, int N, int K, bool transpose, float* sW) {
+    for (int i = threadIdx.x; i < N * K; i += MLP_THREADS) {
+        const int n = i / K, k = i - n * K;
+        const float v = W[i];
+        if (transpose) sW[k * N + n] = v; else sW[i] = v;
+    }
+}
+
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpDev net, const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                                         int64_t n_items, sssgs_scene sc, float* __restrict__ out) {
+    extern __shared__ float smem[];
+    float* sA = smem;
+    float* sB = sA + FWD_ROWS * MLP_LDA;
+    float* sW = sB + FWD_ROWS * MLP_LDA;
+    float* sb = sW + MLP_MAXW * MLP_MAXW;
+    const int64_t n_tiles = (n_items + FWD_ROWS - 1) / FWD_ROWS;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t row0 = tile * FWD_ROWS;
+        if (threadIdx.x < FWD_ROWS) {
+            const int64_t m = row0 + threadIdx.x;
+            float* x = sA + threadIdx.x * MLP_LDA;
+            if (m < n_items) {
+                const int p = pair_of_item(pairs, n_pairs, m);
+                const sssgs_pair& P = pairs[p];
+                build_input(net, P, sc, P.g_begin + (m - P.item_offset), x);
+            } else {
+                for (int k = 0; k < net.w[0]; ++k) x[k] = 0.f;
+            }
+        }
+        float* cur = sA;
+        float* nxt = sB;
+        for (int l = 0; l < net.L; ++l) {
+            const int K = net.w[l], N = net.w[l + 1];
+            __syncthreads();
+            stage_weights(net.W[l], N, K, true, sW);
+            for (int i = threadIdx.x; i < N; i += MLP_THREADS) sb[i] = net.b[l][i];
+            __syncthreads();
+            tile_gemm<FWD_ROWS>(cur, K, sW, N, sb, nxt, l < net.L - 1 ? 1 : 0, nullptr);
+            float* t = cur; cur = nxt; nxt = t;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < FWD_ROWS * 4; o += MLP_THREADS) {
+            const int r = o >> 2, c = o & 3;
+            const int64_t m = row0 + r;
+            if (m >= n_items) continue;
+            const float y = cur[r * MLP_LDA + c];
+            out[4 * m + c] = c < 3 ? 1.f / (1.f + expf(-y)) : fmaxf(y, 0.f);
+        }
+        __syncthreads();   // the next tile overwrites the buffers read above
+    }
+}
+
+// Phase A: recompute, back-propagate, store H_l and dZ_{l+1} for the chunk.
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sssgs_pair* __restrict__ pairs,
+                                                           int n_pairs, int64_t row_begin, int64_t rows,
+                                                           sssgs_scene sc, const float* __restrict__ drec,
+                                                           float* __restrict__ ws, int64_t chunk,
+                                                           float* __restrict__ dx_items) {
+    extern __shared__ float smem[];
+    float* sH = smem;                                          // [L][BWD_ROWS][LDA]
+    float* sD0 = sH + net.L * BWD_ROWS * MLP_LDA;
+    float* sD1 = sD0 + BWD_ROWS * MLP_LDA;
+    float* sW = sD1 + BWD_ROWS * MLP_LDA;
+    float* sb = sW + MLP_MAXW * MLP_MAXW;
+    // workspace offsets (floats): H_l then dZ_{l+1}, each chunk x width
+    int64_t offH[SSSGS_MAX_LAYERS], offD[SSSGS_MAX_LAYERS];
+    {
+        int64_t o = 0;
+        for (int l = 0; l < net.L; ++l) { offH[l] = o; o += chunk * net.w[l]; }
+        for (int l = 0; l < net.L; ++l) { offD[l] = o; o += chunk * net.w[l + 1]; }
+    }
+    const int64_t n_tiles = (rows + BWD_ROWS - 1) / BWD_ROWS;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t r0 = tile * BWD_ROWS;           // row within the chunk
+        if (threadIdx.x < BWD_ROWS) {
+            const int64_t m = row_begin + r0 + threadIdx.x;
+            float* x = sH + threadIdx.x * MLP_LDA;
+            if (r0 + threadIdx.x < rows) {
+                const int p = pair_of_item(pairs, n_pairs, m);
+                const sssgs_pair& P = pairs[p];
+                build_input(net, P, sc, P.g_begin + (m - P.item_offset), x);
+            } else {
+                for (int k = 0; k < net.w[0]; ++k) x[k] = 0.f;
+            }
+        }
+        // forward, keeping every layer input
+        for (int l = 0; l < net.L; ++l) {
+            const int K = net.w[l], N = net.w[l + 1];
+            __syncthreads();
+            stage_weights(net.W[l], N, K, true, sW);
+            for (int i = threadIdx.x; i < N; i += MLP_THREADS) sb[i] = net.b[l][i];
+            __syncthreads();
+            float* dst = (l < net.L - 1) ? sH + (l + 1) * BWD_ROWS * MLP_LDA : sD0;
+            tile_gemm<BWD_ROWS>(sH + l * BWD_ROWS * MLP_LDA, K, sW, N, sb, dst, l < net.L - 1 ? 1 : 0, nullptr);
+        }
+        __syncthreads();
+        // heads: dZ_L from dL/d(L_SSS, L_in)
+        for (int o = threadIdx.x; o < BWD_ROWS * 4; o += MLP_THREADS) {
+            const int r = o >> 2, c = o & 3;
+            const float y = sD0[r * MLP_LDA + c];
+            float d = 0.f;
+            if (r0 + r < rows) {
+                const float up = drec[(int64_t)SSSGS_REC * (row_begin + r0 + r) + 16 + c];
+                if (c < 3) {
+                    const float s = 1.f / (1.f + expf(-y));
+                    d = up * s * (1.f - s);
+                } else {
+                    d = y > 0.f ? up : 0.f;
+                }
+            }
+            sD0[r * MLP_LDA + c] = d;
+        }
+        float* dcur = sD0;
+        float* dnxt = sD1;
+        for (int l = net.L - 1; l >= 0; --l) {
+            const int K = net.w[l], N = net.w[l + 1];
+            __syncthreads();
+            // store H_l and dZ_{l+1} rows of this tile
+            for (int o = threadIdx.x; o < BWD_ROWS * K; o += MLP_THREADS) {
+                const int r = o / K, k = o - r * K;
+                if (r0 + r < rows) ws[offH[l] + (r0 + r) * K + k] = sH[(l * BWD_ROWS + r) * MLP_LDA + k];
+            }
+            for (int o = threadIdx.x; o < BWD_ROWS * N; o += MLP_THREADS) {
+                const int r = o / N, n = o - r * N;
+                if (r0 + r < rows) ws[offD[l] + (r0 + r) * N + n] = dcur[r * MLP_LDA + n];
+            }
+            stage_weights(net.W[l], N, K, false, sW);
+            __syncthreads();
+            // dH_l = dZ_{l+1} W_l ; dZ_l = dH_l * [H_l > 0] (l > 0)
+            tile_gemm<BWD_ROWS>(dcur, N, sW, K, nullptr, dnxt, 0,
+                                l > 0 ? sH + l * BWD_ROWS * MLP_LDA : nullptr);
+            float* t = dcur; dcur = dnxt; dnxt = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < BWD_ROWS && r0 + threadIdx.x < rows) {
+            const int64_t m = row_begin + r0 + threadIdx.x;
+            const int p = pair_of_item(pairs, n_pairs, m);
+            const sssgs_pair& P = pairs[p];
+            float dx[7];
+            input_backward(net, P, sc, P.g_begin + (m - P.item_offset), dcur + threadIdx.x * MLP_LDA, dx);
+            for (int k = 0; k < 7; ++k) dx_items[7 * m + k] += dx[k];
+        }
+        __syncthreads();   // the next tile overwrites the buffers read above
+    }
+}
+
+// Phase B: dW_l += sum_rows dZ_{l+1}^T H_l, db_l += sum_rows dZ_{l+1}.
+template <int TN, int TK>
+__device__ __forceinline__ void reduce_dw16(const float* sD, const float* sHt, int rows_here, int N, int K,
+                                            float* __restrict__ dW) {
+    const int t = threadIdx.x, ng = t >> 4, kg = t & 15;
+    float acc[TN][TK];
+#pragma unroll
+    for (int a = 0; a < TN; ++a)
+#pragma unroll
+        for (int b = 0; b < TK; ++b) acc[a][b] = 0.f;
+    for (int r = 0; r < rows_here; ++r) {
+        float d[TN], h[TK];
+#pragma unroll
+        for (int a = 0; a < TN; ++a) d[a] = sD[r * MLP_LDA + ng * TN + a];
+#pragma unroll
+        for (int b = 0; b < TK; ++b) h[b] = sHt[r * MLP_LDA + kg * TK + b];
+#pragma unroll
+        for (int a = 0; a < TN; ++a)
+#pragma unroll
+            for (int b = 0; b < TK; ++b) acc[a][b] = fmaf(d[a], h[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TN; ++a)
+#pragma unroll
+        for (int b = 0; b < TK; ++b) atomicAdd(&dW[(ng * TN + a) * K + kg * TK + b], acc[a][b]);
+}
+
+template <int TN>
+__device__ __forceinline__ void reduce_dw_tk(const float* sD, const float* sH, int rows_here, int N, int K, float* dW) {
+    switch (K) {
+        case 16: reduce_dw16<TN, 1>(sD, sH, rows_here, N, K, dW); break;
+        case 32: reduce_dw16<TN, 2>(sD, sH, rows_here, N, K, dW); break;
+        case 64: reduce_dw16<TN, 4>(sD, sH, rows_here, N, K, dW); break;
+        default: reduce_dw16<TN, 8>(sD, sH, rows_here, N, K, dW); break;
+    }
+}
+
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_b(MlpDev net, int64_t rows, const float* __restrict__ ws,
+                                                           int64_t chunk, sssgs_mlp_grad gr) {
+    extern __shared__ float smem[];
+    float* sD = smem;                                   // [32][LDA]
+    float* sHs = sD + 32 * MLP_LDA;                     // [32][LDA]
+    const int l = blockIdx.y;
+    const int K = net.w[l], N = net.w[l + 1];
+    int64_t offH = 0, offD = 0;
+    {
+        int64_t o = 0;
+        for (int q = 0; q < net.L; ++q) { if (q == l) offH = o; o += chunk * net.w[q]; }
+        for (int q = 0; q < net.L; ++q) { if (q == l) offD = o; o += chunk * net.w[q + 1]; }
+    }
+    const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+    const int64_t rb = (int64_t)blockIdx.x * per;
+    const int64_t re = min(rows, rb + per);
+    const bool tiled = (N % 16 == 0) && (K % 16 == 0);
+    constexpr int GQ = 4;              // generic path: up to GQ * 256 outputs per layer
+    float accs[GQ] = {0.f, 0.f, 0.f, 0.f};
+    float dbias = 0.f;
+    for (int64_t r0 = rb; r0 < re; r0 += 32) {
+        const int rows_here = (int)min((int64_t)32, re - r0);
+        __syncthreads();
+        for (int o = threadIdx.x; o < rows_here * N; o += MLP_THREADS) {
+            const int r = o / N, n = o - r * N;
+            sD[r * MLP_LDA + n] = ws[offD + (r0 + r) * N + n];
+        }
+        for (int o = threadIdx.x; o < rows_here * K; o += MLP_THREADS) {
+            const int r = o / K, k = o - r * K;
+            sHs[r * MLP_LDA + k] = ws[offH + (r0 + r) * K + k];
+        }
+        __syncthreads();
+        if (threadIdx.x < N)
+            for (int r = 0; r < rows_here; ++r) dbias += sD[r * MLP_LDA + threadIdx.x];
+        if (tiled) {
+            switch (N) {
+                case 16: reduce_dw_tk<1>(sD, sHs, rows_here, N, K, gr.W[l]); break;
+                case 32: reduce_dw_tk<2>(sD, sHs, rows_here, N, K, gr.W[l]); break;
+                case 64: reduce_dw_tk<4>(sD, sHs, rows_here, N, K, gr.W[l]); break;
+                default: reduce_dw_tk<8>(sD, sHs, rows_here, N, K, gr.W[l]); break;
+            }
+        } else {
+            for (int q = 0; q < GQ; ++q) {
+                const int o = threadIdx.x + q * MLP_THREADS;
+                if (o >= N * K) break;
+                const int n = o / K, k = o - n * K;
+                float v = 0.f;
+                for (int r = 0; r < rows_here; ++r) v = fmaf(sD[r * MLP_LDA + n], sHs[r * MLP_LDA + k], v);
+                accs[q] += v;
+            }
+        }
+    }
+    if (!tiled)
+        for (int q = 0; q < GQ; ++q) {
+            const int o = threadIdx.x + q * MLP_THREADS;
+            if (o < N * K) atomicAdd(&gr.W[l][o], accs[q]);
+        }
+    if (threadIdx.x < N && gr.b[l]) atomicAdd(&gr.b[l][threadIdx.x], dbias);
+}
+
+}  // namespace sssgs
+
+using namespace sssgs;
+
+namespace {
+bool mlp_ok(const sssgs_mlp* m) {
+    if (!m || m->n_layers < 2 || m->n_layers > SSSGS_MAX_LAYERS) return false;
+    if (m->kind == SSSGS_MLP_BASIC && m->width[0] != 9) return false;
+    if (m->kind == SSSGS_MLP_PE6 && m->width[0] != 64) return false;
+    if (m->kind != SSSGS_MLP_BASIC && m->kind != SSSGS_MLP_PE6) return false;
+    if (m->width[m->n_layers] != 4) return false;
+    for (int l = 1; l < m->n_layers; ++l)
+        if (m->width[l] < 16 || m->width[l] > MLP_MAXW || m->width[l] % 16) return false;
+    for (int l = 0; l < m->n_layers; ++l) {
+        if (!m->W[l] || !m->b[l]) return false;
+        const bool tiled = m->width[l] % 16 == 0 && m->width[l + 1] % 16 == 0;
+        if (!tiled && m->width[l] * m->width[l + 1] > 4 * MLP_THREADS) return false;
+    }
+    return true;
+}
+
+MlpDev to_dev(const sssgs_mlp* m) {
+    MlpDev d;
+    d.kind = m->kind;
+    d.L = m->n_layers;
+    for (int l = 0; l <= SSSGS_MAX_LAYERS; ++l) d.w[l] = l <= m->n_layers ? m->width[l] : 0;
+    for (int l = 0; l < SSSGS_MAX_LAYERS; ++l) {
+        d.W[l] = l < m->n_layers ? m->W[l] : nullptr;
+        d.b[l] = l < m->n_layers ? m->b[l] : nullptr;
+    }
+    return d;
+}
+
+int64_t floats_per_row(const sssgs_mlp* m) {
+    int64_t f = 0;
+    for (int l = 0; l < m->n_layers; ++l) f += m->width[l] + m->width[l + 1];
+    return f;
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+}  // namespace
+
+int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                     const sssgs_scene* scene, float* out, sssgs_stream stream);
+
+extern "C" int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                             int n_pairs, const sssgs_scene* scene, float* out, sssgs_stream stream) {
+    if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !out) return SSSGS_ERR_INVALID_ARG;
+    if (mlp->precision == SSSGS_BF16) return sssgs_mlp_fwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, out, stream);
+    if (mlp->precision != SSSGS_FP32) return SSSGS_ERR_INVALID_ARG;
+    int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
+    if (n == 0) return SSSGS_OK;
+    size_t sm = (size_t)(2 * FWD_ROWS * MLP_LDA + MLP_MAXW * MLP_MAXW + MLP_MAXW) * 4;
+    cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int64_t tiles = (n + FWD_ROWS - 1) / FWD_ROWS;
+    int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms());
+    k_mlp_fwd<<<grid, MLP_THREADS, sm, (cudaStream_t)stream>>>(to_dev(mlp), d_pairs, n_pairs, n, *scene, out);
+    sssgs::note_launches(1);
+    return launch_status();
+}
+
+extern "C" size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_items) {
+    if (!mlp_ok(mlp) || n_items < 0) return 0;
+    int64_t chunk = std::min<int64_t>(std::max<int64_t>(n_items, 1), MLP_CHUNK);
+    return (size_t)(chunk * floats_per_row(mlp) * 4) + 256;
+}
+
+int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                     const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
+                     void* workspace, size_t workspace_bytes, sssgs_stream stream);
+
+extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                             int n_pairs, const sssgs_scene* scene, const float* drec,
+                             const sssgs_mlp_grad* grad, float* dx_items, void* workspace,
+                             size_t workspace_bytes, sssgs_stream stream) {
+    if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !drec || !grad || !dx_items)
+        return SSSGS_ERR_INVALID_ARG;
+    for (int l = 0; l < mlp->n_layers; ++l)
+        if (!grad->W[l]) return SSSGS_ERR_INVALID_ARG;
+    if (mlp->precision == SSSGS_BF16)
+        return sssgs_mlp_bwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
+                                workspace_bytes, stream);
+    int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
+    if (n == 0) return SSSGS_OK;
+    if (!workspace || workspace_bytes < sssgs_mlp_workspace_bytes(mlp, n)) return SSSGS_ERR_WORKSPACE;
+    int64_t chunk = std::min<int64_t>(n, MLP_CHUNK);
+    float* ws = (float*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    cudaStream_t st = (cudaStream_t)stream;
+    MlpDev net = to_dev(mlp);
+    size_t smA = (size_t)((mlp->n_layers + 2) * BWD_ROWS * MLP_LDA + MLP_MAXW * MLP_MAXW + MLP_MAXW) * 4;
+    size_t smB = (size_t)(2 * 32 * MLP_LDA) * 4;
+    cudaFuncSetAttribute(k_mlp_bwd_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
+    int sms = num_sms();
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        int64_t rows = std::min(chunk, n - r0);
+        int64_t tiles = (rows + BWD_ROWS - 1) / BWD_ROWS;
+        int grid = (int)std::min<int64_t>(tiles, (int64_t)sms);
+        k_mlp_bwd_a<<<grid, MLP_THREADS, smA, st>>>(net, d_pairs, n_pairs, r0, rows, *scene, drec, ws, chunk,
+                                                    dx_items);
+        sssgs::note_launches(1);
+        int splits = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, (int64_t)(2 * sms / mlp->n_layers + 1)));
+        dim3 gb((unsigned)splits, (unsigned)mlp->n_layers);
+        k_mlp_bwd_b<<<gb, MLP_THREADS, smB, st>>>(net, rows, ws, chunk, *grad);
+        sssgs::note_launches(1);
+    }
+    return launch_status();
+}

@@ -1,0 +1,568 @@
+// Per-pixel compositing (Eq. 3) into the deferred G-buffer and deferred
+// shading (Eq. 4, Eq. 7), forward and backward.
+//
+// One CTA per image tile, one thread per pixel. Each CTA walks its tile's
+// depth-ordered instance list in batches: every thread loads one packed 96-B
+// record (six 16-B loads) into shared memory, then all pixels of the tile
+// consume the batch from shared memory (broadcast reads). A pixel stops when
+// its transmittance would drop below T_min; a warp whose lanes have all
+// stopped skips the batch, and the CTA stops loading once every pixel is done
+// (__syncthreads_count).
+//
+// The backward replays each pixel's list back to front starting from the final
+// transmittance stored by the forward (T_i = T_{i+1} / (1 - alpha_i)), so no
+// per-pixel list is kept. Per-Gaussian gradients are summed over the 32 pixels
+// of a warp with a transposing butterfly (31 shuffles for up to 32 values,
+// after which lane k holds component k) and issued as one 21-lane
+// fire-and-forget add per warp, instead of one atomic per pixel.
+#include "common.cuh"
+
+namespace sssgs {
+
+// ---------------------------------------------------------------- shading
+
+// Deferred shading of one pixel (Eq. 4 BRDF, Eq. 7 blend). F: composited
+// features, T: final transmittance, (u, v): pixel centre. With BWD it also
+// back-propagates g3 = dLoss/d(out) to dF (15) and dT.
+template <bool BWD>
+__device__ __forceinline__ void shade_px(const float* F, float T, float u, float v, const sssgs_pair& P,
+                                         float A_eps, float* out, const float* g3, float* dF, float* dT) {
+    out[0] = out[1] = out[2] = 0.f;
+    if (BWD) {
+#pragma unroll
+        for (int k = 0; k < SSSGS_NF; ++k) dF[k] = 0.f;
+        *dT = 0.f;
+    }
+    if (!(T < 1.f)) return;                      // no contribution: black, no gradient
+    const float A = 1.f - T;
+    const float Ad = fmaxf(A, A_eps);
+    const float iA = 1.f / Ad;
+    float g[SSSGS_NF];
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) g[k] = F[k] * iA;
+    const float dbar = g[0], rb = g[7], mb = g[8], sb = g[9], Li = g[13];
+    const float3 nbar = make_float3(g[1], g[2], g[3]);
+    const float bb[3] = {g[4], g[5], g[6]};
+    const float Ls[3] = {g[10], g[11], g[12]};
+    // back-projected surface point x = R^T (dbar * ray - t)
+    const float3 ray = make_float3((u - P.cx) / P.fx, (v - P.cy) / P.fy, 1.f);
+    const float3 Xc = make_float3(dbar * ray.x - P.t[0], dbar * ray.y - P.t[1], dbar * ray.z - P.t[2]);
+    const float3 x = make_float3(P.R[0] * Xc.x + P.R[3] * Xc.y + P.R[6] * Xc.z,
+                                 P.R[1] * Xc.x + P.R[4] * Xc.y + P.R[7] * Xc.z,
+                                 P.R[2] * Xc.x + P.R[5] * Xc.y + P.R[8] * Xc.z);
+    const float3 C = cam_center(P);
+    const float3 Vo = C - x;
+    const float3 Vi = make_float3(P.light[0] - x.x, P.light[1] - x.y, P.light[2] - x.z);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    const float nn = fmaxf(sqrtf(dot3(nbar, nbar)), 1e-12f);
+    const float3 nh = (1.f / nn) * nbar;
+    const float3 Hv = wo + wi;
+    const float lh = fmaxf(sqrtf(dot3(Hv, Hv)), 1e-12f);
+    const float3 h = (1.f / lh) * Hv;
+    const float co = dot3(nh, wo), ci = dot3(nh, wi), ch = dot3(nh, h), cv = dot3(wo, h);
+    const float no = fmaxf(co, 0.f), ni = fmaxf(ci, 0.f), nhc = fmaxf(ch, 0.f), vh = fmaxf(cv, 0.f);
+    const float ar = rb * rb, a2 = ar * ar;
+    const float den = nhc * nhc * (a2 - 1.f) + 1.f;
+    const float D = a2 / (kPi * den * den);
+    const float so = sqrtf(a2 + (1.f - a2) * no * no), si = sqrtf(a2 + (1.f - a2) * ni * ni);
+    const float Lo = no + so, Lm = ni + si;
+    const float Vis = 1.f / (Lo * Lm);
+    const float om = 1.f - vh, om2 = om * om, w5 = om2 * om2 * om;
+    float F0[3], Fr[3], fs[3], fd[3], Lc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        F0[c] = 0.04f * (1.f - mb) + bb[c] * mb;
+        Fr[c] = F0[c] + (1.f - F0[c]) * w5;
+        fs[c] = D * Fr[c] * Vis;
+        fd[c] = (1.f - mb) * bb[c] * (1.f / kPi);
+        Lc[c] = sb * Ls[c] + (1.f - sb) * (fs[c] + fd[c]) * Li * ni;
+        out[c] = A * Lc[c];
+    }
+    if (!BWD) return;
+
+    float dg[SSSGS_NF];
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) dg[k] = 0.f;
+    float dA = 0.f, dni = 0.f, dD = 0.f, dVis = 0.f, dw5 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float gL = g3[c] * A;
+        dA += g3[c] * Lc[c];
+        const float fsd = fs[c] + fd[c];
+        dg[9] += gL * (Ls[c] - fsd * Li * ni);
+        dg[10 + c] += gL * sb;
+        dg[13] += gL * (1.f - sb) * fsd * ni;
+        dni += gL * (1.f - sb) * fsd * Li;
+        const float cm = gL * (1.f - sb) * Li * ni;
+        dg[8] -= cm * bb[c] * (1.f / kPi);
+        dg[4 + c] += cm * (1.f - mb) * (1.f / kPi);
+        dD += cm * Fr[c] * Vis;
+        dVis += cm * D * Fr[c];
+        const float dFr = cm * D * Vis;
+        const float dF0 = dFr * (1.f - w5);
+        dw5 += dFr * (1.f - F0[c]);
+        dg[8] += dF0 * (bb[c] - 0.04f);
+        dg[4 + c] += dF0 * mb;
+    }
+    const float dvh = -5.f * om2 * om2 * dw5;
+    const float dLo = -dVis * Vis / Lo, dLm = -dVis * Vis / Lm;
+    const float dno = dLo * (1.f + (1.f - a2) * no / so);
+    float da2 = dLo * (1.f - no * no) / (2.f * so) + dLm * (1.f - ni * ni) / (2.f * si);
+    dni += dLm * (1.f + (1.f - a2) * ni / si);
+    const float iden3 = 1.f / (kPi * den * den * den);
+    da2 += dD * (den - 2.f * a2 * nhc * nhc) * iden3;
+    const float dnh = dD * (-4.f * a2 * nhc * (a2 - 1.f)) * iden3;
+    dg[7] += da2 * 4.f * rb * rb * rb;
+    const float dco = co > 0.f ? dno : 0.f, dci = ci > 0.f ? dni : 0.f;
+    const float dch = ch > 0.f ? dnh : 0.f, dcv = cv > 0.f ? dvh : 0.f;
+    float3 dn = dco * wo + dci * wi + dch * h;
+    float3 dwo = dco * nh + dcv * h;
+    float3 dwi = dci * nh;
+    const float3 dh = dch * nh + dcv * wo;
+    const float hd = dot3(h, dh);
+    const float3 dHv = (1.f / lh) * (dh - hd * h);
+    dwo = dwo + dHv;
+    dwi = dwi + dHv;
+    const float3 dVo = (1.f / lo) * (dwo - dot3(wo, dwo) * wo);
+    const float3 dVi = (1.f / li) * (dwi - dot3(wi, dwi) * wi);
+    const float3 dx = make_float3(-dVo.x - dVi.x, -dVo.y - dVi.y, -dVo.z - dVi.z);
+    const float3 dnb = (1.f / nn) * (dn - dot3(nh, dn) * nh);
+    dg[1] += dnb.x; dg[2] += dnb.y; dg[3] += dnb.z;
+    const float3 dXc = make_float3(P.R[0] * dx.x + P.R[1] * dx.y + P.R[2] * dx.z,
+                                   P.R[3] * dx.x + P.R[4] * dx.y + P.R[5] * dx.z,
+                                   P.R[6] * dx.x + P.R[7] * dx.y + P.R[8] * dx.z);
+    dg[0] += dot3(dXc, ray);
+    float dAd = 0.f;
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) {
+        dF[k] = dg[k] * iA;
+        dAd -= dg[k] * g[k] * iA;
+    }
+    if (A > A_eps) dA += dAd;
+    *dT = -dA;
+}
+
+// ---------------------------------------------------------------- helpers
+
+struct TilePix {
+    int i, j;
+    bool inside;
+    int64_t pix;
+};
+
+__device__ __forceinline__ TilePix tile_pixel(const sssgs_pair& P, int tile, int TILE) {
+    TilePix r;
+    int lt = tile - P.tile_offset;
+    int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
+    r.i = tx * TILE + (int)(threadIdx.x % TILE);
+    r.j = ty * TILE + (int)(threadIdx.x / TILE);
+    r.inside = r.i < P.W && r.j < P.H;
+    r.pix = P.pixel_offset + (int64_t)r.j * P.W + r.i;
+    return r;
+}
+
+__device__ __forceinline__ void load_pair_shared(const sssgs_pair* __restrict__ pairs, int n_pairs, int tile,
+                                                 sssgs_pair* sP) {
+    if (threadIdx.x < 32) {
+        int p = pair_of_tile(pairs, n_pairs, tile);
+        reinterpret_cast<float4*>(sP)[threadIdx.x & 7] = reinterpret_cast<const float4*>(pairs + p)[threadIdx.x & 7];
+    }
+    __syncthreads();
+}
+
+// Sum v[0..31] over the warp; afterwards lane k returns the sum of component k.
+__device__ __forceinline__ float warp_transpose_sum(float* v, int lane) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            float send = up ? v[i] : v[i + off];
+            float keep = up ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(SSSGS_FULL, send, off);
+        }
+    }
+    return v[0];
+}
+
+// ---------------------------------------------------------------- composite forward
+
+template <int TILE, bool SHADE>
+__global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+                                                               int n_pairs, const float4* __restrict__ rec,
+                                                               const uint32_t* __restrict__ vals,
+                                                               const uint2* __restrict__ ranges,
+                                                               float* __restrict__ gbuf, uint32_t* __restrict__ last,
+                                                               float* __restrict__ img) {
+    constexpr int B = TILE * TILE;
+    extern __shared__ float4 s_rec[];            // [6][B]
+    __shared__ __align__(16) sssgs_pair sP;
+    const int tile = blockIdx.x;
+    load_pair_shared(pairs, n_pairs, tile, &sP);
+    const TilePix px = tile_pixel(sP, tile, TILE);
+    const float fx = px.i + 0.5f, fy = px.j + 0.5f;
+    const uint2 rg = ranges[tile];
+    const float a_min = cfg.alpha_min, a_max = cfg.alpha_max, T_min = cfg.T_min;
+    bool done = !px.inside;
+    float T = 1.f;
+    float F[SSSGS_NF];
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) F[k] = 0.f;
+    uint32_t lastc = 0;
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += B) {
+        if (__syncthreads_count(done) == B) break;
+        const uint32_t idx = b0 + threadIdx.x;
+        if (idx < rg.y) {
+            const float4* r = rec + 6 * (int64_t)vals[idx];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
+        }
+        __syncthreads();
+        const int nb = min(B, (int)(rg.y - b0));
+        if (__any_sync(SSSGS_FULL, !done) && !done) {
+            for (int k = 0; k < nb; ++k) {
+                const float4 g0 = s_rec[k], g1 = s_rec[B + k];
+                const AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
+                if (!e.use) continue;
+                const float Tn = T * (1.f - e.alpha);
+                if (Tn < T_min) { done = true; break; }
+                const float w = T * e.alpha;
+                const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
+                const float g5 = s_rec[5 * B + k].x;
+                F[0] += w * g1.z;  F[1] += w * g1.w;  F[2] += w * g2.x;  F[3] += w * g2.y;
+                F[4] += w * g2.z;  F[5] += w * g2.w;  F[6] += w * g3.x;  F[7] += w * g3.y;
+                F[8] += w * g3.z;  F[9] += w * g3.w;  F[10] += w * g4.x; F[11] += w * g4.y;
+                F[12] += w * g4.z; F[13] += w * g4.w; F[14] += w * g5;
+                T = Tn;
+                lastc = b0 + k + 1;
+            }
+        }
+    }
+    if (!px.inside) return;
+    float4* go = reinterpret_cast<float4*>(gbuf + SSSGS_GBUF * px.pix);
+    go[0] = make_float4(F[0], F[1], F[2], F[3]);
+    go[1] = make_float4(F[4], F[5], F[6], F[7]);
+    go[2] = make_float4(F[8], F[9], F[10], F[11]);
+    go[3] = make_float4(F[12], F[13], F[14], T);
+    last[px.pix] = lastc;
+    if (SHADE) {
+        float o[3];
+        shade_px<false>(F, T, fx, fy, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
+        img[3 * px.pix] = o[0];
+        img[3 * px.pix + 1] = o[1];
+        img[3 * px.pix + 2] = o[2];
+    }
+}
+
+// ---------------------------------------------------------------- shade only
+
+template <int TILE, bool BWD>
+__global__ void __launch_bounds__(TILE * TILE) k_shade(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                                       const float* __restrict__ gbuf, float* __restrict__ img,
+                                                       const float* __restrict__ dimg, float* __restrict__ dgbuf) {
+    __shared__ __align__(16) sssgs_pair sP;
+    const int tile = blockIdx.x;
+    load_pair_shared(pairs, n_pairs, tile, &sP);
+    const TilePix px = tile_pixel(sP, tile, TILE);
+    if (!px.inside) return;
+    const float4* gi = reinterpret_cast<const float4*>(gbuf + SSSGS_GBUF * px.pix);
+    float F[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float4 v = gi[q];
+        F[4 * q] = v.x; F[4 * q + 1] = v.y; F[4 * q + 2] = v.z; F[4 * q + 3] = v.w;
+    }
+    float o[3];
+    if (!BWD) {
+        shade_px<false>(F, F[15], px.i + 0.5f, px.j + 0.5f, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
+        img[3 * px.pix] = o[0];
+        img[3 * px.pix + 1] = o[1];
+        img[3 * px.pix + 2] = o[2];
+    } else {
+        float g3[3] = {dimg[3 * px.pix], dimg[3 * px.pix + 1], dimg[3 * px.pix + 2]};
+        float dF[SSSGS_NF], dT;
+        shade_px<true>(F, F[15], px.i + 0.5f, px.j + 0.5f, sP, cfg.A_eps, o, g3, dF, &dT);
+        float4* go = reinterpret_cast<float4*>(dgbuf + SSSGS_GBUF * px.pix);
+        go[0] = make_float4(dF[0], dF[1], dF[2], dF[3]);
+        go[1] = make_float4(dF[4], dF[5], dF[6], dF[7]);
+        go[2] = make_float4(dF[8], dF[9], dF[10], dF[11]);
+        go[3] = make_float4(dF[12], dF[13], dF[14], dT);
+    }
+}
+
+// ---------------------------------------------------------------- composite backward
+
+enum { UPSTREAM_DGBUF = 0, UPSTREAM_DIMG = 1, UPSTREAM_L1 = 2 };
+
+template <int TILE, int MODE>
+__global__ void __launch_bounds__(TILE * TILE) k_composite_bwd(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+                                                               int n_pairs, const float4* __restrict__ rec,
+                                                               const uint32_t* __restrict__ vals,
+                                                               const uint2* __restrict__ ranges,
+                                                               const float* __restrict__ gbuf,
+                                                               const uint32_t* __restrict__ last,
+                                                               const float* __restrict__ dgbuf,
+                                                               const float* __restrict__ img,
+                                                               const float* __restrict__ dimg,
+                                                               const float* __restrict__ target,
+                                                               const float* __restrict__ weight, float l1_scale,
+                                                               float* __restrict__ drec) {
+    constexpr int B = TILE * TILE;
+    extern __shared__ float4 s_rec[];                       // [6][B] then item ids
+    uint32_t* s_item = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
+    __shared__ __align__(16) sssgs_pair sP;
+    __shared__ uint32_t s_max;
+    const int tile = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_max = 0;
+    load_pair_shared(pairs, n_pairs, tile, &sP);
+    const TilePix px = tile_pixel(sP, tile, TILE);
+    const float fx = px.i + 0.5f, fy = px.j + 0.5f;
+    const uint2 rg = ranges[tile];
+    float dF[SSSGS_NF];
+    float dT = 0.f, T = 1.f;
+    uint32_t lastc = 0;
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) dF[k] = 0.f;
+    if (px.inside) {
+        lastc = last[px.pix];
+        const float4* gi = reinterpret_cast<const float4*>(gbuf + SSSGS_GBUF * px.pix);
+        float F[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 v = gi[q];
+            F[4 * q] = v.x; F[4 * q + 1] = v.y; F[4 * q + 2] = v.z; F[4 * q + 3] = v.w;
+        }
+        T = F[15];
+        if (MODE == UPSTREAM_DGBUF) {
+            const float4* di = reinterpret_cast<const float4*>(dgbuf + SSSGS_GBUF * px.pix);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 v = di[q];
+                float t4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (4 * q + c < SSSGS_NF) dF[4 * q + c] = t4[c]; else dT = t4[c];
+                }
+            }
+        } else {
+            float g3[3], o[3];
+            if (MODE == UPSTREAM_DIMG) {
+                g3[0] = dimg[3 * px.pix]; g3[1] = dimg[3 * px.pix + 1]; g3[2] = dimg[3 * px.pix + 2];
+            } else {
+                const float wgt = l1_scale * (weight ? weight[px.pix] : 1.f);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float d = img[3 * px.pix + c] - target[3 * px.pix + c];
+                    g3[c] = d > 0.f ? wgt : (d < 0.f ? -wgt : 0.f);
+                }
+            }
+            shade_px<true>(F, T, fx, fy, sP, cfg.A_eps, o, g3, dF, &dT);
+        }
+        if (lastc > 0) atomicMax(&s_max, lastc);
+    }
+    __syncthreads();
+    const uint32_t maxlast = s_max;
+    const float dTT = dT * T;        // dLoss/dT_final * T_final
+    float Q = 0.f;                   // sum_k dF_k * (suffix sum of w_j f_jk)
+    const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
+    for (uint32_t b1 = maxlast; b1 > rg.x;) {
+        const uint32_t b0 = b1 - rg.x > (uint32_t)B ? b1 - B : rg.x;
+        __syncthreads();
+        const uint32_t idx = b0 + threadIdx.x;
+        if (idx < b1) {
+            const uint32_t item = vals[idx];
+            s_item[threadIdx.x] = item;
+            const float4* r = rec + 6 * (int64_t)item;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
+        }
+        __syncthreads();
+        if (__any_sync(SSSGS_FULL, lastc > b0)) {
+            for (int k = (int)(b1 - b0) - 1; k >= 0; --k) {
+                const uint32_t pos = b0 + k;
+                const float4 g0 = s_rec[k], g1 = s_rec[B + k];
+                AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
+                const bool act = (pos < lastc) && e.use;
+                if (!__any_sync(SSSGS_FULL, act)) continue;
+                float gr[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) gr[c] = 0.f;
+                if (act) {
+                    const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
+                    const float g5 = s_rec[5 * B + k].x;
+                    const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
+                                               g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
+                    const float ia = 1.f / (1.f - e.alpha);
+                    const float Ti = T * ia;
+                    const float w = e.alpha * Ti;
+                    float dot = 0.f;
+#pragma unroll
+                    for (int c = 0; c < SSSGS_NF; ++c) {
+                        dot += dF[c] * f[c];
+                        gr[6 + c] = w * dF[c];
+                    }
+                    const float da = Ti * dot - (Q + dTT) * ia;
+                    Q += w * dot;
+                    if (!e.clamped) {
+                        const float dp = -da * e.alpha;
+                        gr[5] = da * e.G;
+                        gr[0] = dp * (g0.z * e.dx + g0.w * e.dy);
+                        gr[1] = dp * (g0.w * e.dx + g1.x * e.dy);
+                        gr[2] = dp * 0.5f * e.dx * e.dx;
+                        gr[3] = dp * e.dx * e.dy;
+                        gr[4] = dp * 0.5f * e.dy * e.dy;
+                    }
+                    T = Ti;
+                }
+                const float s = warp_transpose_sum(gr, lane);
+                if (lane < 6 + SSSGS_NF) atomicAdd(drec + (int64_t)SSSGS_REC * s_item[k] + lane, s);
+            }
+        }
+        b1 = b0;
+    }
+}
+
+template <int TILE>
+static size_t fwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4); }
+template <int TILE>
+static size_t bwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4; }
+
+}  // namespace sssgs
+
+using namespace sssgs;
+
+namespace {
+bool args_ok(const sssgs_cfg* cfg, const sssgs_pair* h, const sssgs_pair* d, int n) {
+    return cfg && h && d && n > 0 && (cfg->tile == 8 || cfg->tile == 16 || cfg->tile == 32) && cfg->reserved == 0;
+}
+int tiles_of(const sssgs_pair* h, int n) { return h[n - 1].tile_offset + h[n - 1].tiles_x * h[n - 1].tiles_y; }
+bool a16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+template <int TILE, bool SHADE>
+int launch_fwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
+               const uint32_t* ranges, float* gbuf, uint32_t* last, float* img, cudaStream_t st) {
+    size_t sm = fwd_smem<TILE>();
+    cudaFuncSetAttribute(k_composite_fwd<TILE, SHADE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_composite_fwd<TILE, SHADE><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
+                                                                 (const uint2*)ranges, gbuf, last, img);
+    sssgs::note_launches(1);
+    return launch_status();
+}
+
+template <int TILE, int MODE>
+int launch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
+               const uint32_t* ranges, const float* gbuf, const uint32_t* last, const float* dgbuf,
+               const float* img, const float* dimg, const float* target, const float* weight, float l1,
+               float* drec, cudaStream_t st) {
+    size_t sm = bwd_smem<TILE>();
+    cudaFuncSetAttribute(k_composite_bwd<TILE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_composite_bwd<TILE, MODE><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
+                                                                (const uint2*)ranges, gbuf, last, dgbuf, img, dimg,
+                                                                target, weight, l1, drec);
+    sssgs::note_launches(1);
+    return launch_status();
+}
+
+template <int MODE>
+int dispatch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
+                 const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
+                 const float* dgbuf, const float* img, const float* dimg, const float* target,
+                 const float* weight, float l1, float* drec, cudaStream_t st) {
+    switch (cfg->tile) {
+        case 8: return launch_bwd<8, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
+                                           target, weight, l1, drec, st);
+        case 16: return launch_bwd<16, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
+                                             target, weight, l1, drec, st);
+        default: return SSSGS_ERR_UNSUPPORTED;   // 32x32 tiles: forward only
+    }
+}
+}  // namespace
+
+extern "C" int sssgs_composite_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                                   int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                                   float* gbuf, uint32_t* last, sssgs_stream stream) {
+    if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last) return SSSGS_ERR_INVALID_ARG;
+    if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
+    int tiles = tiles_of(h_pairs, n_pairs);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (cfg->tile) {
+        case 8: return launch_fwd<8, false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
+        case 16: return launch_fwd<16, false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
+        default: return launch_fwd<32, false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
+    }
+}
+
+extern "C" int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                                int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                                float* gbuf, uint32_t* last, float* img, sssgs_stream stream) {
+    if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last || !img)
+        return SSSGS_ERR_INVALID_ARG;
+    if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
+    int tiles = tiles_of(h_pairs, n_pairs);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (cfg->tile) {
+        case 8: return launch_fwd<8, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st);
+        case 16: return launch_fwd<16, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st);
+        default: return launch_fwd<32, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st);
+    }
+}
+
+extern "C" int sssgs_shade_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                               int n_pairs, const float* gbuf, float* img, sssgs_stream stream) {
+    if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !gbuf || !img) return SSSGS_ERR_INVALID_ARG;
+    if (!a16(gbuf) || !a16(d_pairs)) return SSSGS_ERR_INVALID_ARG;
+    int tiles = tiles_of(h_pairs, n_pairs);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (cfg->tile) {
+        case 8: k_shade<8, false><<<tiles, 64, 0, st>>>(*cfg, d_pairs, n_pairs, gbuf, img, nullptr, nullptr); sssgs::note_launches(1); break;
+        case 16: k_shade<16, false><<<tiles, 256, 0, st>>>(*cfg, d_pairs, n_pairs, gbuf, img, nullptr, nullptr); sssgs::note_launches(1); break;
+        default: k_shade<32, false><<<tiles, 1024, 0, st>>>(*cfg, d_pairs, n_pairs, gbuf, img, nullptr, nullptr); sssgs::note_launches(1); break;
+    }
+    return launch_status();
+}
+
+extern "C" int sssgs_shade_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                               int n_pairs, const float* gbuf, const float* dimg, float* dgbuf, sssgs_stream stream) {
+    if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !gbuf || !dimg || !dgbuf) return SSSGS_ERR_INVALID_ARG;
+    if (!a16(gbuf) || !a16(dgbuf) || !a16(d_pairs)) return SSSGS_ERR_INVALID_ARG;
+    int tiles = tiles_of(h_pairs, n_pairs);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (cfg->tile) {
+        case 8: k_shade<8, true><<<tiles, 64, 0, st>>>(*cfg, d_pairs, n_pairs, gbuf, nullptr, dimg, dgbuf); sssgs::note_launches(1); break;
+        case 16: k_shade<16, true><<<tiles, 256, 0, st>>>(*cfg, d_pairs, n_pairs, gbuf, nullptr, dimg, dgbuf); sssgs::note_launches(1); break;
+        default: return SSSGS_ERR_UNSUPPORTED;
+    }
+    return launch_status();
+}
+
+extern "C" int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                                   int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                                   const float* gbuf, const uint32_t* last, const float* dgbuf, float* drec,
+                                   sssgs_stream stream) {
+    if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last || !dgbuf || !drec)
+        return SSSGS_ERR_INVALID_ARG;
+    if (!a16(rec) || !a16(gbuf) || !a16(dgbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
+    return dispatch_bwd<UPSTREAM_DGBUF>(cfg, d_pairs, n_pairs, tiles_of(h_pairs, n_pairs), rec, vals, ranges, gbuf,
+                                        last, dgbuf, nullptr, nullptr, nullptr, nullptr, 0.f, drec,
+                                        (cudaStream_t)stream);
+}
+
+extern "C" int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                                int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                                const float* gbuf, const uint32_t* last, const float* img, const float* dimg,
+                                const float* target, const float* weight, float l1_scale, float* drec,
+                                sssgs_stream stream) {
+    if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last || !drec)
+        return SSSGS_ERR_INVALID_ARG;
+    if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
+    int tiles = tiles_of(h_pairs, n_pairs);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dimg)
+        return dispatch_bwd<UPSTREAM_DIMG>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr,
+                                           nullptr, dimg, nullptr, nullptr, 0.f, drec, st);
+    if (!img || !target) return SSSGS_ERR_INVALID_ARG;
+    return dispatch_bwd<UPSTREAM_L1>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, img,
+                                     nullptr, target, weight, l1_scale, drec, st);
+}

@@ -1,0 +1,241 @@
+"""Device buffers, the per-step call sequence and the torch.autograd.Function.
+
+One step (Fig. 2 of the paper, forward and backward) is the sequence
+    mlp_fwd -> project_fwd -> bin_sort -> render_fwd            (forward)
+    render_bwd -> mlp_bwd -> project_bwd                        (backward)
+of C-ABI calls on one CUDA stream. PyTorch only owns the memory.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+SCENE_KEYS = ("mu", "log_s", "quat", "logit_o", "normal", "base", "rough", "metal", "sss", "vis")
+
+
+def default_cfg(tile: int = 16) -> B.Cfg:
+    c = B.cfg_default()
+    c.tile = tile
+    return c
+
+
+class PairTable:
+    """Host + device copies of a planned batch of view/light pairs."""
+
+    def __init__(self, pairs, cfg: B.Cfg, scene_offsets=None, scene_counts=None, device="cuda"):
+        n = len(pairs)
+        self.h = (B.Pair * n)()
+        for k, p in enumerate(pairs):
+            q = self.h[k]
+            R = np.asarray(p.R, np.float32).ravel()
+            for i in range(9):
+                q.R[i] = float(R[i])
+            for i in range(3):
+                q.t[i] = float(np.float32(p.t[i]))
+                q.light[i] = float(np.float32(p.light[i]))
+            q.fx, q.fy, q.cx, q.cy = float(p.fx), float(p.fy), float(p.cx), float(p.cy)
+            q.W, q.H = int(p.W), int(p.H)
+            s = getattr(p, "scene", 0)
+            q.g_begin = int(scene_offsets[s]) if scene_offsets is not None else 0
+            q.g_count = int(scene_counts[s]) if scene_counts is not None else 0
+        self.info = B.plan(self.h, cfg)
+        raw = np.frombuffer(bytes(self.h), dtype=np.uint8).copy()
+        self.d = torch.from_numpy(raw).to(device)
+        self.n = n
+
+    @property
+    def n_items(self):
+        return int(self.info.n_items)
+
+    @property
+    def n_pixels(self):
+        return int(self.info.n_pixels)
+
+    @property
+    def n_tiles(self):
+        return int(self.info.n_tiles)
+
+
+@dataclass
+class MLPParams:
+    kind: int
+    precision: int
+    W: list
+    b: list
+
+    def struct(self):
+        return B.mlp_struct(self.kind, self.precision, self.W, self.b)
+
+
+class Renderer:
+    """Owns every buffer of a batch and runs the forward/backward call sequence."""
+
+    def __init__(self, scene: dict, mlp: MLPParams, table: PairTable, cfg: B.Cfg, capacity: int | None = None,
+                 fused: bool = True, device="cuda"):
+        self.scene = scene
+        self.mlp = mlp
+        self.table = table
+        self.cfg = cfg
+        self.fused = fused
+        self.device = device
+        n, P, T = table.n_items, table.n_pixels, table.n_tiles
+        f32 = dict(device=device, dtype=torch.float32)
+        i32 = dict(device=device, dtype=torch.int32)
+        self.mlp_out = torch.zeros(n, 4, **f32)
+        self.rec = torch.zeros(n, B.REC, **f32)
+        self.rect = torch.zeros(n, 4, **i32)
+        self.ranges = torch.zeros(T, 2, **i32)
+        self.count = torch.zeros(1, device=device, dtype=torch.int64)
+        self.status = torch.zeros(1, **i32)
+        self.gbuf = torch.zeros(P, B.GBUF, **f32)
+        self.last = torch.zeros(P, **i32)
+        self.img = torch.zeros(P, 3, **f32)
+        self.dgbuf = None if fused else torch.zeros(P, B.GBUF, **f32)
+        self.drec = torch.zeros(n, B.REC, **f32)
+        self.dx_items = torch.zeros(n, 7, **f32)
+        self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
+        self.dW = [torch.zeros_like(w) for w in mlp.W]
+        self.db = [torch.zeros_like(b) for b in mlp.b]
+        self._scene_s = B.scene_struct(scene)
+        self._grad_s = B.scene_grad_struct(self.grads)
+        self._mlp_s = mlp.struct()
+        self._mlp_g = B.mlp_grad_struct(self.dW, self.db)
+        mws = B.mlp_workspace_bytes(self._mlp_s, n) if mlp.precision == B.FP32 else 256
+        self.ws_mlp = torch.empty(max(mws, 256), device=device, dtype=torch.uint8)
+        self.capacity = 0
+        self.set_capacity(capacity if capacity is not None else max(1024, 16 * n))
+
+    # ------------------------------------------------------------------ setup
+    def set_capacity(self, cap: int):
+        cap = int(cap)
+        self.capacity = cap
+        self.vals = torch.zeros(max(cap, 1), device=self.device, dtype=torch.int32)
+        wsb = B.bin_workspace_bytes(self.table.n_items, cap, self.table.n_tiles)
+        self.ws_bin = torch.empty(max(wsb, 256), device=self.device, dtype=torch.uint8)
+
+    def fit_capacity(self, slack: float = 1.15):
+        """Run the front end once and size the instance buffers (syncs)."""
+        self.forward_front()
+        torch.cuda.synchronize()
+        need = int(self.count.item())
+        if need > self.capacity or self.status.item() != 0:
+            self.set_capacity(int(need * slack) + 1024)
+            self.status.zero_()
+            self.forward_front()
+            torch.cuda.synchronize()
+        return need
+
+    # ------------------------------------------------------------------ steps
+    def forward_front(self, stream=None):
+        t = self.table
+        B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, stream)
+        B.project_fwd(self.cfg, t.h, t.d, self._scene_s, self.mlp_out, self.rec, self.rect, stream)
+        B.bin_sort(self.cfg, t.h, t.d, self.rec, self.rect, self.capacity, self.vals, self.ranges, self.count,
+                   self.status, self.ws_bin, stream)
+
+    def forward(self, stream=None):
+        self.forward_front(stream)
+        t = self.table
+        if self.fused:
+            B.render_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img, stream)
+        else:
+            B.composite_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, stream)
+            B.shade_fwd(self.cfg, t.h, t.d, self.gbuf, self.img, stream)
+        return self.img
+
+    def zero_grads(self):
+        self.drec.zero_()
+        self.dx_items.zero_()
+        for g in self.grads.values():
+            g.zero_()
+        for g in self.dW + self.db:
+            g.zero_()
+
+    def backward(self, dimg=None, target=None, weight=None, l1_scale=1.0, stream=None):
+        t = self.table
+        self.zero_grads()
+        if self.fused:
+            B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
+                         dimg, target, weight, l1_scale, self.drec, stream)
+        else:
+            if dimg is None:
+                raise ValueError("the unfused path takes dimg")
+            B.shade_bwd(self.cfg, t.h, t.d, self.gbuf, dimg, self.dgbuf, stream)
+            B.composite_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.dgbuf,
+                            self.drec, stream)
+        B.mlp_bwd(self._mlp_s, t.h, t.d, self._scene_s, self.drec, self._mlp_g, self.dx_items, self.ws_mlp, stream)
+        B.project_bwd(self.cfg, t.h, t.d, self._scene_s, self.drec, self.dx_items, self._grad_s, stream)
+
+    def check_status(self):
+        s = int(self.status.item())
+        if s & B.STATUS_CAPACITY:
+            raise B.SSSGSError(f"instance capacity {self.capacity} exceeded ({int(self.count.item())} needed)")
+
+
+class SSSRenderFunction(torch.autograd.Function):
+    """Differentiable OLAT render: (scene params, MLP weights) -> image (pixels x 3)."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, *params):
+        renderer.forward()
+        ctx.renderer = renderer
+        return renderer.img.clone()
+
+    @staticmethod
+    def backward(ctx, dimg):
+        r = ctx.renderer
+        r.backward(dimg=dimg.contiguous())
+        return (None, *[r.grads[k] for k in SCENE_KEYS], *r.dW, *r.db)
+
+
+def render(renderer: Renderer):
+    params = [renderer.scene[k] for k in SCENE_KEYS] + list(renderer.mlp.W) + list(renderer.mlp.b)
+    return SSSRenderFunction.apply(renderer, *params)
+
+
+# ---------------------------------------------------------------------- helpers
+
+def scene_to_device(scene, device="cuda") -> dict:
+    """scenegen.Scene -> dict of contiguous float32 device tensors."""
+    out = {}
+    for k in SCENE_KEYS:
+        a = np.ascontiguousarray(getattr(scene, k), dtype=np.float32)
+        out[k] = torch.from_numpy(a).to(device).requires_grad_(False)
+    return out
+
+
+def concat_scenes(scenes, device="cuda"):
+    """Concatenate several scenegen.Scene objects; returns (dict, offsets, counts)."""
+    offs, counts, acc = [], [], 0
+    for s in scenes:
+        offs.append(acc)
+        counts.append(s.N)
+        acc += s.N
+    out = {}
+    for k in SCENE_KEYS:
+        a = np.concatenate([np.asarray(getattr(s, k), np.float32) for s in scenes], axis=0)
+        out[k] = torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    return out, offs, counts
+
+
+def mlp_to_device(spec, precision=None, device="cuda") -> MLPParams:
+    kind = B.MLP_BASIC if spec.kind == "basic" else B.MLP_PE6
+    prec = precision if precision is not None else (B.BF16 if spec.precision == "bf16" else B.FP32)
+    W = [torch.from_numpy(np.ascontiguousarray(w, np.float32)).to(device) for w in spec.weights]
+    b = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(device) for x in spec.biases]
+    return MLPParams(kind, prec, W, b)
+
+
+def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=None, device="cuda",
+                          pair_slice=None) -> Renderer:
+    cfg = default_cfg(tile or wl.tile)
+    scene, offs, counts = concat_scenes(wl.scenes, device)
+    pairs = wl.pairs if pair_slice is None else wl.pairs[pair_slice]
+    table = PairTable(pairs, cfg, offs, counts, device)
+    mlp = mlp_to_device(wl.mlp, precision, device)
+    return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device)

@@ -1,0 +1,118 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the FP64 oracle on the same seeded inputs, and compare.
+
+Tolerances (written here, used by every parity test):
+  image / G-buffer   |gpu - ref| <= 1e-4 * max(1, |ref|) on pixels whose
+                     decisions are not within float32 reach of a threshold
+  gradients          per tensor ||g - r||_2 <= 1e-3 ||r||_2 and
+                     max |g - r| <= 1e-3 max |r|
+A pixel is "flagged" when the oracle reports an alpha decision within 2e-4
+(relative) of alpha_min/alpha_max or a stop decision within 5e-4 of T_min:
+float32 rounding of the conic, mean and exp can move such a decision, which
+changes the pixel by a finite jump. Flagged pixels are excluded from the image
+gate and get zero upstream gradient in the gradient tests (both sides).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle as O
+from paper_2408_12282_gb300 import binding as B
+from paper_2408_12282_gb300 import pipeline as PL
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+FLAG_ALPHA = 2e-4
+FLAG_T = 5e-4
+
+
+def run_gpu(wl, precision=B.FP32, fused=True, tile=None, dimg=None, target=None, l1_scale=1.0,
+            weight=None, pair_slice=None, capacity=None, backward=True):
+    r = PL.renderer_for_workload(wl, precision=precision, fused=fused, tile=tile, pair_slice=pair_slice,
+                                 capacity=capacity)
+    r.fit_capacity()
+    r.forward()
+    out = {}
+    if backward:
+        d = torch.from_numpy(np.ascontiguousarray(dimg, np.float32)).cuda() if dimg is not None else None
+        t = torch.from_numpy(np.ascontiguousarray(target, np.float32)).cuda() if target is not None else None
+        w = torch.from_numpy(np.ascontiguousarray(weight, np.float32)).cuda() if weight is not None else None
+        r.backward(dimg=d, target=t, weight=w, l1_scale=l1_scale)
+    torch.cuda.synchronize()
+    r.check_status()
+    out["img"] = r.img.double().cpu().numpy()
+    out["gbuf"] = r.gbuf.double().cpu().numpy()
+    out["last"] = r.last.cpu().numpy()
+    out["mlp_out"] = r.mlp_out.double().cpu().numpy()
+    out["rec"] = r.rec.double().cpu().numpy()
+    out["rect"] = r.rect.cpu().numpy()
+    out["count"] = int(r.count.item())
+    out["renderer"] = r
+    if backward:
+        out["grads"] = {k: v.double().cpu().numpy() for k, v in r.grads.items()}
+        out["dW"] = [w.double().cpu().numpy() for w in r.dW]
+        out["db"] = [b.double().cpu().numpy() for b in r.db]
+    return out
+
+
+def oracle_batch(wl, pair_ids, dimg=None, bf16=False):
+    """Oracle over several pairs of one-scene workload; dimg is pair-major."""
+    imgs, gbufs, margins, ncs = [], [], [], []
+    grads = None
+    dW = db = None
+    off = 0
+    for p in pair_ids:
+        pair = wl.pairs[p]
+        npx = pair.W * pair.H
+        di = dimg[off:off + npx] if dimg is not None else None
+        r = O.render_pair(wl.scenes[pair.scene], pair, wl.mlp, O.Cfg(tile=wl.tile), dimg=di, bf16=bf16)
+        imgs.append(r["img"]); gbufs.append(r["gbuf"]); margins.append(r["margin"]); ncs.append(r["ncontrib"])
+        if di is not None:
+            if grads is None:
+                grads = {k: v.copy() for k, v in r["grads"].items()}
+                dW = [w.copy() for w in r["dW"]]
+                db = [b.copy() for b in r["db"]]
+            else:
+                for k in grads:
+                    grads[k] += r["grads"][k]
+                for l in range(len(dW)):
+                    dW[l] += r["dW"][l]
+                    db[l] += r["db"][l]
+        off += npx
+    out = dict(img=np.concatenate(imgs), gbuf=np.concatenate(gbufs), margin=np.concatenate(margins),
+               ncontrib=np.concatenate(ncs))
+    if dimg is not None:
+        out.update(grads=grads, dW=dW, db=db)
+    return out
+
+
+def flagged(margin):
+    return (margin[:, 0] < FLAG_ALPHA) | (margin[:, 1] < FLAG_T)
+
+
+def assert_image_close(gpu, ref, flags, tol=IMG_TOL, what="image"):
+    ok = ~flags
+    err = np.abs(gpu[ok] - ref[ok]) / np.maximum(1.0, np.abs(ref[ok]))
+    worst = float(err.max()) if err.size else 0.0
+    assert worst <= tol, f"{what}: max scaled error {worst:.3e} > {tol} ({int(flags.sum())} flagged pixels excluded)"
+    return worst
+
+
+def grad_errors(g, r):
+    g = np.asarray(g, np.float64).ravel()
+    r = np.asarray(r, np.float64).ravel()
+    nr = np.linalg.norm(r)
+    rel = np.linalg.norm(g - r) / nr if nr > 0 else np.linalg.norm(g)
+    mx = np.abs(g - r).max() / max(np.abs(r).max(), 1e-30) if r.size else 0.0
+    return float(rel), float(mx)
+
+
+def assert_grads_close(gpu_grads, ref_grads, keys, tol=GRAD_TOL):
+    report = {}
+    for k in keys:
+        rel, mx = grad_errors(gpu_grads[k], ref_grads[k])
+        report[k] = (rel, mx)
+    bad = {k: v for k, v in report.items() if v[0] > tol or v[1] > tol}
+    assert not bad, f"gradient mismatch (rel L2, max rel): {bad}"
+    return report

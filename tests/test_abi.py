@@ -1,0 +1,92 @@
+"""The C-ABI library loads and exports every entry point include/sssgs.h
+declares; host-only entry points behave (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2408_12282_gb300 import binding as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sssgs.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sssgs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = B.load_library()
+    names = _declared()
+    assert len(names) >= 17
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding covers every one of them under the same name
+    assert set(names) <= set(B.EXPORTED), set(names) - set(B.EXPORTED)
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(B.Pair) == 128
+    assert ctypes.sizeof(B.Cfg) == 36
+    assert ctypes.sizeof(B.MLP) == 4 * 3 + 4 * 9 + 8 * 16
+    assert B.Pair.pixel_offset.offset == 112 and B.Pair.item_offset.offset == 120
+
+
+def test_defaults_and_strerror():
+    c = B.cfg_default()
+    assert c.tile == 16 and c.reserved == 0
+    assert c.alpha_min == pytest.approx(np.float32(1 / 255))
+    assert c.alpha_max == pytest.approx(np.float32(0.99))
+    assert c.T_min == pytest.approx(np.float32(1e-4))
+    assert B.strerror(0) == "ok"
+    assert "invalid" in B.strerror(-1)
+    assert B.version().startswith("sssgs")
+
+
+def test_plan_offsets_and_validation():
+    c = B.cfg_default()
+    sizes = [(800, 800), (400, 400), (1600, 1200), (7, 5)]
+    h = (B.Pair * len(sizes))()
+    for k, (w, hh) in enumerate(sizes):
+        h[k].W, h[k].H, h[k].fx, h[k].fy = w, hh, 100.0, 100.0
+        h[k].g_begin, h[k].g_count = 10 * k, 1000 + k
+    info = B.plan(h, c)
+    tiles = [((w + 15) // 16) * ((hh + 15) // 16) for w, hh in sizes]
+    assert info.n_tiles == sum(tiles)
+    assert info.n_pixels == sum(w * hh for w, hh in sizes)
+    assert info.n_items == sum(1000 + k for k in range(4))
+    assert [h[k].tile_offset for k in range(4)] == list(np.cumsum([0] + tiles[:-1]))
+    assert [h[k].item_offset for k in range(4)] == [0, 1000, 2001, 3003]
+    assert (1 << info.tile_bits) >= info.n_tiles > (1 << (info.tile_bits - 1))
+    h[1].W = 0
+    with pytest.raises(B.SSSGSError):
+        B.plan(h, c)
+    c.tile = 12
+    h[1].W = 400
+    with pytest.raises(B.SSSGSError):
+        B.plan(h, c)
+
+
+def test_workspace_queries():
+    assert B.bin_workspace_bytes(0, 0, 1) > 0
+    a = B.bin_workspace_bytes(1000, 10000, 100)
+    b = B.bin_workspace_bytes(1000, 20000, 100)
+    assert b > a >= 1000 * 32 + 10000 * 12
+
+
+def test_argument_errors_launch_nothing():
+    """Host-side checks reject bad arguments before touching the device."""
+    lib = B.load_library()
+    c = B.cfg_default()
+    h = (B.Pair * 1)()
+    h[0].W = h[0].H = 16
+    h[0].fx = h[0].fy = 10.0
+    B.plan(h, c)
+    assert lib.sssgs_project_fwd(ctypes.byref(c), h, None, 1, None, None, None, None, None) == -1
+    assert lib.sssgs_composite_fwd(ctypes.byref(c), h, None, 1, None, None, None, None, None, None) == -1
+    c.tile = 5
+    assert lib.sssgs_render_fwd(ctypes.byref(c), h, 16, 1, 16, 16, 16, 16, 16, 16, None) == -1
+    assert lib.sssgs_bin_sort(ctypes.byref(c), h, 16, 1, 16, 16, -1, 16, 16, 16, 16, 16, 0, None) == -1
