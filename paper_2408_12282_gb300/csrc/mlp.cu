@@ -51,11 +51,11 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
     const float mm[3] = {m0, m1, m2};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const float f = ldexpf(kPi, k);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+            // sin(2^k pi mu) via sinpi of the exact product 2^k mu: no rounding of pi
             float s, co;
-            sincosf(f * mm[c], &s, &co);
+            sincospif(ldexpf(mm[c], k), &s, &co);
             x[6 * k + c] = s;
             x[6 * k + 3 + c] = co;
         }
@@ -92,7 +92,7 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float s, co;
-                sincosf(f * mm[c], &s, &co);
+                sincospif(ldexpf(mm[c], k), &s, &co);
                 dmu[c] += f * (dX[6 * k + c] * co - dX[6 * k + 3 + c] * s);
             }
         }
