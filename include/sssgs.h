@@ -54,7 +54,8 @@ enum {
     SSSGS_ERR_INVALID_ARG = -1,   /* host-side argument check failed; nothing launched */
     SSSGS_ERR_CUDA = -2,          /* a CUDA launch or API call failed */
     SSSGS_ERR_UNSUPPORTED = -3,   /* configuration not compiled in (tile size, MLP shape) */
-    SSSGS_ERR_WORKSPACE = -4      /* workspace smaller than sssgs_*_workspace_bytes */
+    SSSGS_ERR_WORKSPACE = -4,     /* workspace smaller than sssgs_*_workspace_bytes */
+    SSSGS_ERR_TOO_LARGE = -5      /* problem exceeds the fixed scratch of sssgs_bin_sort_static */
 };
 
 /* Device status bits (written with atomicOr into the caller's int32 word). */
@@ -200,6 +201,28 @@ int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_
                    int n_pairs, const float* rec, const int32_t* rect, int64_t capacity,
                    uint32_t* vals, uint32_t* ranges, int64_t* d_count, int32_t* d_status,
                    void* workspace, size_t workspace_bytes, sssgs_stream stream);
+
+/* Allocation-free sssgs_bin_sort. The paper has no counterpart: this is an
+ * interface for callers that cannot call cudaMalloc -- plug-ins whose host
+ * application owns all device memory, and real-time loops that cannot afford
+ * cudaMalloc's implicit device synchronisation. Same arguments and results as
+ * sssgs_bin_sort, without the workspace: the sort runs in a scratch array of
+ * SSSGS_STATIC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library keeps until the process exits.
+ * Limits: n_items <= SSSGS_STATIC_MAX_ITEMS and capacity <=
+ * SSSGS_STATIC_MAX_INSTANCES; larger problems return SSSGS_ERR_TOO_LARGE
+ * before anything is launched.
+ * The first call on a device (with that device current) looks up the
+ * scratch address; make it before any stream capture. All calls share the
+ * scratch, which keeps the last call's contents (nothing in it needs to start
+ * at zero); calls that overlap on the GPU race, so serialise them. */
+#define SSSGS_STATIC_MAX_ITEMS 65536
+#define SSSGS_STATIC_MAX_INSTANCES 524288
+#define SSSGS_STATIC_SCRATCH_BYTES 8912896
+int sssgs_bin_sort_static(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                          int n_pairs, const float* rec, const int32_t* rect, int64_t capacity,
+                          uint32_t* vals, uint32_t* ranges, int64_t* d_count, int32_t* d_status,
+                          sssgs_stream stream);
 
 /* a3 -- front-to-back compositing (Eq. 3) into gbuf[n_pixels*16] (15 features
  * weighted by w_i = T_i alpha_i, then the final T) and last[n_pixels] (one past

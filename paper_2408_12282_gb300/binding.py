@@ -83,6 +83,8 @@ _SIGS = {
     "sssgs_bin_workspace_bytes": ([c_i64, c_i64, c_i32], ctypes.c_size_t),
     "sssgs_bin_sort": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_i64, c_vp,
                         c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
+    "sssgs_bin_sort_static": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_i64,
+                               c_vp, c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_composite_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
                              c_vp, c_vp], ctypes.c_int),
     "sssgs_shade_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp],
@@ -234,6 +236,20 @@ def bin_sort(cfg: Cfg, pairs, d_pairs, rec, rect, capacity: int, vals, ranges, d
                                          capacity, _p(vals), _p(ranges), _p(d_count), _p(d_status), _p(workspace),
                                          workspace.numel() * workspace.element_size(), _stream(stream)),
            "sssgs_bin_sort")
+
+
+STATIC_MAX_ITEMS = 65536
+STATIC_MAX_INSTANCES = 524288
+ERR_TOO_LARGE = -5
+
+
+def bin_sort_static(cfg: Cfg, pairs, d_pairs, rec, rect, capacity: int, vals, ranges, d_count, d_status,
+                    stream=None):
+    """bin_sort without a workspace: for callers that cannot allocate device
+    memory; runs in the library's fixed scratch (limits above)."""
+    _check(load_library().sssgs_bin_sort_static(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec),
+                                                _p(rect), capacity, _p(vals), _p(ranges), _p(d_count),
+                                                _p(d_status), _stream(stream)), "sssgs_bin_sort_static")
 
 
 def composite_fwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, stream=None):

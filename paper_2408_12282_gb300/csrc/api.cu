@@ -22,6 +22,7 @@ extern "C" const char* sssgs_strerror(int code) {
         case SSSGS_ERR_CUDA: return "CUDA launch or API error";
         case SSSGS_ERR_UNSUPPORTED: return "configuration not supported";
         case SSSGS_ERR_WORKSPACE: return "workspace too small";
+        case SSSGS_ERR_TOO_LARGE: return "problem exceeds the static scratch limits";
         default: return "unknown error";
     }
 }
