@@ -303,7 +303,7 @@ def run_ours(args):
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
         ev[0].record(st)
-        B.mlp_fwd(r._mlp_s, table.h, table.d, r._scene_s, r.mlp_out)
+        B.mlp_fwd(r._mlp_s, table.h, table.d, r._scene_s, r.mlp_out, r.status)
         ev[1].record(st)
         B.project_fwd(r.cfg, table.h, table.d, r._scene_s, r.mlp_out, r.rec, r.rect)
         ev[2].record(st)
@@ -317,7 +317,7 @@ def run_ours(args):
         B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, None, target, None,
                      l1_scale, r.drec)
         ev[5].record(st)
-        B.mlp_bwd(r._mlp_s, table.h, table.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp)
+        B.mlp_bwd(r._mlp_s, table.h, table.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp, r.status)
         ev[6].record(st)
         B.project_bwd(r.cfg, table.h, table.d, r._scene_s, r.drec, r.dx_items, r._grad_s)
         ev[7].record(st)

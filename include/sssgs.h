@@ -60,7 +60,9 @@ enum {
 
 /* Device status bits (written with atomicOr into the caller's int32 word). */
 enum {
-    SSSGS_STATUS_CAPACITY = 1     /* more tile instances than `capacity`; lists truncated */
+    SSSGS_STATUS_CAPACITY = 1,    /* more tile instances than `capacity`; lists truncated */
+    SSSGS_STATUS_TIMEOUT = 2      /* a bounded wait inside a tensor-core kernel ran out (~1 s);
+                                     that kernel stopped early and its outputs are incomplete */
 };
 
 #define SSSGS_NF 15          /* composited features: depth, n3, base3, rough, metal, sss, Lsss3, Lin, vis */
@@ -166,9 +168,12 @@ void sssgs_cfg_default(sssgs_cfg* cfg);
  * Pairs must have W, H in 1..16384 and g_count >= 0. Host only. */
 int sssgs_plan(sssgs_pair* pairs, int n_pairs, const sssgs_cfg* cfg, sssgs_plan_info* info);
 
-/* a0 -- network forward (Eq. 6). out[n_items*4] = (L_SSS rgb, L_in) per item. */
+/* a0 -- network forward (Eq. 6). out[n_items*4] = (L_SSS rgb, L_in) per item
+ * (16-byte aligned). d_status (device int32, may be NULL) receives
+ * SSSGS_STATUS_TIMEOUT if a tensor-core wait ran out. */
 int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
-                  int n_pairs, const sssgs_scene* scene, float* out, sssgs_stream stream);
+                  int n_pairs, const sssgs_scene* scene, float* out, int32_t* d_status,
+                  sssgs_stream stream);
 
 /* a5 -- network backward. Reads dL/d(L_SSS, L_in) from the gradient records
  * drec (fields 16..19) and accumulates weight/bias gradients into grad and
@@ -178,7 +183,7 @@ size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_items);
 int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                   int n_pairs, const sssgs_scene* scene, const float* drec,
                   const sssgs_mlp_grad* grad, float* dx_items,
-                  void* workspace, size_t workspace_bytes, sssgs_stream stream);
+                  void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream);
 
 /* a1 -- EWA projection (Eq. 1, Eq. 2). Per item writes the packed record
  * (rec[n_items*24], features copied from the scene and from mlp_out[n_items*4])

@@ -19,6 +19,7 @@ NF, REC, GBUF = 15, 24, 16
 MLP_BASIC, MLP_PE6 = 0, 1
 FP32, BF16 = 0, 1
 STATUS_CAPACITY = 1
+STATUS_TIMEOUT = 2
 
 
 class SSSGSError(RuntimeError):
@@ -74,10 +75,10 @@ _SIGS = {
     "sssgs_cfg_default": ([ctypes.POINTER(Cfg)], None),
     "sssgs_plan": ([ctypes.POINTER(Pair), ctypes.c_int, ctypes.POINTER(Cfg), ctypes.POINTER(PlanInfo)], ctypes.c_int),
     "sssgs_mlp_fwd": ([ctypes.POINTER(MLP), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp,
-                       c_vp], ctypes.c_int),
+                       c_vp, c_vp], ctypes.c_int),
     "sssgs_mlp_workspace_bytes": ([ctypes.POINTER(MLP), c_i64], ctypes.c_size_t),
     "sssgs_mlp_bwd": ([ctypes.POINTER(MLP), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp,
-                       ctypes.POINTER(MLPGrad), c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
+                       ctypes.POINTER(MLPGrad), c_vp, c_vp, ctypes.c_size_t, c_vp, c_vp], ctypes.c_int),
     "sssgs_project_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
                            c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_bin_workspace_bytes": ([c_i64, c_i64, c_i32], ctypes.c_size_t),
@@ -205,20 +206,21 @@ def mlp_grad_struct(dWs, dbs) -> MLPGrad:
 
 # --------------------------------------------------------------------------- entry points
 
-def mlp_fwd(mlp: MLP, pairs, d_pairs, scene: Scene, out, stream=None):
+def mlp_fwd(mlp: MLP, pairs, d_pairs, scene: Scene, out, d_status=None, stream=None):
     _check(load_library().sssgs_mlp_fwd(ctypes.byref(mlp), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
-                                        _p(out), _stream(stream)), "sssgs_mlp_fwd")
+                                        _p(out), _p(d_status), _stream(stream)), "sssgs_mlp_fwd")
 
 
 def mlp_workspace_bytes(mlp: MLP, n_items: int) -> int:
     return int(load_library().sssgs_mlp_workspace_bytes(ctypes.byref(mlp), n_items))
 
 
-def mlp_bwd(mlp: MLP, pairs, d_pairs, scene: Scene, drec, grad: MLPGrad, dx_items, workspace, stream=None):
+def mlp_bwd(mlp: MLP, pairs, d_pairs, scene: Scene, drec, grad: MLPGrad, dx_items, workspace, d_status=None,
+            stream=None):
     _check(load_library().sssgs_mlp_bwd(ctypes.byref(mlp), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
                                         _p(drec), ctypes.byref(grad), _p(dx_items), _p(workspace),
                                         workspace.numel() * workspace.element_size() if workspace is not None else 0,
-                                        _stream(stream)), "sssgs_mlp_bwd")
+                                        _p(d_status), _stream(stream)), "sssgs_mlp_bwd")
 
 
 def project_fwd(cfg: Cfg, pairs, d_pairs, scene: Scene, mlp_out, rec, rect, stream=None):

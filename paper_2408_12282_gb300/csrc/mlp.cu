@@ -15,7 +15,7 @@
 // register micro-tile per thread and one atomic per weight per CTA.
 #include <algorithm>
 
-#include "common.cuh"
+#include "mlp_common.cuh"
 
 namespace sssgs {
 
@@ -26,90 +26,6 @@ constexpr int FWD_ROWS = 64;
 constexpr int BWD_ROWS = 32;
 constexpr int64_t MLP_CHUNK = 131072;
 
-struct MlpDev {
-    int kind, L;
-    int w[SSSGS_MAX_LAYERS + 1];
-    const float* W[SSSGS_MAX_LAYERS];
-    const float* b[SSSGS_MAX_LAYERS];
-};
-
-// Network input of item m (row of width w[0]) written to x.
-__device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
-                                            int64_t g, float* x) {
-    const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
-    const float3 C = cam_center(P);
-    float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
-    float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
-    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
-    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
-    if (net.kind == SSSGS_MLP_BASIC) {
-        x[0] = m0; x[1] = m1; x[2] = m2;
-        x[3] = wo.x; x[4] = wo.y; x[5] = wo.z;
-        x[6] = wi.x; x[7] = wi.y; x[8] = wi.z;
-        return;
-    }
-    const float mm[3] = {m0, m1, m2};
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            // sin(2^k pi mu) via sinpi of the exact product 2^k mu: no rounding of pi
-            float s, co;
-            sincospif(ldexpf(mm[c], k), &s, &co);
-            x[6 * k + c] = s;
-            x[6 * k + 3 + c] = co;
-        }
-    }
-    x[36] = m0; x[37] = m1; x[38] = m2;
-    x[39] = wo.x; x[40] = wo.y; x[41] = wo.z;
-    x[42] = wi.x; x[43] = wi.y; x[44] = wi.z;
-    x[45] = sc.normal[3 * g]; x[46] = sc.normal[3 * g + 1]; x[47] = sc.normal[3 * g + 2];
-    x[48] = li;
-    x[49] = sc.vis[g];
-    for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
-}
-
-// Input gradient dX (row) -> (dmu, dn, dv) of item m, written to dx[7].
-__device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
-                                               int64_t g, const float* dX, float* dx) {
-    const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
-    const float3 C = cam_center(P);
-    float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
-    float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
-    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
-    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
-    int o_mu, o_wo, o_wi;
-    float dmu[3] = {0.f, 0.f, 0.f};
-    if (net.kind == SSSGS_MLP_BASIC) {
-        o_mu = 0; o_wo = 3; o_wi = 6;
-        dx[3] = dx[4] = dx[5] = dx[6] = 0.f;
-    } else {
-        o_mu = 36; o_wo = 39; o_wi = 42;
-        const float mm[3] = {m0, m1, m2};
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float f = ldexpf(kPi, k);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float s, co;
-                sincospif(ldexpf(mm[c], k), &s, &co);
-                dmu[c] += f * (dX[6 * k + c] * co - dX[6 * k + 3 + c] * s);
-            }
-        }
-        dx[3] = dX[45]; dx[4] = dX[46]; dx[5] = dX[47];
-        dx[6] = dX[49];
-        dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
-    }
-    dmu[0] += dX[o_mu]; dmu[1] += dX[o_mu + 1]; dmu[2] += dX[o_mu + 2];
-    // d unit(P - mu) / d mu applied to g:  -(g - w (w.g)) / |P - mu|
-    const float3 go = make_float3(dX[o_wo], dX[o_wo + 1], dX[o_wo + 2]);
-    const float3 gi = make_float3(dX[o_wi], dX[o_wi + 1], dX[o_wi + 2]);
-    const float3 bo = (-1.f / lo) * (go - dot3(wo, go) * wo);
-    const float3 bi = (-1.f / li) * (gi - dot3(wi, gi) * wi);
-    dx[0] = dmu[0] + bo.x + bi.x;
-    dx[1] = dmu[1] + bo.y + bi.y;
-    dx[2] = dmu[2] + bo.z + bi.z;
-}
 
 // out[r][j] = bias[j] + sum_i in[r][i] * M[i*J + j] over a ROWS-row tile
 // (act 1: ReLU; mask != null: out *= (mask[r][j] > 0)). J multiple of 16.
@@ -466,12 +382,14 @@ int num_sms() {
 }  // namespace
 
 int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
-                     const sssgs_scene* scene, float* out, sssgs_stream stream);
+                     const sssgs_scene* scene, float* out, int32_t* d_status, sssgs_stream stream);
 
 extern "C" int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
-                             int n_pairs, const sssgs_scene* scene, float* out, sssgs_stream stream) {
+                             int n_pairs, const sssgs_scene* scene, float* out, int32_t* d_status,
+                             sssgs_stream stream) {
     if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !out) return SSSGS_ERR_INVALID_ARG;
-    if (mlp->precision == SSSGS_BF16) return sssgs_mlp_fwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, out, stream);
+    if (mlp->precision == SSSGS_BF16)
+        return sssgs_mlp_fwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, out, d_status, stream);
     if (mlp->precision != SSSGS_FP32) return SSSGS_ERR_INVALID_ARG;
     int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
     if (n == 0) return SSSGS_OK;
@@ -492,19 +410,19 @@ extern "C" size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_item
 
 int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
                      const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
-                     void* workspace, size_t workspace_bytes, sssgs_stream stream);
+                     void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream);
 
 extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                              int n_pairs, const sssgs_scene* scene, const float* drec,
                              const sssgs_mlp_grad* grad, float* dx_items, void* workspace,
-                             size_t workspace_bytes, sssgs_stream stream) {
+                             size_t workspace_bytes, int32_t* d_status, sssgs_stream stream) {
     if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !drec || !grad || !dx_items)
         return SSSGS_ERR_INVALID_ARG;
     for (int l = 0; l < mlp->n_layers; ++l)
         if (!grad->W[l]) return SSSGS_ERR_INVALID_ARG;
     if (mlp->precision == SSSGS_BF16)
         return sssgs_mlp_bwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
-                                workspace_bytes, stream);
+                                workspace_bytes, d_status, stream);
     int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
     if (n == 0) return SSSGS_OK;
     if (!workspace || workspace_bytes < sssgs_mlp_workspace_bytes(mlp, n)) return SSSGS_ERR_WORKSPACE;

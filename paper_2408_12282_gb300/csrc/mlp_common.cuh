@@ -1,0 +1,92 @@
+// Network input encoding shared by the CUDA-core and tensor-core networks.
+#pragma once
+#include "common.cuh"
+
+namespace sssgs {
+
+struct MlpDev {
+    int kind, L;
+    int w[SSSGS_MAX_LAYERS + 1];
+    const float* W[SSSGS_MAX_LAYERS];
+    const float* b[SSSGS_MAX_LAYERS];
+};
+
+// Network input of item m (row of width w[0]) written to x.
+__device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
+                                            int64_t g, float* x) {
+    const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
+    const float3 C = cam_center(P);
+    float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
+    float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    if (net.kind == SSSGS_MLP_BASIC) {
+        x[0] = m0; x[1] = m1; x[2] = m2;
+        x[3] = wo.x; x[4] = wo.y; x[5] = wo.z;
+        x[6] = wi.x; x[7] = wi.y; x[8] = wi.z;
+        return;
+    }
+    const float mm[3] = {m0, m1, m2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // sin(2^k pi mu) via sinpi of the exact product 2^k mu: no rounding of pi
+            float s, co;
+            sincospif(ldexpf(mm[c], k), &s, &co);
+            x[6 * k + c] = s;
+            x[6 * k + 3 + c] = co;
+        }
+    }
+    x[36] = m0; x[37] = m1; x[38] = m2;
+    x[39] = wo.x; x[40] = wo.y; x[41] = wo.z;
+    x[42] = wi.x; x[43] = wi.y; x[44] = wi.z;
+    x[45] = sc.normal[3 * g]; x[46] = sc.normal[3 * g + 1]; x[47] = sc.normal[3 * g + 2];
+    x[48] = li;
+    x[49] = sc.vis[g];
+    for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
+}
+
+// Input gradient dX (row) -> (dmu, dn, dv) of item m, written to dx[7].
+__device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
+                                               int64_t g, const float* dX, float* dx) {
+    const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
+    const float3 C = cam_center(P);
+    float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
+    float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    int o_mu, o_wo, o_wi;
+    float dmu[3] = {0.f, 0.f, 0.f};
+    if (net.kind == SSSGS_MLP_BASIC) {
+        o_mu = 0; o_wo = 3; o_wi = 6;
+        dx[3] = dx[4] = dx[5] = dx[6] = 0.f;
+    } else {
+        o_mu = 36; o_wo = 39; o_wi = 42;
+        const float mm[3] = {m0, m1, m2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float f = ldexpf(kPi, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s, co;
+                sincospif(ldexpf(mm[c], k), &s, &co);
+                dmu[c] += f * (dX[6 * k + c] * co - dX[6 * k + 3 + c] * s);
+            }
+        }
+        dx[3] = dX[45]; dx[4] = dX[46]; dx[5] = dX[47];
+        dx[6] = dX[49];
+        dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
+    }
+    dmu[0] += dX[o_mu]; dmu[1] += dX[o_mu + 1]; dmu[2] += dX[o_mu + 2];
+    // d unit(P - mu) / d mu applied to g:  -(g - w (w.g)) / |P - mu|
+    const float3 go = make_float3(dX[o_wo], dX[o_wo + 1], dX[o_wo + 2]);
+    const float3 gi = make_float3(dX[o_wi], dX[o_wi + 1], dX[o_wi + 2]);
+    const float3 bo = (-1.f / lo) * (go - dot3(wo, go) * wo);
+    const float3 bi = (-1.f / li) * (gi - dot3(wi, gi) * wi);
+    dx[0] = dmu[0] + bo.x + bi.x;
+    dx[1] = dmu[1] + bo.y + bi.y;
+    dx[2] = dmu[2] + bo.z + bi.z;
+}
+
+}  // namespace sssgs

@@ -133,7 +133,7 @@ class Renderer:
     # ------------------------------------------------------------------ steps
     def forward_front(self, stream=None):
         t = self.table
-        B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, stream)
+        B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, self.status, stream)
         B.project_fwd(self.cfg, t.h, t.d, self._scene_s, self.mlp_out, self.rec, self.rect, stream)
         B.bin_sort(self.cfg, t.h, t.d, self.rec, self.rect, self.capacity, self.vals, self.ranges, self.count,
                    self.status, self.ws_bin, stream)
@@ -168,13 +168,16 @@ class Renderer:
             B.shade_bwd(self.cfg, t.h, t.d, self.gbuf, dimg, self.dgbuf, stream)
             B.composite_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.dgbuf,
                             self.drec, stream)
-        B.mlp_bwd(self._mlp_s, t.h, t.d, self._scene_s, self.drec, self._mlp_g, self.dx_items, self.ws_mlp, stream)
+        B.mlp_bwd(self._mlp_s, t.h, t.d, self._scene_s, self.drec, self._mlp_g, self.dx_items, self.ws_mlp,
+                  self.status, stream)
         B.project_bwd(self.cfg, t.h, t.d, self._scene_s, self.drec, self.dx_items, self._grad_s, stream)
 
     def check_status(self):
         s = int(self.status.item())
         if s & B.STATUS_CAPACITY:
             raise B.SSSGSError(f"instance capacity {self.capacity} exceeded ({int(self.count.item())} needed)")
+        if s & B.STATUS_TIMEOUT:
+            raise B.SSSGSError("a tensor-core kernel stopped on its wait limit; outputs are incomplete")
 
 
 class SSSRenderFunction(torch.autograd.Function):
