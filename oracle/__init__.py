@@ -164,8 +164,10 @@ def mlp_forward(spec, X, bf16=False):
 def mlp_backward(spec, acts, y, Ls, dLs, dLin, bf16=False):
     """Backward of mlp_forward. Returns (dW list, db list, dX).
 
-    BF16 mode rounds each layer's pre-activation gradient to bfloat16 before
-    it is used as a GEMM operand, matching operands that are stored in bf16."""
+    BF16 mode rounds each layer's pre-activation gradient dz to bfloat16
+    before it is used: as a GEMM operand (dW = dz^T h, dh = dz W) and in the
+    bias gradient db = sum over rows of dz, i.e. every use of dz sees the same
+    bf16 value, as when dz is stored in bf16 once."""
     rnd = bf16_round if bf16 else (lambda a: a)
     nl = len(spec.weights)
     dz = np.zeros_like(y)
@@ -177,7 +179,7 @@ def mlp_backward(spec, acts, y, Ls, dLs, dLin, bf16=False):
         W = rnd(np.asarray(spec.weights[l], np.float64))
         dzr = rnd(dz)
         dWs[l] = dzr.T @ acts[l]
-        dbs[l] = dz.sum(axis=0)
+        dbs[l] = dzr.sum(axis=0)
         dh = dzr @ W
         if l > 0:
             dz = dh * (acts[l] > 0)

@@ -180,6 +180,429 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const 
     if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
+
+// ---------------------------------------------------------------- backward
+//
+// Per 128-row tile: rebuild the input H_0, recompute the forward keeping every
+// layer input H_l (BF16) in shared memory, form the head gradient dZ_L, then
+// for l = L-1 .. 0 (one elected thread issues, all warps run epilogues):
+//   dW_l (+)= dZ_{l+1}^T H_l   hidden layers: accumulated across tiles in TMEM
+//                              first/last layer: per tile, summed in registers
+//   db_l (+)= dZ_{l+1}^T 1     (MMA against a ones operand)
+//   dH_l  = dZ_{l+1} W_l       (two 64-column halves), then
+//   dZ_l  = bf16(dH_l * [H_l > 0]) written in place over H_l; dH_0 is the
+//   network-input gradient, mapped to (d mu, d n, d v) per item.
+// Weight images (BF16, operand layout) stream from global memory with
+// cp.async.bulk into two shared-memory slots, one layer ahead.
+// TMEM columns: [0, 64) dH half / recompute, [64, 128) per-tile dW/db,
+// [128, 512) the hidden layers' dW accumulators.
+
+struct TcBwdLayout {
+    uint32_t offH[SSSGS_MAX_LAYERS];   // layer inputs (later dZ, in place)
+    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offBar;
+    uint32_t total;
+    uint32_t gW[SSSGS_MAX_LAYERS];     // weight image offsets in the global workspace
+    uint32_t wbytes[SSSGS_MAX_LAYERS];
+    uint32_t gtotal;
+    int Np[SSSGS_MAX_LAYERS];
+    int biasOff[SSSGS_MAX_LAYERS];
+    int colW[SSSGS_MAX_LAYERS];        // TMEM column of dW_l (hidden layers)
+};
+
+__host__ __device__ inline TcBwdLayout tc_bwd_layout(const MlpDev& net) {
+    TcBwdLayout T;
+    uint32_t o = 0, g = 0, wmax = 0;
+    int bo = 0, col = 128;
+    for (int l = 0; l < net.L; ++l) {
+        T.Np[l] = (net.w[l + 1] + 15) & ~15;
+        T.offH[l] = o;
+        o += (uint32_t)(TC_ROWS * net.w[l] * 2);
+        T.wbytes[l] = (uint32_t)(T.Np[l] * net.w[l] * 2);
+        T.gW[l] = g;
+        g += (T.wbytes[l] + 127) & ~127u;
+        wmax = T.wbytes[l] > wmax ? T.wbytes[l] : wmax;
+        T.biasOff[l] = bo;
+        bo += T.Np[l];
+        T.colW[l] = -1;
+        if (l >= 1 && l <= net.L - 2) {
+            T.colW[l] = col;
+            col += net.w[l];
+        }
+    }
+    T.offDZL = o;  o += TC_ROWS * 16 * 2;
+    T.offOnes = o; o += 16 * TC_ROWS * 2;
+    T.offW[0] = o; o += wmax;
+    T.offW[1] = o; o += wmax;
+    T.offBias = o; o += (uint32_t)(bo * 4);
+    T.offDbL = o;  o += 16 * 4;
+    T.offBar = o;  o += 32;
+    T.total = o;
+    T.gtotal = g;
+    T.colW[0] = col;          // > 512 signals "does not fit" to the host check
+    return T;
+}
+
+__global__ void k_mlp_weights_bf16(MlpDev net, TcBwdLayout T, uint8_t* __restrict__ gimg) {
+    const int l = blockIdx.y;
+    const int K = net.w[l], N = net.w[l + 1], Np = T.Np[l];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Np * K; i += gridDim.x * blockDim.x) {
+        const int n = i / K, k = i - n * K;
+        const float v = n < N ? net.W[l][n * K + k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(gimg + T.gW[l] + tc::blk_offset(n, k, K)) = __float2bfloat16_rn(v);
+    }
+}
+
+// Store 8 consecutive BF16 values (already packed) of row r.
+__device__ __forceinline__ void store8_packed(uint8_t* base, int r, int c, int C, uint4 q) {
+    *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
+}
+
+__device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c, int C) {
+    return *reinterpret_cast<const uint4*>(base + tc::blk_offset(r, c, C));
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdLayout T,
+                                                              const uint8_t* __restrict__ gimg,
+                                                              const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                                              int64_t n_items, sssgs_scene sc,
+                                                              const float* __restrict__ drec, sssgs_mlp_grad gr,
+                                                              float* __restrict__ dx_items,
+                                                              int32_t* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = net.L;
+    float* sbias = reinterpret_cast<float*>(smem + T.offBias);
+    float* sdbL = reinterpret_cast<float*>(smem + T.offDbL);
+    const uint32_t bar_m = tc::smem_u32(smem + T.offBar);
+    const uint32_t bar_w0 = bar_m + 8, bar_w1 = bar_m + 16;
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + T.offBar + 24);
+    uint8_t* sDZL = smem + T.offDZL;
+
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(s_tmem), 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar_m, 1);
+        tc::mbar_init(bar_w0, 1);
+        tc::mbar_init(bar_w1, 1);
+        tc::fence_mbar_init();
+    }
+    // constants: ones operand (16 x 128, K-major), biases, last-layer db partials
+    for (int i = tid; i < 16 * TC_ROWS / 2; i += TC_THREADS)
+        reinterpret_cast<uint32_t*>(smem + T.offOnes)[i] = 0x3F803F80u;   // two bf16 1.0
+    for (int l = 0; l < L; ++l)
+        for (int n = tid; n < T.Np[l]; n += TC_THREADS) sbias[T.biasOff[l] + n] = n < net.w[l + 1] ? net.b[l][n] : 0.f;
+    if (tid < 16) sdbL[tid] = 0.f;
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+
+    // per-thread accumulators: dW_0 row (thread = output unit), dW_{L-1}^T row
+    // (thread = input unit of the last layer), db of layers 0..L-2
+    float acc0[64];
+    float accL[4] = {0.f, 0.f, 0.f, 0.f};
+    float dbacc[SSSGS_MAX_LAYERS];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc0[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < SSSGS_MAX_LAYERS; ++j) dbacc[j] = 0.f;
+
+    uint32_t ph_m = 0, ph_w[2] = {0u, 0u};
+    uint32_t use = 0;            // weight-use counter (2L uses per tile)
+    bool ok = true, any_tile = false;
+    const int uses_per_tile = 2 * L;
+    auto layer_of_use = [&](uint32_t u) -> int {
+        const int k = (int)(u % (uint32_t)uses_per_tile);
+        return k < L ? k : 2 * L - 1 - k;
+    };
+    const int64_t n_tiles = (n_items + TC_ROWS - 1) / TC_ROWS;
+    if (tid == 0 && (int64_t)blockIdx.x < n_tiles) {   // first weights
+        const int l0 = layer_of_use(0);
+        tc::mbar_arrive_expect_tx(bar_w0, T.wbytes[l0]);
+        tc::bulk_g2s(tc::smem_u32(smem + T.offW[0]), gimg + T.gW[l0], T.wbytes[l0], bar_w0);
+    }
+    // thread 0: prefetch the next use, then wait for this use's weights
+    auto begin_use = [&]() -> bool {
+        bool got = true;
+        if (tid == 0) {
+            const uint32_t nu = use + 1;
+            const int ln = layer_of_use(nu);
+            const int64_t nt = (int64_t)blockIdx.x + (int64_t)(nu / uses_per_tile) * gridDim.x;
+            if (nt < n_tiles) {
+                const uint32_t nb = (nu & 1) ? bar_w1 : bar_w0;
+                tc::mbar_arrive_expect_tx(nb, T.wbytes[ln]);
+                tc::bulk_g2s(tc::smem_u32(smem + T.offW[nu & 1]), gimg + T.gW[ln], T.wbytes[ln], nb);
+            }
+            got = tc::mbar_wait((use & 1) ? bar_w1 : bar_w0, ph_w[use & 1]);
+            tc::fence_after();
+        }
+        ph_w[use & 1] ^= 1u;
+        return got;
+    };
+    auto wait_mma = [&]() -> bool {
+        const bool got = tc::mbar_wait(bar_m, ph_m);
+        ph_m ^= 1u;
+        tc::fence_after();
+        return got;
+    };
+    auto sync_all = [&](bool mine) -> bool {
+        tc::fence_before();
+        tc::fence_async_smem();
+        return __syncthreads_and(mine) != 0;
+    };
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t m = tile * TC_ROWS + tid;
+        const bool valid = m < n_items;
+        int pidx = 0;
+        int64_t gidx = 0;
+        if (valid) {
+            pidx = pair_of_item(pairs, n_pairs, m);
+            gidx = pairs[pidx].g_begin + (m - pairs[pidx].item_offset);
+        }
+        {   // H_0: network input
+            float x[64];
+#pragma unroll
+            for (int k = 0; k < 64; ++k) x[k] = 0.f;
+            if (valid) build_input(net, pairs[pidx], sc, gidx, x);
+            for (int c = 0; c < net.w[0]; c += 8) store8_bf16(smem + T.offH[0], tid, c, net.w[0], x + c);
+        }
+        ok = sync_all(true);
+        // ---------------- forward recompute
+        for (int l = 0; l < L && ok; ++l) {
+            const int K = net.w[l], Np = T.Np[l];
+            bool mine = begin_use();
+            ++use;
+            if (tid == 0) {
+                const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Np, false, false);
+                const uint32_t a0 = tc::smem_u32(smem + T.offH[l]);
+                const uint32_t b0 = tc::smem_u32(smem + T.offW[(use - 1) & 1]);
+                const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+                for (int k = 0; k < K / 16; ++k)
+                    tc::mma_bf16(tmem, tc::make_desc(a0 + k * 256, 128, sbo), tc::make_desc(b0 + k * 256, 128, sbo),
+                                 idesc, k > 0 ? 1u : 0u);
+                tc::mma_commit(bar_m);
+            }
+            __syncwarp();
+            mine = wait_mma() && mine;
+            const float* bl = sbias + T.biasOff[l];
+            if (l < L - 1) {
+                const int N = net.w[l + 1];
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + lane_off + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) store8_bf16(smem + T.offH[l + 1], tid, c0 + 8 * q, N, v + 8 * q);
+                }
+            } else {
+                // heads and their gradient: dZ_L (padded to 16 columns), db_{L-1}
+                float v[16];
+                tc::tmem_ld16(tmem + lane_off, v);
+                float dz[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) dz[j] = 0.f;
+                if (valid) {
+                    const float* up = drec + (int64_t)SSSGS_REC * m + 16;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float s = 1.f / (1.f + expf(-(v[c] + bl[c])));
+                        dz[c] = up[c] * s * (1.f - s);
+                    }
+                    dz[3] = (v[3] + bl[3]) > 0.f ? up[3] : 0.f;
+                }
+                uint4 q0, q1;
+                q0.x = tc::pack_bf16(dz[0], dz[1]); q0.y = tc::pack_bf16(dz[2], dz[3]);
+                q0.z = tc::pack_bf16(dz[4], dz[5]); q0.w = tc::pack_bf16(dz[6], dz[7]);
+                q1.x = tc::pack_bf16(dz[8], dz[9]); q1.y = tc::pack_bf16(dz[10], dz[11]);
+                q1.z = tc::pack_bf16(dz[12], dz[13]); q1.w = tc::pack_bf16(dz[14], dz[15]);
+                store8_packed(sDZL, tid, 0, 16, q0);
+                store8_packed(sDZL, tid, 8, 16, q1);
+                // db_{L-1} = sum over rows of bf16(dZ_L)
+                float r4[4] = {tc::bf16_lo(q0.x), tc::bf16_hi(q0.x), tc::bf16_lo(q0.y), tc::bf16_hi(q0.y)};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float a = r4[c];
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) a += __shfl_xor_sync(SSSGS_FULL, a, off);
+                    if (lane == 0) atomicAdd(&sdbL[c], a);
+                }
+            }
+            ok = sync_all(mine);
+        }
+        // ---------------- backward
+        for (int l = L - 1; l >= 0 && ok; --l) {
+            const int Kin = net.w[l];
+            const bool last = (l == L - 1);
+            const int Nout = last ? 16 : net.w[l + 1];        // dZ_{l+1} columns (padded for the last layer)
+            const uint8_t* dzbuf = last ? sDZL : smem + T.offH[l + 1];
+            const uint32_t dz_addr = tc::smem_u32(dzbuf);
+            const uint32_t dz_sr = (uint32_t)(Nout / 8) * 128u;
+            const uint32_t h_addr = tc::smem_u32(smem + T.offH[l]);
+            const uint32_t h_sr = (uint32_t)(Kin / 8) * 128u;
+            bool mine = begin_use();
+            ++use;
+            const uint32_t w_addr = tc::smem_u32(smem + T.offW[(use - 1) & 1]);
+            const uint32_t w_sr = (uint32_t)(Kin / 8) * 128u;    // weight image: rows = outputs, C = Kin
+            const int halves = Kin > 64 ? 2 : 1;
+            if (tid == 0) {
+                // per-tile or accumulated weight gradient, K' = 128 rows
+                if (T.colW[l] >= 0 && l >= 1 && l <= L - 2) {
+                    const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin, true, true);
+                    for (int k = 0; k < TC_ROWS / 16; ++k)
+                        tc::mma_bf16(tmem + T.colW[l], tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
+                                     tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128), idesc,
+                                     (any_tile || k > 0) ? 1u : 0u);
+                } else if (last) {      // dW_{L-1}^T = H_{L-1}^T dZ_L  -> [Kin x 16]
+                    const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, true);
+                    for (int k = 0; k < TC_ROWS / 16; ++k)
+                        tc::mma_bf16(tmem + 64, tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128),
+                                     tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128), idesc, k > 0 ? 1u : 0u);
+                } else {                // l == 0: dW_0 = dZ_1^T H_0 -> [w1 x Kin]
+                    const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin, true, true);
+                    for (int k = 0; k < TC_ROWS / 16; ++k)
+                        tc::mma_bf16(tmem + 64, tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
+                                     tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128), idesc, k > 0 ? 1u : 0u);
+                }
+                if (!last && l >= 1) {  // db_l = dZ_{l+1}^T 1 -> [Nout x 16]
+                    const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
+                    const uint32_t ones = tc::smem_u32(smem + T.offOnes);
+                    for (int k = 0; k < TC_ROWS / 16; ++k)
+                        tc::mma_bf16(tmem + 64, tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
+                                     tc::make_desc(ones + k * 256, 128, (TC_ROWS / 8) * 128), idesc, k > 0 ? 1u : 0u);
+                }
+                // dH_l, first half: [128 x min(64, Kin)] = dZ_{l+1} W_l
+                const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin > 64 ? 64 : Kin, false, true);
+                for (int k = 0; k < Nout / 16; ++k)
+                    tc::mma_bf16(tmem, tc::make_desc(dz_addr + k * 256, 128, dz_sr),
+                                 tc::make_desc(w_addr + k * 2 * w_sr, w_sr, 128), idesc, k > 0 ? 1u : 0u);
+                tc::mma_commit(bar_m);
+            }
+            __syncwarp();
+            mine = wait_mma() && mine;
+            // epilogue, round 1
+            if (last) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_off + 64, v);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) accL[c] += v[c];
+            } else if (l == 0) {
+                for (int c0 = 0; c0 < 64; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + lane_off + 64 + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc0[c0 + j] += v[j];
+                }
+            } else {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_off + 64, v);
+                dbacc[l] += v[0];
+            }
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1) {
+                    if (halves == 1) break;
+                    mine = sync_all(mine);
+                    if (tid == 0) {
+                        tc::fence_after();
+                        const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 64, false, true);
+                        for (int k = 0; k < Nout / 16; ++k)
+                            tc::mma_bf16(tmem, tc::make_desc(dz_addr + k * 256, 128, dz_sr),
+                                         tc::make_desc(w_addr + 8 * 128 + k * 2 * w_sr, w_sr, 128), idesc,
+                                         k > 0 ? 1u : 0u);
+                        tc::mma_commit(bar_m);
+                    }
+                    __syncwarp();
+                    mine = wait_mma() && mine;
+                }
+                const int cbase = 64 * h;
+                const int ncols = Kin - cbase < 64 ? Kin - cbase : 64;
+                if (l > 0) {
+                    for (int c0 = 0; c0 < ncols; c0 += 32) {
+                        float v[32];
+                        tc::tmem_ld32(tmem + lane_off + c0, v);
+                        uint8_t* hb = smem + T.offH[l];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = cbase + c0 + 8 * q;
+                            const uint4 hq = load8_packed(hb, tid, c, Kin);
+                            float o8[8];
+                            o8[0] = tc::bf16_lo(hq.x) > 0.f ? v[8 * q + 0] : 0.f;
+                            o8[1] = tc::bf16_hi(hq.x) > 0.f ? v[8 * q + 1] : 0.f;
+                            o8[2] = tc::bf16_lo(hq.y) > 0.f ? v[8 * q + 2] : 0.f;
+                            o8[3] = tc::bf16_hi(hq.y) > 0.f ? v[8 * q + 3] : 0.f;
+                            o8[4] = tc::bf16_lo(hq.z) > 0.f ? v[8 * q + 4] : 0.f;
+                            o8[5] = tc::bf16_hi(hq.z) > 0.f ? v[8 * q + 5] : 0.f;
+                            o8[6] = tc::bf16_lo(hq.w) > 0.f ? v[8 * q + 6] : 0.f;
+                            o8[7] = tc::bf16_hi(hq.w) > 0.f ? v[8 * q + 7] : 0.f;
+                            store8_bf16(hb, tid, c, Kin, o8);
+                        }
+                    }
+                } else {
+                    // network-input gradient (64 columns) -> (d mu, d n, d v)
+                    float dX[64];
+                    tc::tmem_ld32(tmem + lane_off, dX);
+                    tc::tmem_ld32(tmem + lane_off + 32, dX + 32);
+                    if (valid) {
+                        float dx[7];
+                        input_backward(net, pairs[pidx], sc, gidx, dX, dx);
+                        for (int k = 0; k < 7; ++k) dx_items[7 * m + k] += dx[k];
+                    }
+                }
+            }
+            mine = sync_all(mine);
+            if (l == 0) {   // db_0 = dZ_1^T 1 (its TMEM columns were busy above)
+                if (tid == 0) {
+                    const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
+                    const uint32_t ones = tc::smem_u32(smem + T.offOnes);
+                    for (int k = 0; k < TC_ROWS / 16; ++k)
+                        tc::mma_bf16(tmem, tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
+                                     tc::make_desc(ones + k * 256, 128, (TC_ROWS / 8) * 128), idesc, k > 0 ? 1u : 0u);
+                    tc::mma_commit(bar_m);
+                }
+                __syncwarp();
+                mine = wait_mma() && mine;
+                float v[16];
+                tc::tmem_ld16(tmem + lane_off, v);
+                dbacc[0] += v[0];
+                mine = sync_all(mine);
+            }
+            ok = mine;
+        }
+        any_tile = true;
+    }
+    if (!ok) {
+        if (tid == 0 && status) atomicOr(status, SSSGS_STATUS_TIMEOUT);
+    } else if (any_tile) {
+        // flush: dW of hidden layers from TMEM, dW_0 / dW_{L-1} / db from registers
+        for (int l = 1; l <= L - 2; ++l) {
+            const int Kin = net.w[l];
+            for (int c0 = 0; c0 < Kin; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + lane_off + T.colW[l] + c0, v);
+                if (tid < net.w[l + 1])
+                    for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[l][tid * Kin + c0 + j], v[j]);
+            }
+        }
+        if (tid < net.w[1])
+            for (int j = 0; j < net.w[0]; ++j) atomicAdd(&gr.W[0][tid * net.w[0] + j], acc0[j]);
+        if (tid < net.w[L - 1])
+            for (int c = 0; c < net.w[L]; ++c) atomicAdd(&gr.W[L - 1][c * net.w[L - 1] + tid], accL[c]);
+        for (int l = 0; l <= L - 2; ++l)
+            if (gr.b[l] && tid < net.w[l + 1]) atomicAdd(&gr.b[l][tid], dbacc[l]);
+        __syncthreads();
+        if (gr.b[L - 1] && tid < net.w[L]) atomicAdd(&gr.b[L - 1][tid], sdbL[tid]);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 }  // namespace sssgs
 
 using namespace sssgs;
@@ -230,7 +653,33 @@ int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     return launch_status();
 }
 
-int sssgs_mlp_bwd_tc(const sssgs_mlp*, const sssgs_pair*, const sssgs_pair*, int, const sssgs_scene*, const float*,
-                     const sssgs_mlp_grad*, float*, void*, size_t, int32_t*, sssgs_stream) {
-    return SSSGS_ERR_UNSUPPORTED;
+
+size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp) {
+    if (!tc_supported(mlp)) return 0;
+    return (size_t)tc_bwd_layout(to_dev_tc(mlp)).gtotal + 256;
+}
+
+int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                     const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
+                     void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream) {
+    if (!tc_supported(mlp)) return SSSGS_ERR_UNSUPPORTED;
+    MlpDev net = to_dev_tc(mlp);
+    TcBwdLayout T = tc_bwd_layout(net);
+    if (T.colW[0] > 512 || T.total > 227 * 1024 || net.w[1] != 128) return SSSGS_ERR_UNSUPPORTED;
+    for (int l = 1; l < net.L; ++l)
+        if (net.w[l] != 128) return SSSGS_ERR_UNSUPPORTED;
+    int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
+    if (n == 0) return SSSGS_OK;
+    if (!workspace || workspace_bytes < (size_t)T.gtotal + 256) return SSSGS_ERR_WORKSPACE;
+    uint8_t* gimg = (uint8_t*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_mlp_weights_bf16<<<dim3(32, net.L), 256, 0, st>>>(net, T, gimg);
+    sssgs::note_launches(1);
+    cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
+    int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
+    k_mlp_bwd_tc<<<grid, TC_THREADS, T.total, st>>>(net, T, gimg, d_pairs, n_pairs, n, *scene, drec, *grad,
+                                                    dx_items, d_status);
+    sssgs::note_launches(1);
+    return launch_status();
 }

@@ -105,7 +105,7 @@ class Renderer:
         self._grad_s = B.scene_grad_struct(self.grads)
         self._mlp_s = mlp.struct()
         self._mlp_g = B.mlp_grad_struct(self.dW, self.db)
-        mws = B.mlp_workspace_bytes(self._mlp_s, n) if mlp.precision == B.FP32 else 256
+        mws = B.mlp_workspace_bytes(self._mlp_s, n)
         self.ws_mlp = torch.empty(max(mws, 256), device=device, dtype=torch.uint8)
         self.capacity = 0
         self.set_capacity(capacity if capacity is not None else max(1024, 16 * n))
