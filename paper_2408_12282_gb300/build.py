@@ -42,6 +42,8 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    # SSSGS_NVCC_FLAGS: extra nvcc flags (e.g. -DSSSGS_BWD_MIN_BLOCKS=2) for tuning builds
+    extra = tuple(extra) + tuple(os.environ.get("SSSGS_NVCC_FLAGS", "").split())
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

@@ -12,9 +12,10 @@
 // The backward replays each pixel's list back to front starting from the final
 // transmittance stored by the forward (T_i = T_{i+1} / (1 - alpha_i)), so no
 // per-pixel list is kept. Per-Gaussian gradients are summed over the 32 pixels
-// of a warp with a transposing butterfly (31 shuffles for up to 32 values,
-// after which lane k holds component k) and issued as one 21-lane
-// fire-and-forget add per warp, instead of one atomic per pixel.
+// of a warp through a per-warp shared-memory transpose (each lane stores its
+// 21 values in a column, lane k then sums row k with eight 16-byte loads) and
+// issued as one 21-lane fire-and-forget add per warp, instead of one atomic
+// per pixel.
 #include "common.cuh"
 
 namespace sssgs {
@@ -171,21 +172,6 @@ __device__ __forceinline__ void load_pair_shared(const sssgs_pair* __restrict__ 
     __syncthreads();
 }
 
-// Sum v[0..31] over the warp; afterwards lane k returns the sum of component k.
-__device__ __forceinline__ float warp_transpose_sum(float* v, int lane) {
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < off; ++i) {
-            float send = up ? v[i] : v[i + off];
-            float keep = up ? v[i + off] : v[i];
-            v[i] = keep + __shfl_xor_sync(SSSGS_FULL, send, off);
-        }
-    }
-    return v[0];
-}
-
 // ---------------------------------------------------------------- composite forward
 
 template <int TILE, bool SHADE>
@@ -295,8 +281,12 @@ __global__ void __launch_bounds__(TILE * TILE) k_shade(sssgs_cfg cfg, const sssg
 
 enum { UPSTREAM_DGBUF = 0, UPSTREAM_DIMG = 1, UPSTREAM_L1 = 2 };
 
+#ifndef SSSGS_BWD_MIN_BLOCKS
+#define SSSGS_BWD_MIN_BLOCKS 3     // resident CTAs per SM the register budget is sized for
+#endif
+
 template <int TILE, int MODE>
-__global__ void __launch_bounds__(TILE * TILE) k_composite_bwd(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+__global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite_bwd(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                                int n_pairs, const float4* __restrict__ rec,
                                                                const uint32_t* __restrict__ vals,
                                                                const uint2* __restrict__ ranges,
@@ -309,8 +299,11 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_bwd(sssgs_cfg cfg, co
                                                                const float* __restrict__ weight, float l1_scale,
                                                                float* __restrict__ drec) {
     constexpr int B = TILE * TILE;
-    extern __shared__ float4 s_rec[];                       // [6][B] then item ids
+    constexpr int NG = 6 + SSSGS_NF;                        // gradient components per Gaussian
+    constexpr int RS = 36;                                  // row stride of the transpose scratch (floats)
+    extern __shared__ float4 s_rec[];                       // [6][B], item ids, reduction scratch
     uint32_t* s_item = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
+    float* s_red = reinterpret_cast<float*>(s_item + B) + (threadIdx.x >> 5) * (NG * RS);
     __shared__ __align__(16) sssgs_pair sP;
     __shared__ uint32_t s_max;
     const int tile = blockIdx.x;
@@ -386,9 +379,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_bwd(sssgs_cfg cfg, co
                 AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
                 const bool act = (pos < lastc) && e.use;
                 if (!__any_sync(SSSGS_FULL, act)) continue;
-                float gr[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c) gr[c] = 0.f;
+                // column `lane` of the per-warp scratch holds this pixel's 21 values
                 if (act) {
                     const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
                     const float g5 = s_rec[5 * B + k].x;
@@ -401,23 +392,38 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_bwd(sssgs_cfg cfg, co
 #pragma unroll
                     for (int c = 0; c < SSSGS_NF; ++c) {
                         dot += dF[c] * f[c];
-                        gr[6 + c] = w * dF[c];
+                        s_red[(6 + c) * RS + lane] = w * dF[c];
                     }
                     const float da = Ti * dot - (Q + dTT) * ia;
                     Q += w * dot;
+                    float dp = 0.f, gdo = 0.f;
                     if (!e.clamped) {
-                        const float dp = -da * e.alpha;
-                        gr[5] = da * e.G;
-                        gr[0] = dp * (g0.z * e.dx + g0.w * e.dy);
-                        gr[1] = dp * (g0.w * e.dx + g1.x * e.dy);
-                        gr[2] = dp * 0.5f * e.dx * e.dx;
-                        gr[3] = dp * e.dx * e.dy;
-                        gr[4] = dp * 0.5f * e.dy * e.dy;
+                        dp = -da * e.alpha;
+                        gdo = da * e.G;
                     }
+                    s_red[0 * RS + lane] = dp * (g0.z * e.dx + g0.w * e.dy);
+                    s_red[1 * RS + lane] = dp * (g0.w * e.dx + g1.x * e.dy);
+                    s_red[2 * RS + lane] = dp * 0.5f * e.dx * e.dx;
+                    s_red[3 * RS + lane] = dp * e.dx * e.dy;
+                    s_red[4 * RS + lane] = dp * 0.5f * e.dy * e.dy;
+                    s_red[5 * RS + lane] = gdo;
                     T = Ti;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NG; ++c) s_red[c * RS + lane] = 0.f;
                 }
-                const float s = warp_transpose_sum(gr, lane);
-                if (lane < 6 + SSSGS_NF) atomicAdd(drec + (int64_t)SSSGS_REC * s_item[k] + lane, s);
+                __syncwarp();
+                if (lane < NG) {
+                    const float4* row = reinterpret_cast<const float4*>(s_red + lane * RS);
+                    float4 a = row[0];
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) {
+                        const float4 b = row[q];
+                        a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                    }
+                    atomicAdd(drec + (int64_t)SSSGS_REC * s_item[k] + lane, (a.x + a.y) + (a.z + a.w));
+                }
+                __syncwarp();
             }
         }
         b1 = b0;
@@ -427,7 +433,10 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_bwd(sssgs_cfg cfg, co
 template <int TILE>
 static size_t fwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4); }
 template <int TILE>
-static size_t bwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4; }
+static size_t bwd_smem() {
+    return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4 +
+           (size_t)(TILE * TILE / 32) * (6 + SSSGS_NF) * 36 * 4;
+}
 
 }  // namespace sssgs
 
