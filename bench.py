@@ -205,6 +205,17 @@ def algorithmic_bytes(stage, n_items, n_pixels, n_inst, n_gauss, n_pairs):
     return 0
 
 
+# FP32 operations per unit of the fused render kernels (counted from the kernel
+# source: an alpha evaluation, a composited contribution, the per-pixel
+# shading and its backward; an FMA counts 2)
+FLOP_EVAL = 14
+FLOP_FWD_CONTRIB = 47
+FLOP_BWD_CONTRIB = 105
+FLOP_SHADE_FWD = 120
+FLOP_SHADE_BWD = 300
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def mlp_flops(widths, rows):
     f = 0
     for a, b in zip(widths[:-1], widths[1:]):
@@ -253,9 +264,19 @@ def run_ours(args):
     l1_scale = 1.0 / (3.0 * table.n_pixels)
     grads_flat = [g for g in r.grads.values()] + r.dW + r.db
 
+    graph = None
+    graph_launches = 0
+    if not args.no_graph:
+        c0 = B.launch_count()
+        graph = r.capture(target=target, l1_scale=l1_scale)
+        graph_launches = (B.launch_count() - c0) // 2      # capture() runs the step once eagerly, once captured
+
     def step():
-        r.forward()
-        r.backward(target=target, l1_scale=l1_scale)
+        if graph is not None:
+            graph.replay()
+        else:
+            r.forward()
+            r.backward(target=target, l1_scale=l1_scale)
         if world > 1:
             for g in grads_flat:
                 dist.all_reduce(g)
@@ -286,7 +307,7 @@ def run_ours(args):
         step()
     e1.record(st)
     torch.cuda.synchronize()
-    launches = (B.launch_count() - l0) // args.steps
+    launches = graph_launches if graph is not None else (B.launch_count() - l0) // args.steps
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
@@ -300,6 +321,8 @@ def run_ours(args):
     # ---------------- per-stage timing (separate pass, events between calls)
     stage_ms = {s: 0.0 for s in STAGES}
     reps = max(2, min(args.steps, 5))
+    stats_f = torch.zeros(2, dtype=torch.int64, device="cuda")
+    stats_b = torch.zeros(2, dtype=torch.int64, device="cuda")
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
         ev[0].record(st)
@@ -309,13 +332,13 @@ def run_ours(args):
         ev[2].record(st)
         B.bin_sort(r.cfg, table.h, table.d, r.rec, r.rect, r.capacity, r.vals, r.ranges, r.count, r.status, r.ws_bin)
         ev[3].record(st)
-        B.render_fwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img)
+        B.render_fwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, stats_f)
         ev[4].record(st)
         r.zero_grads()
         e_z = torch.cuda.Event(enable_timing=True)
         e_z.record(st)
         B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, None, target, None,
-                     l1_scale, r.drec)
+                     l1_scale, r.drec, stats_b)
         ev[5].record(st)
         B.mlp_bwd(r._mlp_s, table.h, table.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp, r.status)
         ev[6].record(st)
@@ -327,6 +350,12 @@ def run_ours(args):
             stage_ms[s] += a.elapsed_time(ev[i + 1]) / reps
     n_items, n_pixels = table.n_items, table.n_pixels
     n_gauss = wl.scenes[0].N
+    contrib_f, evals_f = (int(x) // reps for x in stats_f.tolist())
+    contrib_b, evals_b = (int(x) // reps for x in stats_b.tolist())
+    alu_flops = {
+        "render_fwd": FLOP_FWD_CONTRIB * contrib_f + FLOP_EVAL * (evals_f - contrib_f) + FLOP_SHADE_FWD * n_pixels,
+        "render_bwd": FLOP_BWD_CONTRIB * contrib_b + FLOP_EVAL * (evals_b - contrib_b) + FLOP_SHADE_BWD * n_pixels,
+    }
     dom = max(STAGES, key=lambda s: stage_ms[s])
     widths = [int(r._mlp_s.width[i]) for i in range(r._mlp_s.n_layers + 1)]
     if dom in ("mlp_fwd", "mlp_bwd") and precision == B.BF16:
@@ -334,6 +363,15 @@ def run_ours(args):
         ach = fl / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
                 "frac": ach / bf16_sus, "traffic": None, "peak_source": peak_src + " (bf16 sustained)"}
+    elif dom in alu_flops:
+        ach = alu_flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / ALU_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                "work": {"contributions": contrib_b if dom == "render_bwd" else contrib_f,
+                         "alpha_evaluations": evals_b if dom == "render_bwd" else evals_f},
+                "hbm_frac_of_algorithmic_bytes": algorithmic_bytes(dom, n_items, n_pixels, n_inst, n_gauss, n_pairs)
+                / (stage_ms[dom] * 1e-3) / 1e9 / hbm}
     else:
         by = algorithmic_bytes(dom, n_items, n_pixels, n_inst, n_gauss, n_pairs)
         ach = by / (stage_ms[dom] * 1e-3) / 1e9
@@ -385,8 +423,11 @@ def run_ours(args):
             for k2, v in host_in.items():
                 r.scene[k2].copy_(v, non_blocking=True)
             target.copy_(host_tgt, non_blocking=True)
-            r.forward()
-            r.backward(target=target, l1_scale=l1_scale)
+            if graph is not None:
+                graph.replay()
+            else:
+                r.forward()
+                r.backward(target=target, l1_scale=l1_scale)
             if world > 1:
                 for g in grads_flat:
                     dist.all_reduce(g)
@@ -424,6 +465,8 @@ def run_ours(args):
                 "data": "synthetic", "config": _config(args),
                 "roofline": roof, "step_hbm_frac_of_algorithmic": step_hbm_frac,
                 "stage_ms": stage_ms, "instances": n_inst, "items": n_items, "pixels": n_pixels,
+                "contributions_per_step": {"forward": contrib_f, "backward": contrib_b},
+                "cuda_graph": graph is not None,
                 "plain_fp32": plain, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
@@ -444,6 +487,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

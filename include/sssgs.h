@@ -252,19 +252,23 @@ int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const s
                         const float* gbuf, const uint32_t* last, const float* dgbuf,
                         float* drec, sssgs_stream stream);
 
-/* Fused a3+a4 forward: composite then shade in one pass; writes gbuf, last, img. */
+/* Fused a3+a4 forward: composite then shade in one pass; writes gbuf, last, img.
+ * d_stats (device uint64[2], may be NULL) accumulates the number of
+ * contributions (pixel-Gaussian pairs composited) and of alpha evaluations. */
 int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                      int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
-                     float* gbuf, uint32_t* last, float* img, sssgs_stream stream);
+                     float* gbuf, uint32_t* last, float* img, uint64_t* d_stats, sssgs_stream stream);
 
 /* Fused a4+a3 backward. Upstream gradient either dimg[n_pixels*3], or (dimg ==
  * NULL) the L1 loss  l1_scale * sum |img - target|  with optional per-pixel
- * weights (NULL = 1): dimg = l1_scale * w * sign(img - target). Accumulates drec. */
+ * weights (NULL = 1): dimg = l1_scale * w * sign(img - target). Accumulates drec.
+ * d_stats (device uint64[2], may be NULL) accumulates the contributions
+ * replayed and the alpha evaluations (list positions below each pixel's end). */
 int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                      int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
                      const float* gbuf, const uint32_t* last, const float* img,
                      const float* dimg, const float* target, const float* weight, float l1_scale,
-                     float* drec, sssgs_stream stream);
+                     float* drec, uint64_t* d_stats, sssgs_stream stream);
 
 /* a5 -- projection backward. For every Gaussian of the scene, sums over the
  * pairs that render it: the gradient records drec (geometry via Eq. 2 and the

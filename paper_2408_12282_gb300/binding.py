@@ -95,9 +95,9 @@ _SIGS = {
     "sssgs_composite_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
                              c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_render_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
-                          c_vp, c_vp, c_vp], ctypes.c_int),
+                          c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_render_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
-                          c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp], ctypes.c_int),
+                          c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_project_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
                            c_vp, c_vp, ctypes.POINTER(SceneGrad), c_vp], ctypes.c_int),
 }
@@ -276,17 +276,17 @@ def composite_bwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, dgbuf
                                               _stream(stream)), "sssgs_composite_bwd")
 
 
-def render_fwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, stream=None):
+def render_fwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, stats=None, stream=None):
     _check(load_library().sssgs_render_fwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(vals),
-                                           _p(ranges), _p(gbuf), _p(last), _p(img), _stream(stream)),
+                                           _p(ranges), _p(gbuf), _p(last), _p(img), _p(stats), _stream(stream)),
            "sssgs_render_fwd")
 
 
 def render_bwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, dimg, target, weight, l1_scale,
-               drec, stream=None):
+               drec, stats=None, stream=None):
     _check(load_library().sssgs_render_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(rec), _p(vals),
                                            _p(ranges), _p(gbuf), _p(last), _p(img), _p(dimg), _p(target),
-                                           _p(weight), float(l1_scale), _p(drec), _stream(stream)),
+                                           _p(weight), float(l1_scale), _p(drec), _p(stats), _stream(stream)),
            "sssgs_render_bwd")
 
 

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
                                                                const uint32_t* __restrict__ vals,
                                                                const uint2* __restrict__ ranges,
                                                                float* __restrict__ gbuf, uint32_t* __restrict__ last,
-                                                               float* __restrict__ img) {
+                                                               float* __restrict__ img,
+                                                               unsigned long long* __restrict__ stats) {
     constexpr int B = TILE * TILE;
     extern __shared__ float4 s_rec[];            // [6][B]
     __shared__ __align__(16) sssgs_pair sP;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
     float F[SSSGS_NF];
 #pragma unroll
     for (int k = 0; k < SSSGS_NF; ++k) F[k] = 0.f;
-    uint32_t lastc = 0;
+    uint32_t lastc = 0, n_eval = 0, n_use = 0;
     for (uint32_t b0 = rg.x; b0 < rg.y; b0 += B) {
         if (__syncthreads_count(done) == B) break;
         const uint32_t idx = b0 + threadIdx.x;
@@ -210,9 +211,11 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
             for (int k = 0; k < nb; ++k) {
                 const float4 g0 = s_rec[k], g1 = s_rec[B + k];
                 const AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
+                ++n_eval;
                 if (!e.use) continue;
                 const float Tn = T * (1.f - e.alpha);
                 if (Tn < T_min) { done = true; break; }
+                ++n_use;
                 const float w = T * e.alpha;
                 const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
                 const float g5 = s_rec[5 * B + k].x;
@@ -223,6 +226,18 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
                 T = Tn;
                 lastc = b0 + k + 1;
             }
+        }
+    }
+    if (stats) {   // algorithmic work counters: contributions and alpha evaluations
+        unsigned long long u = n_use, v = n_eval;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            u += __shfl_xor_sync(SSSGS_FULL, u, o);
+            v += __shfl_xor_sync(SSSGS_FULL, v, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(stats, u);
+            atomicAdd(stats + 1, v);
         }
     }
     if (!px.inside) return;
@@ -297,7 +312,8 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
                                                                const float* __restrict__ dimg,
                                                                const float* __restrict__ target,
                                                                const float* __restrict__ weight, float l1_scale,
-                                                               float* __restrict__ drec) {
+                                                               float* __restrict__ drec,
+                                                               unsigned long long* __restrict__ stats) {
     constexpr int B = TILE * TILE;
     constexpr int NG = 6 + SSSGS_NF;                        // gradient components per Gaussian
     constexpr int RS = 36;                                  // row stride of the transpose scratch (floats)
@@ -359,6 +375,7 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
     const uint32_t maxlast = s_max;
     const float dTT = dT * T;        // dLoss/dT_final * T_final
     float Q = 0.f;                   // sum_k dF_k * (suffix sum of w_j f_jk)
+    uint32_t n_use = 0;
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
     for (uint32_t b1 = maxlast; b1 > rg.x;) {
         const uint32_t b0 = b1 - rg.x > (uint32_t)B ? b1 - B : rg.x;
@@ -381,6 +398,7 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
                 if (!__any_sync(SSSGS_FULL, act)) continue;
                 // column `lane` of the per-warp scratch holds this pixel's 21 values
                 if (act) {
+                    ++n_use;
                     const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
                     const float g5 = s_rec[5 * B + k].x;
                     const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
@@ -428,6 +446,18 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
         }
         b1 = b0;
     }
+    if (stats) {   // contributions replayed and alpha evaluations (positions below each pixel's end)
+        unsigned long long u = n_use, v = lastc > rg.x ? lastc - rg.x : 0;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            u += __shfl_xor_sync(SSSGS_FULL, u, o);
+            v += __shfl_xor_sync(SSSGS_FULL, v, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, u);
+            atomicAdd(stats + 1, v);
+        }
+    }
 }
 
 template <int TILE>
@@ -451,11 +481,12 @@ bool a16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 template <int TILE, bool SHADE>
 int launch_fwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
-               const uint32_t* ranges, float* gbuf, uint32_t* last, float* img, cudaStream_t st) {
+               const uint32_t* ranges, float* gbuf, uint32_t* last, float* img, cudaStream_t st,
+               unsigned long long* stats = nullptr) {
     size_t sm = fwd_smem<TILE>();
     cudaFuncSetAttribute(k_composite_fwd<TILE, SHADE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_composite_fwd<TILE, SHADE><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
-                                                                 (const uint2*)ranges, gbuf, last, img);
+                                                                 (const uint2*)ranges, gbuf, last, img, stats);
     sssgs::note_launches(1);
     return launch_status();
 }
@@ -464,12 +495,12 @@ template <int TILE, int MODE>
 int launch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
                const uint32_t* ranges, const float* gbuf, const uint32_t* last, const float* dgbuf,
                const float* img, const float* dimg, const float* target, const float* weight, float l1,
-               float* drec, cudaStream_t st) {
+               float* drec, cudaStream_t st, unsigned long long* stats) {
     size_t sm = bwd_smem<TILE>();
     cudaFuncSetAttribute(k_composite_bwd<TILE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_composite_bwd<TILE, MODE><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
                                                                 (const uint2*)ranges, gbuf, last, dgbuf, img, dimg,
-                                                                target, weight, l1, drec);
+                                                                target, weight, l1, drec, stats);
     sssgs::note_launches(1);
     return launch_status();
 }
@@ -478,12 +509,12 @@ template <int MODE>
 int dispatch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
                  const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
                  const float* dgbuf, const float* img, const float* dimg, const float* target,
-                 const float* weight, float l1, float* drec, cudaStream_t st) {
+                 const float* weight, float l1, float* drec, cudaStream_t st, unsigned long long* stats = nullptr) {
     switch (cfg->tile) {
         case 8: return launch_bwd<8, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
-                                           target, weight, l1, drec, st);
+                                           target, weight, l1, drec, st, stats);
         case 16: return launch_bwd<16, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
-                                             target, weight, l1, drec, st);
+                                             target, weight, l1, drec, st, stats);
         default: return SSSGS_ERR_UNSUPPORTED;   // 32x32 tiles: forward only
     }
 }
@@ -505,16 +536,17 @@ extern "C" int sssgs_composite_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pai
 
 extern "C" int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                                 int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
-                                float* gbuf, uint32_t* last, float* img, sssgs_stream stream) {
+                                float* gbuf, uint32_t* last, float* img, uint64_t* d_stats, sssgs_stream stream) {
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(d_stats);
     if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last || !img)
         return SSSGS_ERR_INVALID_ARG;
     if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
     int tiles = tiles_of(h_pairs, n_pairs);
     cudaStream_t st = (cudaStream_t)stream;
     switch (cfg->tile) {
-        case 8: return launch_fwd<8, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st);
-        case 16: return launch_fwd<16, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st);
-        default: return launch_fwd<32, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st);
+        case 8: return launch_fwd<8, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
+        case 16: return launch_fwd<16, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
+        default: return launch_fwd<32, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
     }
 }
 
@@ -562,7 +594,8 @@ extern "C" int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs,
                                 int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
                                 const float* gbuf, const uint32_t* last, const float* img, const float* dimg,
                                 const float* target, const float* weight, float l1_scale, float* drec,
-                                sssgs_stream stream) {
+                                uint64_t* d_stats, sssgs_stream stream) {
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(d_stats);
     if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last || !drec)
         return SSSGS_ERR_INVALID_ARG;
     if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
@@ -570,8 +603,8 @@ extern "C" int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs,
     cudaStream_t st = (cudaStream_t)stream;
     if (dimg)
         return dispatch_bwd<UPSTREAM_DIMG>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr,
-                                           nullptr, dimg, nullptr, nullptr, 0.f, drec, st);
+                                           nullptr, dimg, nullptr, nullptr, 0.f, drec, st, stats);
     if (!img || !target) return SSSGS_ERR_INVALID_ARG;
     return dispatch_bwd<UPSTREAM_L1>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, img,
-                                     nullptr, target, weight, l1_scale, drec, st);
+                                     nullptr, target, weight, l1_scale, drec, st, stats);
 }

@@ -107,6 +107,8 @@ class Renderer:
         self._mlp_g = B.mlp_grad_struct(self.dW, self.db)
         mws = B.mlp_workspace_bytes(self._mlp_s, n)
         self.ws_mlp = torch.empty(max(mws, 256), device=device, dtype=torch.uint8)
+        self.stats_fwd = None        # optional uint64[2] work counters (see sssgs_render_fwd/bwd)
+        self.stats_bwd = None
         self.capacity = 0
         self.set_capacity(capacity if capacity is not None else max(1024, 16 * n))
 
@@ -142,7 +144,8 @@ class Renderer:
         self.forward_front(stream)
         t = self.table
         if self.fused:
-            B.render_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img, stream)
+            B.render_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
+                         self.stats_fwd, stream)
         else:
             B.composite_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, stream)
             B.shade_fwd(self.cfg, t.h, t.d, self.gbuf, self.img, stream)
@@ -161,7 +164,7 @@ class Renderer:
         self.zero_grads()
         if self.fused:
             B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
-                         dimg, target, weight, l1_scale, self.drec, stream)
+                         dimg, target, weight, l1_scale, self.drec, self.stats_bwd, stream)
         else:
             if dimg is None:
                 raise ValueError("the unfused path takes dimg")
@@ -171,6 +174,27 @@ class Renderer:
         B.mlp_bwd(self._mlp_s, t.h, t.d, self._scene_s, self.drec, self._mlp_g, self.dx_items, self.ws_mlp,
                   self.status, stream)
         B.project_bwd(self.cfg, t.h, t.d, self._scene_s, self.drec, self.dx_items, self._grad_s, stream)
+
+    def capture(self, dimg=None, target=None, weight=None, l1_scale=1.0):
+        """Capture one forward + backward step as a CUDA graph and return it.
+
+        The step has no host synchronisation (instance buffers are sized by
+        capacity, counts stay on the device), so it can be replayed as is;
+        call fit_capacity() first. Inputs are read from the same buffers at
+        every replay."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.forward()
+            self.backward(dimg=dimg, target=target, weight=weight, l1_scale=l1_scale)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self.forward()
+            self.backward(dimg=dimg, target=target, weight=weight, l1_scale=l1_scale)
+        torch.cuda.synchronize()
+        return g
 
     def check_status(self):
         s = int(self.status.item())

@@ -88,5 +88,5 @@ def test_argument_errors_launch_nothing():
     assert lib.sssgs_project_fwd(ctypes.byref(c), h, None, 1, None, None, None, None, None) == -1
     assert lib.sssgs_composite_fwd(ctypes.byref(c), h, None, 1, None, None, None, None, None, None) == -1
     c.tile = 5
-    assert lib.sssgs_render_fwd(ctypes.byref(c), h, 16, 1, 16, 16, 16, 16, 16, 16, None) == -1
+    assert lib.sssgs_render_fwd(ctypes.byref(c), h, 16, 1, 16, 16, 16, 16, 16, 16, None, None) == -1
     assert lib.sssgs_bin_sort(ctypes.byref(c), h, 16, 1, 16, 16, -1, 16, 16, 16, 16, 16, 0, None) == -1
