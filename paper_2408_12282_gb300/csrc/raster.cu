@@ -152,15 +152,61 @@ struct TilePix {
     int64_t pix;
 };
 
+// Pixel of this thread. Each warp covers an 8 x 4 sub-tile (TILE / 8 sub-tiles
+// across), so the per-warp culling mask below is selective.
 __device__ __forceinline__ TilePix tile_pixel(const sssgs_pair& P, int tile, int TILE) {
     TilePix r;
     int lt = tile - P.tile_offset;
     int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
-    r.i = tx * TILE + (int)(threadIdx.x % TILE);
-    r.j = ty * TILE + (int)(threadIdx.x / TILE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_row = TILE / 8;
+    r.i = tx * TILE + (warp % per_row) * 8 + (lane & 7);
+    r.j = ty * TILE + (warp / per_row) * 4 + (lane >> 3);
     r.inside = r.i < P.W && r.j < P.H;
     r.pix = P.pixel_offset + (int64_t)r.j * P.W + r.i;
     return r;
+}
+
+// Conservative test: does the support ellipse {p <= L} of a splat (mean m,
+// conic (a, b, c)) reach the box of pixel centres [x0,x1] x [y0,y1]? The
+// minimum of the convex p over the box is at the mean if it lies inside,
+// else on an edge (1-D minimum clamped to the edge). L is padded so float32
+// rounding of the per-pixel test can never pass where this one fails.
+__device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, float b, float c, float L,
+                                                  float x0, float x1, float y0, float y1) {
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+    const float lim = L * 1.001f + 0.01f;
+    const float ia = 1.f / a, ic = 1.f / c;
+    float best = 3.0e38f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = (e ? x1 : x0) - mx;
+        const float dy = fminf(fmaxf(-b * dx * ic, y0 - my), y1 - my);
+        best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy);
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = (e ? y1 : y0) - my;
+        const float dx = fminf(fmaxf(-b * dy * ia, x0 - mx), x1 - mx);
+        best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy);
+    }
+    return best <= lim;
+}
+
+// Bit w set: the splat can reach warp w's 8 x 4 sub-tile of this tile.
+template <int TILE>
+__device__ __forceinline__ uint32_t subtile_mask(const sssgs_pair& P, int tile, float4 g0, float4 g1, float a_min) {
+    constexpr int NW = TILE * TILE / 32, PER_ROW = TILE / 8;
+    const int lt = tile - P.tile_offset;
+    const float bx = (float)((lt % P.tiles_x) * TILE) + 0.5f, by = (float)((lt / P.tiles_x) * TILE) + 0.5f;
+    const float L = logf(g1.y / a_min);
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const float x0 = bx + (float)((w % PER_ROW) * 8), y0 = by + (float)((w / PER_ROW) * 4);
+        if (ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, L, x0, x0 + 7.f, y0, y0 + 3.f)) m |= 1u << w;
+    }
+    return m;
 }
 
 __device__ __forceinline__ void load_pair_shared(const sssgs_pair* __restrict__ pairs, int n_pairs, int tile,
@@ -183,9 +229,11 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
                                                                float* __restrict__ img,
                                                                unsigned long long* __restrict__ stats) {
     constexpr int B = TILE * TILE;
-    extern __shared__ float4 s_rec[];            // [6][B]
+    extern __shared__ float4 s_rec[];            // [6][B], then sub-tile masks
+    uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
     __shared__ __align__(16) sssgs_pair sP;
     const int tile = blockIdx.x;
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
     load_pair_shared(pairs, n_pairs, tile, &sP);
     const TilePix px = tile_pixel(sP, tile, TILE);
     const float fx = px.i + 0.5f, fy = px.j + 0.5f;
@@ -204,11 +252,13 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
             const float4* r = rec + 6 * (int64_t)vals[idx];
 #pragma unroll
             for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
+            s_mask[threadIdx.x] = subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], a_min);
         }
         __syncthreads();
         const int nb = min(B, (int)(rg.y - b0));
         if (__any_sync(SSSGS_FULL, !done) && !done) {
             for (int k = 0; k < nb; ++k) {
+                if (!(s_mask[k] & wbit)) continue;       // splat misses this warp's sub-tile
                 const float4 g0 = s_rec[k], g1 = s_rec[B + k];
                 const AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
                 ++n_eval;
@@ -317,9 +367,11 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
     constexpr int B = TILE * TILE;
     constexpr int NG = 6 + SSSGS_NF;                        // gradient components per Gaussian
     constexpr int RS = 36;                                  // row stride of the transpose scratch (floats)
-    extern __shared__ float4 s_rec[];                       // [6][B], item ids, reduction scratch
+    extern __shared__ float4 s_rec[];                       // [6][B], item ids, masks, reduction scratch
     uint32_t* s_item = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
-    float* s_red = reinterpret_cast<float*>(s_item + B) + (threadIdx.x >> 5) * (NG * RS);
+    uint32_t* s_mask = s_item + B;
+    float* s_red = reinterpret_cast<float*>(s_mask + B) + (threadIdx.x >> 5) * (NG * RS);
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
     __shared__ __align__(16) sssgs_pair sP;
     __shared__ uint32_t s_max;
     const int tile = blockIdx.x;
@@ -387,10 +439,12 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
             const float4* r = rec + 6 * (int64_t)item;
 #pragma unroll
             for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
+            s_mask[threadIdx.x] = subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], a_min);
         }
         __syncthreads();
         if (__any_sync(SSSGS_FULL, lastc > b0)) {
             for (int k = (int)(b1 - b0) - 1; k >= 0; --k) {
+                if (!(s_mask[k] & wbit)) continue;       // splat misses this warp's sub-tile
                 const uint32_t pos = b0 + k;
                 const float4 g0 = s_rec[k], g1 = s_rec[B + k];
                 AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
@@ -461,10 +515,10 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
 }
 
 template <int TILE>
-static size_t fwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4); }
+static size_t fwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4; }
 template <int TILE>
 static size_t bwd_smem() {
-    return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4 +
+    return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 8 +
            (size_t)(TILE * TILE / 32) * (6 + SSSGS_NF) * 36 * 4;
 }
 
