@@ -193,18 +193,20 @@ __device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, f
     return best <= lim;
 }
 
-// Bit w set: the splat can reach warp w's 8 x 4 sub-tile of this tile.
-template <int TILE>
+// Bit w set: the splat can reach warp w's SW x SH sub-tile of this tile
+// (sub-tiles numbered row-major, TILE / SW across).
+template <int TILE, int SW = 8, int SH = 4>
 __device__ __forceinline__ uint32_t subtile_mask(const sssgs_pair& P, int tile, float4 g0, float4 g1, float a_min) {
-    constexpr int NW = TILE * TILE / 32, PER_ROW = TILE / 8;
+    constexpr int PER_ROW = TILE / SW, NW = (TILE / SW) * (TILE / SH);
     const int lt = tile - P.tile_offset;
     const float bx = (float)((lt % P.tiles_x) * TILE) + 0.5f, by = (float)((lt / P.tiles_x) * TILE) + 0.5f;
     const float L = logf(g1.y / a_min);
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-        const float x0 = bx + (float)((w % PER_ROW) * 8), y0 = by + (float)((w / PER_ROW) * 4);
-        if (ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, L, x0, x0 + 7.f, y0, y0 + 3.f)) m |= 1u << w;
+        const float x0 = bx + (float)((w % PER_ROW) * SW), y0 = by + (float)((w / PER_ROW) * SH);
+        if (ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, L, x0, x0 + (float)(SW - 1), y0, y0 + (float)(SH - 1)))
+            m |= 1u << w;
     }
     return m;
 }
@@ -514,6 +516,197 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
     }
 }
 
+
+// ---------------------------------------------------------------- composite backward, 2 px / thread
+//
+// 16 x 16 tiles with 128 threads: each warp owns an 8 x 8 sub-tile, each lane
+// two vertically adjacent pixels. Both pixels' gradient contributions to a
+// splat are summed in registers before the warp reduction, which halves the
+// shared-memory reduction traffic and the record broadcasts per pixel.
+
+struct PixBwd {
+    float dF[SSSGS_NF];
+    float T, Q, dTT, fx, fy;
+    uint32_t lastc;
+};
+
+// Back-to-front step for one contributing splat at one pixel: updates the
+// pixel's replay state and adds its 21 gradient terms into acc.
+__device__ __forceinline__ void bwd_contrib(PixBwd& p, const AlphaEval& e, float4 g0, float4 g1, const float* f,
+                                            float* acc) {
+    const float ia = 1.f / (1.f - e.alpha);
+    const float Ti = p.T * ia;
+    const float w = e.alpha * Ti;
+    float dot = 0.f;
+#pragma unroll
+    for (int c = 0; c < SSSGS_NF; ++c) {
+        dot += p.dF[c] * f[c];
+        acc[6 + c] += w * p.dF[c];
+    }
+    const float da = Ti * dot - (p.Q + p.dTT) * ia;
+    p.Q += w * dot;
+    if (!e.clamped) {
+        const float dp = -da * e.alpha;
+        acc[0] += dp * (g0.z * e.dx + g0.w * e.dy);
+        acc[1] += dp * (g0.w * e.dx + g1.x * e.dy);
+        acc[2] += dp * 0.5f * e.dx * e.dx;
+        acc[3] += dp * e.dx * e.dy;
+        acc[4] += dp * 0.5f * e.dy * e.dy;
+        acc[5] += da * e.G;
+    }
+    p.T = Ti;
+}
+
+template <int MODE>
+__device__ __forceinline__ void bwd_pixel_setup(PixBwd& p, bool inside, int64_t pix, const sssgs_pair& P,
+                                                const sssgs_cfg& cfg, const float* __restrict__ gbuf,
+                                                const uint32_t* __restrict__ last, const float* __restrict__ img,
+                                                const float* __restrict__ dimg, const float* __restrict__ target,
+                                                const float* __restrict__ weight, float l1_scale) {
+    float dT = 0.f;
+    p.T = 1.f;
+    p.lastc = 0;
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) p.dF[k] = 0.f;
+    if (inside) {
+        p.lastc = last[pix];
+        const float4* gi = reinterpret_cast<const float4*>(gbuf + SSSGS_GBUF * pix);
+        float F[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 v = gi[q];
+            F[4 * q] = v.x; F[4 * q + 1] = v.y; F[4 * q + 2] = v.z; F[4 * q + 3] = v.w;
+        }
+        p.T = F[15];
+        float g3[3], o[3];
+        if (MODE == UPSTREAM_DIMG) {
+            g3[0] = dimg[3 * pix]; g3[1] = dimg[3 * pix + 1]; g3[2] = dimg[3 * pix + 2];
+        } else {
+            const float wgt = l1_scale * (weight ? weight[pix] : 1.f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float d = img[3 * pix + c] - target[3 * pix + c];
+                g3[c] = d > 0.f ? wgt : (d < 0.f ? -wgt : 0.f);
+            }
+        }
+        shade_px<true>(F, p.T, p.fx, p.fy, P, cfg.A_eps, o, g3, p.dF, &dT);
+    }
+    p.dTT = dT * p.T;
+    p.Q = 0.f;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 4) k_composite_bwd2(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+                                                         int n_pairs, const float4* __restrict__ rec,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint2* __restrict__ ranges,
+                                                         const float* __restrict__ gbuf,
+                                                         const uint32_t* __restrict__ last,
+                                                         const float* __restrict__ img,
+                                                         const float* __restrict__ dimg,
+                                                         const float* __restrict__ target,
+                                                         const float* __restrict__ weight, float l1_scale,
+                                                         float* __restrict__ drec,
+                                                         unsigned long long* __restrict__ stats) {
+    constexpr int TILE = 16, B = 128, NG = 6 + SSSGS_NF, RS = 36;
+    extern __shared__ float4 s_rec[];                       // [6][B], item ids, masks, reduction scratch
+    uint32_t* s_item = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
+    uint32_t* s_mask = s_item + B;
+    float* s_red = reinterpret_cast<float*>(s_mask + B) + (threadIdx.x >> 5) * (NG * RS);
+    __shared__ __align__(16) sssgs_pair sP;
+    __shared__ uint32_t s_max;
+    const int tile = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t wbit = 1u << warp;
+    if (threadIdx.x == 0) s_max = 0;
+    load_pair_shared(pairs, n_pairs, tile, &sP);
+    const int lt = tile - sP.tile_offset;
+    const int i = (lt % sP.tiles_x) * TILE + (warp & 1) * 8 + (lane & 7);
+    const int j0 = (lt / sP.tiles_x) * TILE + (warp >> 1) * 8 + (lane >> 3) * 2;
+    const uint2 rg = ranges[tile];
+    PixBwd p[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = j0 + q;
+        const bool inside = i < sP.W && j < sP.H;
+        const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
+        p[q].fx = i + 0.5f;
+        p[q].fy = j + 0.5f;
+        bwd_pixel_setup<MODE>(p[q], inside, pix, sP, cfg, gbuf, last, img, dimg, target, weight, l1_scale);
+    }
+    const uint32_t mylast = max(p[0].lastc, p[1].lastc);
+    if (mylast > 0) atomicMax(&s_max, mylast);
+    __syncthreads();
+    const uint32_t maxlast = s_max;
+    const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
+    uint32_t n_use = 0;
+    for (uint32_t b1 = maxlast; b1 > rg.x;) {
+        const uint32_t b0 = b1 - rg.x > (uint32_t)B ? b1 - B : rg.x;
+        __syncthreads();
+        const uint32_t idx = b0 + threadIdx.x;
+        if (idx < b1) {
+            const uint32_t item = vals[idx];
+            s_item[threadIdx.x] = item;
+            const float4* r = rec + 6 * (int64_t)item;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
+            s_mask[threadIdx.x] = subtile_mask<TILE, 8, 8>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], a_min);
+        }
+        __syncthreads();
+        if (__any_sync(SSSGS_FULL, mylast > b0)) {
+            for (int k = (int)(b1 - b0) - 1; k >= 0; --k) {
+                if (!(s_mask[k] & wbit)) continue;
+                const uint32_t pos = b0 + k;
+                const float4 g0 = s_rec[k], g1 = s_rec[B + k];
+                const AlphaEval e0 = eval_alpha(g0, g1, p[0].fx, p[0].fy, a_min, a_max);
+                const AlphaEval e1 = eval_alpha(g0, g1, p[1].fx, p[1].fy, a_min, a_max);
+                const bool act0 = (pos < p[0].lastc) && e0.use;
+                const bool act1 = (pos < p[1].lastc) && e1.use;
+                if (!__any_sync(SSSGS_FULL, act0 || act1)) continue;
+                float acc[NG];
+#pragma unroll
+                for (int c = 0; c < NG; ++c) acc[c] = 0.f;
+                if (act0 || act1) {
+                    const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
+                    const float g5 = s_rec[5 * B + k].x;
+                    const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
+                                               g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
+                    if (act0) { bwd_contrib(p[0], e0, g0, g1, f, acc); ++n_use; }
+                    if (act1) { bwd_contrib(p[1], e1, g0, g1, f, acc); ++n_use; }
+                }
+#pragma unroll
+                for (int c = 0; c < NG; ++c) s_red[c * RS + lane] = acc[c];
+                __syncwarp();
+                if (lane < NG) {
+                    const float4* row = reinterpret_cast<const float4*>(s_red + lane * RS);
+                    float4 a = row[0];
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) {
+                        const float4 bq = row[q];
+                        a.x += bq.x; a.y += bq.y; a.z += bq.z; a.w += bq.w;
+                    }
+                    atomicAdd(drec + (int64_t)SSSGS_REC * s_item[k] + lane, (a.x + a.y) + (a.z + a.w));
+                }
+                __syncwarp();
+            }
+        }
+        b1 = b0;
+    }
+    if (stats) {
+        unsigned long long u = n_use;
+        unsigned long long v = (p[0].lastc > rg.x ? p[0].lastc - rg.x : 0) + (p[1].lastc > rg.x ? p[1].lastc - rg.x : 0);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            u += __shfl_xor_sync(SSSGS_FULL, u, o);
+            v += __shfl_xor_sync(SSSGS_FULL, v, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, u);
+            atomicAdd(stats + 1, v);
+        }
+    }
+}
+
 template <int TILE>
 static size_t fwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4; }
 template <int TILE>
@@ -560,6 +753,19 @@ int launch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, cons
 }
 
 template <int MODE>
+int launch_bwd2(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
+                const uint32_t* ranges, const float* gbuf, const uint32_t* last, const float* img,
+                const float* dimg, const float* target, const float* weight, float l1, float* drec,
+                cudaStream_t st, unsigned long long* stats) {
+    const size_t sm = (size_t)6 * 128 * sizeof(float4) + (size_t)128 * 8 + (size_t)4 * (6 + SSSGS_NF) * 36 * 4;
+    cudaFuncSetAttribute(k_composite_bwd2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_composite_bwd2<MODE><<<tiles, 128, sm, st>>>(*cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf,
+                                                   last, img, dimg, target, weight, l1, drec, stats);
+    sssgs::note_launches(1);
+    return launch_status();
+}
+
+template <int MODE>
 int dispatch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
                  const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
                  const float* dgbuf, const float* img, const float* dimg, const float* target,
@@ -567,8 +773,12 @@ int dispatch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, co
     switch (cfg->tile) {
         case 8: return launch_bwd<8, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
                                            target, weight, l1, drec, st, stats);
-        case 16: return launch_bwd<16, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
-                                             target, weight, l1, drec, st, stats);
+        case 16:
+            if (MODE != UPSTREAM_DGBUF)
+                return launch_bwd2<MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, dimg, target, weight,
+                                         l1, drec, st, stats);
+            return launch_bwd<16, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
+                                        target, weight, l1, drec, st, stats);
         default: return SSSGS_ERR_UNSUPPORTED;   // 32x32 tiles: forward only
     }
 }
