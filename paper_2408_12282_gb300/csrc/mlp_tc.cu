@@ -45,12 +45,12 @@ __host__ __device__ inline TcLayout tc_layout(const MlpDev& net) {
         bo += T.Np[l];
     }
     T.offA = o;
-    o += TC_ROWS * TC_MAXW * 2;
+    o += 2 * TC_ROWS * TC_MAXW * 2;             // one activation tile per lane
     T.offBias = o;
     o += (uint32_t)(bo * 4);
     o = (o + 15) & ~15u;
     T.offBar = o;
-    o += 16;
+    o += 32 + 8 * 256;                           // mbarriers, TMEM address, flags, pair offsets
     T.total = o;
     return T;
 }
@@ -80,56 +80,86 @@ __device__ __forceinline__ void store8_bf16(uint8_t* base, int r, int c, int C, 
     *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const sssgs_pair* __restrict__ pairs,
-                                                              int n_pairs, int64_t n_items, sssgs_scene sc,
-                                                              float* __restrict__ out, int32_t* __restrict__ status) {
+constexpr int TC_MAX_SMEM_PAIRS = 256;
+
+// Item -> pair lookup against a shared-memory copy of the pairs' item offsets
+// (falls back to the global table for very large batches).
+__device__ __forceinline__ int pair_lookup(const int64_t* s_off, const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                           int64_t item) {
+    if (n_pairs > TC_MAX_SMEM_PAIRS) return pair_of_item(pairs, n_pairs, item);
+    int lo = 0, hi = n_pairs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Two independent tile lanes per CTA: warpgroup g (4 warps) owns activation
+// buffer g, TMEM columns [128 g, 128 g + 128) and mbarrier g, and processes
+// every other tile; the tensor core interleaves the two lanes' MMAs, so one
+// lane's epilogue overlaps the other's matrix work. Weights are shared.
+__global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const sssgs_pair* __restrict__ pairs,
+                                                                  int n_pairs, int64_t n_items, sssgs_scene sc,
+                                                                  float* __restrict__ out,
+                                                                  int32_t* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcLayout T = tc_layout(net);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = (tid >> 5) & 3;
     float* sbias = reinterpret_cast<float*>(smem + T.offBias);
-    const uint32_t bar = tc::smem_u32(smem + T.offBar);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + T.offBar + 8);
-    uint8_t* sA = smem + T.offA;
+    const uint32_t bar = tc::smem_u32(smem + T.offBar) + 8 * wg;
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + T.offBar + 16);
+    volatile int* s_fail = reinterpret_cast<volatile int*>(smem + T.offBar + 24);
+    int64_t* s_off = reinterpret_cast<int64_t*>(smem + T.offBar + 32);
+    uint8_t* sA = smem + T.offA + wg * (TC_ROWS * TC_MAXW * 2);
     const uint32_t a_addr = tc::smem_u32(sA);
 
-    if (warp == 0) {
-        tc::tmem_alloc(tc::smem_u32(s_tmem), 128);
+    if (tid < 32) {
+        tc::tmem_alloc(tc::smem_u32(s_tmem), 256);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        tc::mbar_init(tc::smem_u32(smem + T.offBar), 1);
+        tc::mbar_init(tc::smem_u32(smem + T.offBar) + 8, 1);
         tc::fence_mbar_init();
+        s_fail[0] = 0;
+        s_fail[1] = 0;
     }
+    for (int p = tid; p < n_pairs && p < TC_MAX_SMEM_PAIRS; p += blockDim.x) s_off[p] = pairs[p].item_offset;
     stage_weights_bf16(net, T, smem, sbias);
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t tmem = *s_tmem;
+    const uint32_t tmem = *s_tmem + (uint32_t)(wg * 128);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t phase = 0;
     bool ok = true;
     const int64_t n_tiles = (n_items + TC_ROWS - 1) / TC_ROWS;
     const int K0 = net.w[0];
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t m = tile * TC_ROWS + tid;
+    for (int64_t tile = 2 * (int64_t)blockIdx.x + wg; tile < n_tiles && ok; tile += 2 * (int64_t)gridDim.x) {
+        const int64_t m = tile * TC_ROWS + t;
         {
             float x[TC_MAXW];
 #pragma unroll
             for (int k = 0; k < 64; ++k) x[k] = 0.f;
             if (m < n_items) {
-                const int p = pair_of_item(pairs, n_pairs, m);
+                const int p = pair_lookup(s_off, pairs, n_pairs, m);
                 const sssgs_pair& P = pairs[p];
                 build_input(net, P, sc, P.g_begin + (m - P.item_offset), x);
             }
-            for (int c = 0; c < K0; c += 8) store8_bf16(sA, tid, c, K0, x + c);
+            for (int c = 0; c < K0; c += 8) store8_bf16(sA, t, c, K0, x + c);
         }
         tc::fence_async_smem();
         tc::fence_before();
-        __syncthreads();
+        named_sync(1 + wg, 128);
         for (int l = 0; l < net.L; ++l) {
             const int K = net.w[l], N = T.Np[l];
-            if (tid == 0) {
+            if (t == 0) {
                 tc::fence_after();
                 const uint32_t idesc = tc::idesc_bf16(TC_ROWS, N, false, false);
                 const uint32_t w_addr = tc::smem_u32(smem + T.offW[l]);
@@ -142,9 +172,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const 
                 tc::mma_commit(bar);
             }
             __syncwarp();
-            bool got = tc::mbar_wait(bar, phase);
+            const bool got = tc::mbar_wait(bar, phase);
             phase ^= 1;
             tc::fence_after();
+            if (!got) s_fail[wg] = 1;
             if (got) {
                 const float* bl = sbias + T.biasOff[l];
                 if (l < net.L - 1) {
@@ -154,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const 
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) store8_bf16(sA, tid, c0 + 8 * q, N, v + 8 * q);
+                        for (int q = 0; q < 4; ++q) store8_bf16(sA, t, c0 + 8 * q, N, v + 8 * q);
                     }
                 } else {
                     float v[16];
@@ -171,15 +202,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const 
             }
             tc::fence_before();
             tc::fence_async_smem();
-            ok = __syncthreads_and(got) != 0;
+            named_sync(1 + wg, 128);
+            ok = s_fail[wg] == 0;
             if (!ok) break;
         }
     }
-    if (!ok && tid == 0 && status) atomicOr(status, SSSGS_STATUS_TIMEOUT);
+    if (!ok && t == 0 && status) atomicOr(status, SSSGS_STATUS_TIMEOUT);
+    tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    tc::fence_after();
+    if (tid < 32) tc::tmem_dealloc(*s_tmem, 256);
 }
-
 
 // ---------------------------------------------------------------- backward
 //
@@ -199,7 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, const 
 
 struct TcBwdLayout {
     uint32_t offH[SSSGS_MAX_LAYERS];   // layer inputs (later dZ, in place)
-    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offBar;
+    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offBar, offPairs;
     uint32_t total;
     uint32_t gW[SSSGS_MAX_LAYERS];     // weight image offsets in the global workspace
     uint32_t wbytes[SSSGS_MAX_LAYERS];
@@ -236,6 +269,7 @@ __host__ __device__ inline TcBwdLayout tc_bwd_layout(const MlpDev& net) {
     T.offBias = o; o += (uint32_t)(bo * 4);
     T.offDbL = o;  o += 16 * 4;
     T.offBar = o;  o += 32;
+    T.offPairs = o; o += 8 * 256;
     T.total = o;
     T.gtotal = g;
     T.colW[0] = col;          // > 512 signals "does not fit" to the host check
@@ -261,7 +295,7 @@ __device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c,
     return *reinterpret_cast<const uint4*>(base + tc::blk_offset(r, c, C));
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdLayout T,
+__global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdLayout T,
                                                               const uint8_t* __restrict__ gimg,
                                                               const sssgs_pair* __restrict__ pairs, int n_pairs,
                                                               int64_t n_items, sssgs_scene sc,
@@ -269,8 +303,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
                                                               float* __restrict__ dx_items,
                                                               int32_t* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // 8 warps: warpgroup wg handles half of the columns of every column-parallel
+    // epilogue; per-row scalar work (input, heads, input gradient) runs on wg 0.
+    const int tid = threadIdx.x, lane = tid & 31, wg = tid >> 7, t = tid & 127, warp = (tid >> 5) & 3;
     const int L = net.L;
+    int64_t* s_off = reinterpret_cast<int64_t*>(smem + T.offPairs);
     float* sbias = reinterpret_cast<float*>(smem + T.offBias);
     float* sdbL = reinterpret_cast<float*>(smem + T.offDbL);
     const uint32_t bar_m = tc::smem_u32(smem + T.offBar);
@@ -278,10 +315,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + T.offBar + 24);
     uint8_t* sDZL = smem + T.offDZL;
 
-    if (warp == 0) {
+    if (tid < 32) {
         tc::tmem_alloc(tc::smem_u32(s_tmem), 512);
         tc::tmem_relinquish();
     }
+    for (int p = tid; p < n_pairs && p < TC_MAX_SMEM_PAIRS; p += blockDim.x) s_off[p] = pairs[p].item_offset;
     if (tid == 0) {
         tc::mbar_init(bar_m, 1);
         tc::mbar_init(bar_w0, 1);
@@ -289,10 +327,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
         tc::fence_mbar_init();
     }
     // constants: ones operand (16 x 128, K-major), biases, last-layer db partials
-    for (int i = tid; i < 16 * TC_ROWS / 2; i += TC_THREADS)
+    for (int i = tid; i < 16 * TC_ROWS / 2; i += blockDim.x)
         reinterpret_cast<uint32_t*>(smem + T.offOnes)[i] = 0x3F803F80u;   // two bf16 1.0
     for (int l = 0; l < L; ++l)
-        for (int n = tid; n < T.Np[l]; n += TC_THREADS) sbias[T.biasOff[l] + n] = n < net.w[l + 1] ? net.b[l][n] : 0.f;
+        for (int n = tid; n < T.Np[l]; n += blockDim.x) sbias[T.biasOff[l] + n] = n < net.w[l + 1] ? net.b[l][n] : 0.f;
     if (tid < 16) sdbL[tid] = 0.f;
     tc::fence_async_smem();
     tc::fence_before();
@@ -303,11 +341,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
 
     // per-thread accumulators: dW_0 row (thread = output unit), dW_{L-1}^T row
     // (thread = input unit of the last layer), db of layers 0..L-2
-    float acc0[64];
+    float acc0[32];                    // this warpgroup's 32 of dW_0's 64 input columns
     float accL[4] = {0.f, 0.f, 0.f, 0.f};
     float dbacc[SSSGS_MAX_LAYERS];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc0[j] = 0.f;
+    for (int j = 0; j < 32; ++j) acc0[j] = 0.f;
 #pragma unroll
     for (int j = 0; j < SSSGS_MAX_LAYERS; ++j) dbacc[j] = 0.f;
 
@@ -356,20 +394,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
     };
 
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t m = tile * TC_ROWS + tid;
+        const int64_t m = tile * TC_ROWS + t;
         const bool valid = m < n_items;
         int pidx = 0;
         int64_t gidx = 0;
         if (valid) {
-            pidx = pair_of_item(pairs, n_pairs, m);
+            pidx = pair_lookup(s_off, pairs, n_pairs, m);
             gidx = pairs[pidx].g_begin + (m - pairs[pidx].item_offset);
         }
-        {   // H_0: network input
+        if (wg == 0) {   // H_0: network input
             float x[64];
 #pragma unroll
             for (int k = 0; k < 64; ++k) x[k] = 0.f;
             if (valid) build_input(net, pairs[pidx], sc, gidx, x);
-            for (int c = 0; c < net.w[0]; c += 8) store8_bf16(smem + T.offH[0], tid, c, net.w[0], x + c);
+            for (int c = 0; c < net.w[0]; c += 8) store8_bf16(smem + T.offH[0], t, c, net.w[0], x + c);
         }
         ok = sync_all(true);
         // ---------------- forward recompute
@@ -392,15 +430,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
             const float* bl = sbias + T.biasOff[l];
             if (l < L - 1) {
                 const int N = net.w[l + 1];
-                for (int c0 = 0; c0 < N; c0 += 32) {
+                for (int c0 = wg * (N / 2); c0 < (wg + 1) * (N / 2); c0 += 32) {
                     float v[32];
                     tc::tmem_ld32(tmem + lane_off + c0, v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) store8_bf16(smem + T.offH[l + 1], tid, c0 + 8 * q, N, v + 8 * q);
+                    for (int q = 0; q < 4; ++q) store8_bf16(smem + T.offH[l + 1], t, c0 + 8 * q, N, v + 8 * q);
                 }
-            } else {
+            } else if (wg == 0) {
                 // heads and their gradient: dZ_L (padded to 16 columns), db_{L-1}
                 float v[16];
                 tc::tmem_ld16(tmem + lane_off, v);
@@ -421,8 +459,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
                 q0.z = tc::pack_bf16(dz[4], dz[5]); q0.w = tc::pack_bf16(dz[6], dz[7]);
                 q1.x = tc::pack_bf16(dz[8], dz[9]); q1.y = tc::pack_bf16(dz[10], dz[11]);
                 q1.z = tc::pack_bf16(dz[12], dz[13]); q1.w = tc::pack_bf16(dz[14], dz[15]);
-                store8_packed(sDZL, tid, 0, 16, q0);
-                store8_packed(sDZL, tid, 8, 16, q1);
+                store8_packed(sDZL, t, 0, 16, q0);
+                store8_packed(sDZL, t, 8, 16, q1);
                 // db_{L-1} = sum over rows of bf16(dZ_L)
                 float r4[4] = {tc::bf16_lo(q0.x), tc::bf16_hi(q0.x), tc::bf16_lo(q0.y), tc::bf16_hi(q0.y)};
 #pragma unroll
@@ -487,18 +525,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
             mine = wait_mma() && mine;
             // epilogue, round 1
             if (last) {
-                float v[16];
-                tc::tmem_ld16(tmem + lane_off + 64, v);
+                if (wg == 0) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + lane_off + 64, v);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) accL[c] += v[c];
-            } else if (l == 0) {
-                for (int c0 = 0; c0 < 64; c0 += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tmem + lane_off + 64 + c0, v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) acc0[c0 + j] += v[j];
+                    for (int c = 0; c < 4; ++c) accL[c] += v[c];
                 }
-            } else {
+            } else if (l == 0) {
+                float v[32];
+                tc::tmem_ld32(tmem + lane_off + 64 + 32 * wg, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc0[j] += v[j];
+            } else if (wg == 0) {
                 float v[16];
                 tc::tmem_ld16(tmem + lane_off + 64, v);
                 dbacc[l] += v[0];
@@ -522,14 +560,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
                 const int cbase = 64 * h;
                 const int ncols = Kin - cbase < 64 ? Kin - cbase : 64;
                 if (l > 0) {
-                    for (int c0 = 0; c0 < ncols; c0 += 32) {
+                    for (int c0 = 32 * wg; c0 < ncols; c0 += 64) {
                         float v[32];
                         tc::tmem_ld32(tmem + lane_off + c0, v);
                         uint8_t* hb = smem + T.offH[l];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int c = cbase + c0 + 8 * q;
-                            const uint4 hq = load8_packed(hb, tid, c, Kin);
+                            const uint4 hq = load8_packed(hb, t, c, Kin);
                             float o8[8];
                             o8[0] = tc::bf16_lo(hq.x) > 0.f ? v[8 * q + 0] : 0.f;
                             o8[1] = tc::bf16_hi(hq.x) > 0.f ? v[8 * q + 1] : 0.f;
@@ -539,10 +577,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
                             o8[5] = tc::bf16_hi(hq.z) > 0.f ? v[8 * q + 5] : 0.f;
                             o8[6] = tc::bf16_lo(hq.w) > 0.f ? v[8 * q + 6] : 0.f;
                             o8[7] = tc::bf16_hi(hq.w) > 0.f ? v[8 * q + 7] : 0.f;
-                            store8_bf16(hb, tid, c, Kin, o8);
+                            store8_bf16(hb, t, c, Kin, o8);
                         }
                     }
-                } else {
+                } else if (wg == 0) {
                     // network-input gradient (64 columns) -> (d mu, d n, d v)
                     float dX[64];
                     tc::tmem_ld32(tmem + lane_off, dX);
@@ -566,9 +604,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
                 }
                 __syncwarp();
                 mine = wait_mma() && mine;
-                float v[16];
-                tc::tmem_ld16(tmem + lane_off, v);
-                dbacc[0] += v[0];
+                if (wg == 0) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + lane_off, v);
+                    dbacc[0] += v[0];
+                }
                 mine = sync_all(mine);
             }
             ok = mine;
@@ -581,26 +621,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdL
         // flush: dW of hidden layers from TMEM, dW_0 / dW_{L-1} / db from registers
         for (int l = 1; l <= L - 2; ++l) {
             const int Kin = net.w[l];
-            for (int c0 = 0; c0 < Kin; c0 += 32) {
+            for (int c0 = 32 * wg; c0 < Kin; c0 += 64) {
                 float v[32];
                 tc::tmem_ld32(tmem + lane_off + T.colW[l] + c0, v);
-                if (tid < net.w[l + 1])
-                    for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[l][tid * Kin + c0 + j], v[j]);
+                if (t < net.w[l + 1])
+                    for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[l][t * Kin + c0 + j], v[j]);
             }
         }
-        if (tid < net.w[1])
-            for (int j = 0; j < net.w[0]; ++j) atomicAdd(&gr.W[0][tid * net.w[0] + j], acc0[j]);
-        if (tid < net.w[L - 1])
-            for (int c = 0; c < net.w[L]; ++c) atomicAdd(&gr.W[L - 1][c * net.w[L - 1] + tid], accL[c]);
-        for (int l = 0; l <= L - 2; ++l)
-            if (gr.b[l] && tid < net.w[l + 1]) atomicAdd(&gr.b[l][tid], dbacc[l]);
+        if (t < net.w[1])
+            for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[0][t * net.w[0] + 32 * wg + j], acc0[j]);
+        if (wg == 0) {
+            if (t < net.w[L - 1])
+                for (int c = 0; c < net.w[L]; ++c) atomicAdd(&gr.W[L - 1][c * net.w[L - 1] + t], accL[c]);
+            for (int l = 0; l <= L - 2; ++l)
+                if (gr.b[l] && t < net.w[l + 1]) atomicAdd(&gr.b[l][t], dbacc[l]);
+        }
         __syncthreads();
         if (gr.b[L - 1] && tid < net.w[L]) atomicAdd(&gr.b[L - 1][tid], sdbL[tid]);
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (tid < 32) tc::tmem_dealloc(tmem, 512);
 }
 
 }  // namespace sssgs
@@ -646,9 +688,9 @@ int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     if (T.total > 227 * 1024) return SSSGS_ERR_UNSUPPORTED;
     cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
     int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
-    k_mlp_fwd_tc<<<grid, TC_THREADS, T.total, (cudaStream_t)stream>>>(net, d_pairs, n_pairs, n, *scene, out,
-                                                                        d_status);
+    int grid = (int)std::min<int64_t>((tiles + 1) / 2, (int64_t)sm_count());
+    k_mlp_fwd_tc<<<grid, 2 * TC_THREADS, T.total, (cudaStream_t)stream>>>(net, d_pairs, n_pairs, n, *scene, out,
+                                                                            d_status);
     sssgs::note_launches(1);
     return launch_status();
 }
@@ -678,7 +720,7 @@ int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
     int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
-    k_mlp_bwd_tc<<<grid, TC_THREADS, T.total, st>>>(net, T, gimg, d_pairs, n_pairs, n, *scene, drec, *grad,
+    k_mlp_bwd_tc<<<grid, 2 * TC_THREADS, T.total, st>>>(net, T, gimg, d_pairs, n_pairs, n, *scene, drec, *grad,
                                                     dx_items, d_status);
     sssgs::note_launches(1);
     return launch_status();
