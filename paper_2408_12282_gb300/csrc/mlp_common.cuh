@@ -89,4 +89,69 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
     dx[2] = dmu[2] + bo.z + bi.z;
 }
 
+// PE6 input (64 features, fixed layout) with compile-time indices, so the
+// row stays in registers.
+__device__ __forceinline__ void build_input_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g, float (&x)[64]) {
+    const float m0 = __ldg(sc.mu + 3 * g), m1 = __ldg(sc.mu + 3 * g + 1), m2 = __ldg(sc.mu + 3 * g + 2);
+    const float n0 = __ldg(sc.normal + 3 * g), n1 = __ldg(sc.normal + 3 * g + 1), n2 = __ldg(sc.normal + 3 * g + 2);
+    const float vv = __ldg(sc.vis + g);
+    const float3 C = cam_center(P);
+    const float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
+    const float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    const float mm[3] = {m0, m1, m2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float sn, cs;
+            sincospif(ldexpf(mm[c], k), &sn, &cs);
+            x[6 * k + c] = sn;
+            x[6 * k + 3 + c] = cs;
+        }
+    }
+    x[36] = m0; x[37] = m1; x[38] = m2;
+    x[39] = wo.x; x[40] = wo.y; x[41] = wo.z;
+    x[42] = wi.x; x[43] = wi.y; x[44] = wi.z;
+    x[45] = n0; x[46] = n1; x[47] = n2;
+    x[48] = li;
+    x[49] = vv;
+#pragma unroll
+    for (int k = 50; k < 64; ++k) x[k] = 0.f;
+}
+
+// Backward of build_input_pe6: dX (64) -> dx[7] = (d mu, d n, d v).
+__device__ __forceinline__ void input_backward_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g,
+                                                   const float (&dX)[64], float (&dx)[7]) {
+    const float m0 = __ldg(sc.mu + 3 * g), m1 = __ldg(sc.mu + 3 * g + 1), m2 = __ldg(sc.mu + 3 * g + 2);
+    const float3 C = cam_center(P);
+    const float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
+    const float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    const float mm[3] = {m0, m1, m2};
+    float dmu[3] = {dX[36], dX[37], dX[38]};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float f = ldexpf(kPi, k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float sn, cs;
+            sincospif(ldexpf(mm[c], k), &sn, &cs);
+            dmu[c] += f * (dX[6 * k + c] * cs - dX[6 * k + 3 + c] * sn);
+        }
+    }
+    dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
+    const float3 go = make_float3(dX[39], dX[40], dX[41]);
+    const float3 gi = make_float3(dX[42], dX[43], dX[44]);
+    const float3 bo = (-1.f / lo) * (go - dot3(wo, go) * wo);
+    const float3 bi = (-1.f / li) * (gi - dot3(wi, gi) * wi);
+    dx[0] = dmu[0] + bo.x + bi.x;
+    dx[1] = dmu[1] + bo.y + bi.y;
+    dx[2] = dmu[2] + bo.z + bi.z;
+    dx[3] = dX[45]; dx[4] = dX[46]; dx[5] = dX[47];
+    dx[6] = dX[49];
+}
+
 }  // namespace sssgs

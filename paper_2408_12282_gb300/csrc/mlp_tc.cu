@@ -140,19 +140,19 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, co
     uint32_t phase = 0;
     bool ok = true;
     const int64_t n_tiles = (n_items + TC_ROWS - 1) / TC_ROWS;
-    const int K0 = net.w[0];
     for (int64_t tile = 2 * (int64_t)blockIdx.x + wg; tile < n_tiles && ok; tile += 2 * (int64_t)gridDim.x) {
         const int64_t m = tile * TC_ROWS + t;
         {
-            float x[TC_MAXW];
+            float x[64];
 #pragma unroll
             for (int k = 0; k < 64; ++k) x[k] = 0.f;
             if (m < n_items) {
                 const int p = pair_lookup(s_off, pairs, n_pairs, m);
                 const sssgs_pair& P = pairs[p];
-                build_input(net, P, sc, P.g_begin + (m - P.item_offset), x);
+                build_input_pe6(P, sc, P.g_begin + (m - P.item_offset), x);
             }
-            for (int c = 0; c < K0; c += 8) store8_bf16(sA, t, c, K0, x + c);
+#pragma unroll
+            for (int c = 0; c < 64; c += 8) store8_bf16(sA, t, c, 64, x + c);
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -406,8 +406,9 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             float x[64];
 #pragma unroll
             for (int k = 0; k < 64; ++k) x[k] = 0.f;
-            if (valid) build_input(net, pairs[pidx], sc, gidx, x);
-            for (int c = 0; c < net.w[0]; c += 8) store8_bf16(smem + T.offH[0], t, c, net.w[0], x + c);
+            if (valid) build_input_pe6(pairs[pidx], sc, gidx, x);
+#pragma unroll
+            for (int c = 0; c < 64; c += 8) store8_bf16(smem + T.offH[0], t, c, 64, x + c);
         }
         ok = sync_all(true);
         // ---------------- forward recompute
@@ -587,7 +588,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                     tc::tmem_ld32(tmem + lane_off + 32, dX + 32);
                     if (valid) {
                         float dx[7];
-                        input_backward(net, pairs[pidx], sc, gidx, dX, dx);
+                        input_backward_pe6(pairs[pidx], sc, gidx, dX, dx);
+#pragma unroll
                         for (int k = 0; k < 7; ++k) dx_items[7 * m + k] += dx[k];
                     }
                 }
