@@ -175,6 +175,8 @@ def _config(args):
         "c3": "300K Gaussians on a seeded SH blob, 1 view/light pair at 800x800, PE6 MLP 64-128x4-4",
         "c2": "100K Gaussians on a seeded SH blob, 1 pair at 512x512, MLP 9-64x3-4",
         "c1": "1,024 Gaussians in a shell, 1 pair at 128x128, MLP 9-32x2-4",
+        "c5": "8 blob scenes of 50K-1M Gaussians x 8 view/light pairs each, resolutions drawn from "
+              "{400,800,1200,1600}^2, PE6 MLP 64-128x4-4",
     }
     return {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
             "loss": "L1 vs target rendered from perturbed parameters",
@@ -253,8 +255,9 @@ def run_ours(args):
     table = r.table
     n_pairs = table.n
     # target images from the perturbed scene (untimed set-up)
-    tgt_scene = wl.target_scene or sg.perturbed(wl.scenes[0], 4242 + rank)
-    wl_t = sg.Workload(wl.name, [tgt_scene], wl.pairs, wl.mlp, wl.tile)
+    tgt_scenes = ([wl.target_scene] if wl.target_scene is not None and len(wl.scenes) == 1 else
+                  [sg.perturbed(s, 4242 + 97 * rank + i) for i, s in enumerate(wl.scenes)])
+    wl_t = sg.Workload(wl.name, tgt_scenes, wl.pairs, wl.mlp, wl.tile)
     rt = PL.renderer_for_workload(wl_t, precision=precision, tile=args.tile)
     rt.fit_capacity()
     rt.forward()
@@ -349,7 +352,7 @@ def run_ours(args):
             a = e_z if s == "render_bwd" else ev[i]
             stage_ms[s] += a.elapsed_time(ev[i + 1]) / reps
     n_items, n_pixels = table.n_items, table.n_pixels
-    n_gauss = wl.scenes[0].N
+    n_gauss = sum(sc.N for sc in wl.scenes)
     contrib_f, evals_f = (int(x) // reps for x in stats_f.tolist())
     contrib_b, evals_b = (int(x) // reps for x in stats_b.tolist())
     alu_flops = {

@@ -266,3 +266,29 @@ def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=No
     table = PairTable(pairs, cfg, offs, counts, device)
     mlp = mlp_to_device(wl.mlp, precision, device)
     return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device)
+
+
+def autotune_tile(wl, candidates=(16, 8), precision=None, steps=2, device="cuda", capacity_slack=1.15):
+    """Pick the tile edge for a workload by timing full forward + backward steps
+    of each candidate on the device (CUDA events). Returns (best_tile, {tile: ms})."""
+    timings = {}
+    for tile in candidates:
+        r = renderer_for_workload(wl, precision=precision, tile=tile, device=device)
+        r.fit_capacity(capacity_slack)
+        dimg = torch.full((r.table.n_pixels, 3), 1e-6, device=device)
+        r.forward()
+        r.backward(dimg=dimg)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            r.forward()
+            r.backward(dimg=dimg)
+        e1.record()
+        torch.cuda.synchronize()
+        timings[tile] = e0.elapsed_time(e1) / steps
+        del r
+        torch.cuda.empty_cache()
+    best = min(timings, key=timings.get)
+    return best, timings

@@ -296,9 +296,10 @@ def _hemisphere_dir(rng, zmin=0.15):
             return v
 
 
-def make_workload(name: str, *, N: int | None = None, res: int | None = None,
+def make_workload(name: str, *, N: int | None = None, res=None,
                   n_pairs: int | None = None, seed_offset: int = 0) -> Workload:
-    """Build configuration `name` ("c1".."c5"); N/res/n_pairs shrink it for tests."""
+    """Build configuration `name` ("c1".."c5"); N/res/n_pairs shrink it for tests.
+    For c5, `res` may be a tuple of resolutions to draw from."""
     idx = int(name[1])
     seed = idx * 1000 + seed_offset
     rng = np.random.Generator(np.random.PCG64(seed + 7))
@@ -351,8 +352,9 @@ def make_workload(name: str, *, N: int | None = None, res: int | None = None,
             scenes.append(blob_scene(seed + 100 * s, c))
             cams = fibonacci_sphere(per, 3.0, upper=True)
             lights = fibonacci_sphere(per, 4.0)
+            choices = list(res) if isinstance(res, (tuple, list)) else ([res] if res else [400, 800, 1200, 1600])
             for k in range(per):
-                r = res or int(rng.choice([400, 800, 1200, 1600]))
+                r = int(rng.choice(choices))
                 rc = (k + s) % per
                 pairs.append(_make_pair(cams[k], lights[rc], r, r, scene=s))
         mlp = mlp_spec(seed + 11, "pe6", [128, 128, 128, 128], precision="bf16")

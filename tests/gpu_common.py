@@ -57,8 +57,10 @@ def run_gpu(wl, precision=B.FP32, fused=True, tile=None, dimg=None, target=None,
 
 
 def oracle_batch(wl, pair_ids, dimg=None, bf16=False):
-    """Oracle over several pairs of one-scene workload; dimg is pair-major."""
+    """Oracle over several pairs; dimg is pair-major. Scene gradients are
+    returned concatenated over the workload's scenes (the GPU layout)."""
     imgs, gbufs, margins, ncs = [], [], [], []
+    offs = np.cumsum([0] + [s.N for s in wl.scenes])
     grads = None
     dW = db = None
     off = 0
@@ -70,15 +72,15 @@ def oracle_batch(wl, pair_ids, dimg=None, bf16=False):
         imgs.append(r["img"]); gbufs.append(r["gbuf"]); margins.append(r["margin"]); ncs.append(r["ncontrib"])
         if di is not None:
             if grads is None:
-                grads = {k: v.copy() for k, v in r["grads"].items()}
-                dW = [w.copy() for w in r["dW"]]
-                db = [b.copy() for b in r["db"]]
-            else:
-                for k in grads:
-                    grads[k] += r["grads"][k]
-                for l in range(len(dW)):
-                    dW[l] += r["dW"][l]
-                    db[l] += r["db"][l]
+                grads = {k: np.zeros((offs[-1],) + v.shape[1:]) for k, v in r["grads"].items()}
+                dW = [np.zeros_like(w) for w in r["dW"]]
+                db = [np.zeros_like(b) for b in r["db"]]
+            a, b = offs[pair.scene], offs[pair.scene + 1]
+            for k in grads:
+                grads[k][a:b] += r["grads"][k]
+            for l in range(len(dW)):
+                dW[l] += r["dW"][l]
+                db[l] += r["db"][l]
         off += npx
     out = dict(img=np.concatenate(imgs), gbuf=np.concatenate(gbufs), margin=np.concatenate(margins),
                ncontrib=np.concatenate(ncs))

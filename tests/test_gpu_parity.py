@@ -281,3 +281,25 @@ def test_work_counters():
     assert cf == cb
     assert abs(cf - n_ref) <= 0.001 * n_ref
     assert ef >= cf and eb >= cb
+
+
+def test_uneven_batch_several_scenes_and_resolutions():
+    """The uneven configuration shape: several scenes of different sizes, each
+    with its own pairs, images of different sizes, one batch."""
+    wl = sg.make_workload("c5", N=20000, res=(40, 64, 88), n_pairs=2)
+    for p in wl.pairs:
+        assert p.W in (40, 64, 88)
+    pid = list(range(len(wl.pairs)))
+    ref0, dimg = _masked_dimg(wl, pid, seed=31)
+    ref = oracle_batch(wl, pid, dimg=dimg)
+    g = run_gpu(wl, precision=B.FP32, dimg=dimg)
+    fl = flagged(ref0["margin"])
+    assert_image_close(g["img"], ref0["img"], fl)
+    assert_grads_close(g["grads"], ref["grads"], SCENE_KEYS)
+    assert len({(p.W, p.H) for p in wl.pairs}) > 1 and len(wl.scenes) == 8
+
+
+def test_autotuner_picks_a_measured_candidate():
+    wl = sg.make_workload("c4", N=3000, res=64, n_pairs=2)
+    best, t = PL.autotune_tile(wl, candidates=(16, 8), precision=B.FP32, steps=1)
+    assert best in (8, 16) and t[best] == min(t.values())
