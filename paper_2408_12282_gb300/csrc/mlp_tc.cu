@@ -179,13 +179,13 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, co
             if (got) {
                 const float* bl = sbias + T.biasOff[l];
                 if (l < net.L - 1) {
-                    for (int c0 = 0; c0 < N; c0 += 32) {
-                        float v[32];
-                        tc::tmem_ld32(lane_base + c0, v);
+                    for (int c0 = 0; c0 < N; c0 += 64) {
+                        float v[64];
+                        tc::tmem_ld64(lane_base + c0, v);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
+                        for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) store8_bf16(sA, t, c0 + 8 * q, N, v + 8 * q);
+                        for (int q = 0; q < 8; ++q) store8_bf16(sA, t, c0 + 8 * q, N, v + 8 * q);
                     }
                 } else {
                     float v[16];
@@ -431,13 +431,23 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             const float* bl = sbias + T.biasOff[l];
             if (l < L - 1) {
                 const int N = net.w[l + 1];
-                for (int c0 = wg * (N / 2); c0 < (wg + 1) * (N / 2); c0 += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tmem + lane_off + c0, v);
+                if (N == 128) {
+                    const int c0 = wg * 64;
+                    float v[64];
+                    tc::tmem_ld64(tmem + lane_off + c0, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
+                    for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) store8_bf16(smem + T.offH[l + 1], t, c0 + 8 * q, N, v + 8 * q);
+                    for (int q = 0; q < 8; ++q) store8_bf16(smem + T.offH[l + 1], t, c0 + 8 * q, N, v + 8 * q);
+                } else {
+                    for (int c0 = wg * (N / 2); c0 < (wg + 1) * (N / 2); c0 += 32) {
+                        float v[32];
+                        tc::tmem_ld32(tmem + lane_off + c0, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) store8_bf16(smem + T.offH[l + 1], t, c0 + 8 * q, N, v + 8 * q);
+                    }
                 }
             } else if (wg == 0) {
                 // heads and their gradient: dZ_L (padded to 16 columns), db_{L-1}
@@ -584,8 +594,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 } else if (wg == 0) {
                     // network-input gradient (64 columns) -> (d mu, d n, d v)
                     float dX[64];
-                    tc::tmem_ld32(tmem + lane_off, dX);
-                    tc::tmem_ld32(tmem + lane_off + 32, dX + 32);
+                    tc::tmem_ld64(tmem + lane_off, dX);
                     if (valid) {
                         float dx[7];
                         input_backward_pe6(pairs[pidx], sc, gidx, dX, dx);

@@ -49,16 +49,11 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the mbarrier phase with parity `parity`; gives up after ~1 s and
-// returns false (the caller records a timeout and stops).
+// Wait for the mbarrier phase with parity `parity`. The limit is counted in
+// SM clock cycles (cheap to read): about 2 s at the maximum clock. Returns
+// false when it runs out (the caller records a timeout and stops).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    uint64_t t0 = 0;
+    long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
@@ -69,8 +64,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (it == 0) t0 = globaltimer();
-        else if ((it & 63) == 0 && globaltimer() - t0 > 1000000000ull) return false;
+        if (it == 0) t0 = clock64();
+        else if ((it & 15) == 0 && clock64() - t0 > 4000000000ll) return false;
     }
 }
 
@@ -130,6 +125,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 64 consecutive FP32 columns (two x32 loads, one wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+    uint32_t r[64];
+#define SSSGS_LD32(OFF, BASE)                                                                              \
+    asm volatile(                                                                                          \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                          \
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                                        \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                        \
+        : "=r"(r[BASE + 0]), "=r"(r[BASE + 1]), "=r"(r[BASE + 2]), "=r"(r[BASE + 3]), "=r"(r[BASE + 4]),   \
+          "=r"(r[BASE + 5]), "=r"(r[BASE + 6]), "=r"(r[BASE + 7]), "=r"(r[BASE + 8]), "=r"(r[BASE + 9]),   \
+          "=r"(r[BASE + 10]), "=r"(r[BASE + 11]), "=r"(r[BASE + 12]), "=r"(r[BASE + 13]),                  \
+          "=r"(r[BASE + 14]), "=r"(r[BASE + 15]), "=r"(r[BASE + 16]), "=r"(r[BASE + 17]),                  \
+          "=r"(r[BASE + 18]), "=r"(r[BASE + 19]), "=r"(r[BASE + 20]), "=r"(r[BASE + 21]),                  \
+          "=r"(r[BASE + 22]), "=r"(r[BASE + 23]), "=r"(r[BASE + 24]), "=r"(r[BASE + 25]),                  \
+          "=r"(r[BASE + 26]), "=r"(r[BASE + 27]), "=r"(r[BASE + 28]), "=r"(r[BASE + 29]),                  \
+          "=r"(r[BASE + 30]), "=r"(r[BASE + 31])                                                           \
+        : "r"(taddr + OFF));
+    SSSGS_LD32(0, 0)
+    SSSGS_LD32(32, 32)
+#undef SSSGS_LD32
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // 16 consecutive FP32 columns of this thread's TMEM lane.
