@@ -281,8 +281,7 @@ def run_ours(args):
             r.forward()
             r.backward(target=target, l1_scale=l1_scale)
         if world > 1:
-            for g in grads_flat:
-                dist.all_reduce(g)
+            PL.allreduce_gradients(grads_flat)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -432,8 +431,7 @@ def run_ours(args):
                 r.forward()
                 r.backward(target=target, l1_scale=l1_scale)
             if world > 1:
-                for g in grads_flat:
-                    dist.all_reduce(g)
+                PL.allreduce_gradients(grads_flat)
             for k2, v in host_out.items():
                 v.copy_(r.grads[k2], non_blocking=True)
         e2e_step()

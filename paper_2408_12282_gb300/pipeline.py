@@ -292,3 +292,20 @@ def autotune_tile(wl, candidates=(16, 8), precision=None, steps=2, device="cuda"
         torch.cuda.empty_cache()
     best = min(timings, key=timings.get)
     return best, timings
+
+
+# ---------------------------------------------------------------------- data parallel
+
+def shard_pairs(n_pairs: int, rank: int, world: int) -> list:
+    """Pairs owned by `rank` when a batch of view/light pairs is split over
+    `world` processes (round-robin, so uneven batches stay balanced)."""
+    return list(range(rank, n_pairs, world))
+
+
+def allreduce_gradients(tensors, group=None):
+    """Sum gradients over the process group: the one exchange of a
+    data-parallel step (renders of different pairs are independent; the
+    parameters are shared)."""
+    import torch.distributed as dist
+    for t in tensors:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)

@@ -1,0 +1,80 @@
+"""Full-size parity, in the launch configuration the benchmark times.
+
+* The 300K-Gaussian 800x800 pair (tensor-core network, fused kernels): every
+  pixel and every gradient tensor against the oracle with the BF16-emulating
+  network (gates of test_gpu_tc: bf16 decision flips are the only expected
+  differences).
+* The 64-pair 300K batch replayed from a captured CUDA graph with the fused
+  L1 loss, as in bench.py: sampled pixels of two pairs against the oracle, and
+  those pairs bit-identical to single-pair renders.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenegen as sg
+from gpu_common import flagged, grad_errors, oracle_batch, run_gpu
+from paper_2408_12282_gb300 import binding as B
+from paper_2408_12282_gb300 import pipeline as PL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(gpu_lib):
+    return gpu_lib
+
+
+def test_full_300k_800_pair_image_and_gradients():
+    wl = sg.make_workload("c3")
+    ref0 = oracle_batch(wl, [0], bf16=True)
+    fl = flagged(ref0["margin"])
+    dimg = sg.random_dimg(123, ref0["img"].shape[0])
+    dimg[fl] = 0.0
+    ref = oracle_batch(wl, [0], dimg=dimg, bf16=True)
+    g = run_gpu(wl, precision=B.BF16, dimg=dimg)
+    ok = ~fl
+    e = np.abs(g["img"][ok] - ref0["img"][ok]).max(axis=1)
+    print(f"\nfull 300K/800 pair: {fl.mean():.2%} flagged; image max {e.max():.2e} p99.9 {np.quantile(e, 0.999):.2e}")
+    assert fl.mean() < 0.05
+    assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 5e-3
+    errs = {k: grad_errors(g["grads"][k], ref["grads"][k])[0] for k in PL.SCENE_KEYS}
+    errs.update({f"W{l}": grad_errors(g["dW"][l], ref["dW"][l])[0] for l in range(len(g["dW"]))})
+    print("gradient rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert all(v <= 2e-3 for v in errs.values()), errs
+
+
+def test_full_64_pair_batch_graph_replay_sampled():
+    wl = sg.make_workload("c4")
+    r = PL.renderer_for_workload(wl, precision=B.BF16)
+    r.fit_capacity()
+    target = torch.zeros(r.table.n_pixels, 3, device="cuda")
+    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * r.table.n_pixels))
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    r.check_status()
+    img = r.img.double().cpu().numpy()
+    rng = np.random.default_rng(5)
+    off = 0
+    offs = [0]
+    for p in wl.pairs:
+        offs.append(offs[-1] + p.W * p.H)
+    for p in (7, 41):
+        pair = wl.pairs[p]
+        pix = O.all_pixels(pair.W, pair.H)
+        sel = rng.choice(len(pix), 1500, replace=False)
+        res = O.render_pair(wl.scenes[0], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=True)
+        fl = flagged(res["margin"])
+        got = img[offs[p] + sel]
+        e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
+        print(f"\npair {p}: {fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
+        assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
+        one = PL.renderer_for_workload(wl, precision=B.BF16, pair_slice=slice(p, p + 1))
+        one.fit_capacity()
+        one.forward()
+        torch.cuda.synchronize()
+        assert torch.equal(one.img, r.img[offs[p]:offs[p + 1]])
+        del one
+        torch.cuda.empty_cache()
