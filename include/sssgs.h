@@ -223,7 +223,7 @@ int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_
  * at zero); calls that overlap on the GPU race, so serialise them. */
 #define SSSGS_STATIC_MAX_ITEMS 65536
 #define SSSGS_STATIC_MAX_INSTANCES 524288
-#define SSSGS_STATIC_SCRATCH_BYTES 8912896
+#define SSSGS_STATIC_SCRATCH_BYTES 9437184
 int sssgs_bin_sort_static(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                           int n_pairs, const float* rec, const int32_t* rect, int64_t capacity,
                           uint32_t* vals, uint32_t* ranges, int64_t* d_count, int32_t* d_status,

@@ -127,12 +127,12 @@ static void exclusive_scan(const T* in, T* out, int64_t L, T* part, cudaStream_t
 
 // ---------------------------------------------------------------- radix pass
 
-template <typename K>
+template <typename K, int NB>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, const int64_t* d_n, int64_t cap,
                                                         int shift, uint32_t mask, uint32_t* __restrict__ hist,
                                                         int nblocks) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[NB];
+    for (int d = threadIdx.x; d < NB; d += RS_THREADS) h[d] = 0;
     __syncthreads();
     int64_t n = eff_n(d_n, cap);
     int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -140,29 +140,30 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
     for (int k = 0; k < RS_ITEMS; ++k) {
         int64_t idx = base + (int64_t)k * RS_THREADS + threadIdx.x;
         bool ok = idx < n;
-        uint32_t d = ok ? ((uint32_t)(keys[idx] >> shift) & mask) : 0x100u;
+        uint32_t d = ok ? ((uint32_t)(keys[idx] >> shift) & mask) : 0xFFFFu;
         uint32_t peers = __match_any_sync(SSSGS_FULL, d);
         if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < NB; d += RS_THREADS) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
 }
 
-template <typename K>
+template <typename K, int NB>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            const int64_t* d_n, int64_t cap, int shift, uint32_t mask,
                                                            const uint32_t* __restrict__ hoff, int nblocks) {
+    constexpr int DPT = NB / RS_THREADS;          // digits per thread in the digit scans
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* skey = reinterpret_cast<K*>(smem_raw);
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + RS_TILE);
-    uint32_t* wcnt = sval + RS_TILE;               // [RS_WARPS][256]
-    uint32_t* bstart = wcnt + RS_WARPS * 256;      // [256]
-    uint32_t* gbase = bstart + 256;                // [256]
-    uint32_t* sh = gbase + 256;                    // [RS_WARPS]
+    uint32_t* wcnt = sval + RS_TILE;               // [RS_WARPS][NB]
+    uint32_t* bstart = wcnt + RS_WARPS * NB;       // [NB]
+    uint32_t* gbase = bstart + NB;                 // [NB]
+    uint32_t* sh = gbase + NB;                     // [RS_WARPS]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) wcnt[i] = 0;
-    gbase[tid] = hoff[(int64_t)tid * nblocks + blockIdx.x];
+    for (int i = tid; i < RS_WARPS * NB; i += RS_THREADS) wcnt[i] = 0;
+    for (int d = tid; d < NB; d += RS_THREADS) gbase[d] = hoff[(int64_t)d * nblocks + blockIdx.x];
     __syncthreads();
     const int64_t n = eff_n(d_n, cap);
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -177,23 +178,36 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
         bool ok = idx < n;
         key[j] = ok ? kin[idx] : K(0);
         val[j] = ok ? vin[idx] : 0u;
-        uint32_t d = ok ? ((uint32_t)(key[j] >> shift) & mask) : 0x100u;
+        uint32_t d = ok ? ((uint32_t)(key[j] >> shift) & mask) : 0xFFFFu;
         uint32_t peers = __match_any_sync(SSSGS_FULL, d);
-        rank[j] = ok ? wcnt[warp * 256 + d] + __popc(peers & lt) : 0u;
+        rank[j] = ok ? wcnt[warp * NB + d] + __popc(peers & lt) : 0u;
         __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wcnt[warp * 256 + d] += __popc(peers);
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp * NB + d] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    {   // digit `tid`: exclusive over warps, then exclusive over digits
-        uint32_t run = 0;
-        for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = wcnt[w * 256 + tid];
-            wcnt[w * 256 + tid] = run;
-            run += c;
+    {   // digits [DPT*tid, DPT*tid + DPT): exclusive over warps, then over digits
+        uint32_t tot[DPT];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = DPT * tid + q;
+            uint32_t run = 0;
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = wcnt[w * NB + d];
+                wcnt[w * NB + d] = run;
+                run += c;
+            }
+            tot[q] = run;
+            sum += run;
         }
-        uint32_t inc = block_incl_scan(run, sh);
-        bstart[tid] = inc - run;
+        uint32_t inc = block_incl_scan(sum, sh);
+        uint32_t start = inc - sum;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            bstart[DPT * tid + q] = start;
+            start += tot[q];
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -201,7 +215,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
         int64_t idx = wbase + j * 32 + lane;
         if (idx < n) {
             uint32_t d = (uint32_t)(key[j] >> shift) & mask;
-            uint32_t lpos = bstart[d] + wcnt[warp * 256 + d] + rank[j];
+            uint32_t lpos = bstart[d] + wcnt[warp * NB + d] + rank[j];
             skey[lpos] = key[j];
             sval[lpos] = val[j];
         }
@@ -217,39 +231,54 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     }
 }
 
-template <typename K>
+template <typename K, int NB>
 static size_t scatter_smem() {
-    return (size_t)RS_TILE * (sizeof(K) + 4) + (RS_WARPS * 256 + 256 + 256 + RS_WARPS) * 4;
+    return (size_t)RS_TILE * (sizeof(K) + 4) + (size_t)(RS_WARPS * NB + 2 * NB + RS_WARPS) * 4;
 }
 
-// Stable sort of (key, value) pairs over `bits` low key bits. Buffers ping-pong;
-// returns the index (0: kA/vA, 1: kB/vB) holding the result.
+template <typename K, int NB>
+static void radix_pass(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, const int64_t* d_n, int64_t cap,
+                       int shift, int nb, uint32_t* hist, uint32_t* part32, int nblocks, cudaStream_t st) {
+    const uint32_t mask = (1u << nb) - 1u;
+    const size_t sm = scatter_smem<K, NB>();
+    cudaFuncSetAttribute(k_rs_scatter<K, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_rs_hist<K, NB><<<nblocks, RS_THREADS, 0, st>>>(kin, d_n, cap, shift, mask, hist, nblocks);
+    sssgs::note_launches(1);
+    exclusive_scan<uint32_t>(hist, hist, (int64_t)NB * nblocks, part32, st);
+    k_rs_scatter<K, NB><<<nblocks, RS_THREADS, sm, st>>>(kin, vin, kout, vout, d_n, cap, shift, mask, hist, nblocks);
+    sssgs::note_launches(1);
+}
+
+// Stable sort of (key, value) pairs over `bits` low key bits, in the fewest
+// passes of at most 10 bits (<= 1024 buckets), bits spread evenly. Buffers
+// ping-pong; returns the index (0: kA/vA, 1: kB/vB) holding the result.
 template <typename K>
 static int radix_sort(K* kA, uint32_t* vA, K* kB, uint32_t* vB, const int64_t* d_n, int64_t cap, int bits,
                       uint32_t* hist, uint32_t* part32, cudaStream_t st) {
     int nblocks = (int)((cap + RS_TILE - 1) / RS_TILE);
     if (nblocks == 0) return 0;
-    size_t sm = scatter_smem<K>();
-    cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int np = (bits + 9) / 10;
+    const int per = (bits + np - 1) / np;
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
-        int nb = bits - shift < 8 ? bits - shift : 8;
-        uint32_t mask = (1u << nb) - 1u;
+    for (int shift = 0; shift < bits; shift += per) {
+        const int nb = bits - shift < per ? bits - shift : per;
         K* kin = cur ? kB : kA;
         uint32_t* vin = cur ? vB : vA;
         K* kout = cur ? kA : kB;
         uint32_t* vout = cur ? vA : vB;
-        k_rs_hist<K><<<nblocks, RS_THREADS, 0, st>>>(kin, d_n, cap, shift, mask, hist, nblocks);
-        sssgs::note_launches(1);
-        exclusive_scan<uint32_t>(hist, hist, (int64_t)256 * nblocks, part32, st);
-        k_rs_scatter<K><<<nblocks, RS_THREADS, sm, st>>>(kin, vin, kout, vout, d_n, cap, shift, mask, hist, nblocks);
-        sssgs::note_launches(1);
+        if (nb <= 8) radix_pass<K, 256>(kin, vin, kout, vout, d_n, cap, shift, nb, hist, part32, nblocks, st);
+        else if (nb == 9) radix_pass<K, 512>(kin, vin, kout, vout, d_n, cap, shift, nb, hist, part32, nblocks, st);
+        else radix_pass<K, 1024>(kin, vin, kout, vout, d_n, cap, shift, nb, hist, part32, nblocks, st);
         cur ^= 1;
     }
     return cur;
 }
 
-static int passes(int bits) { return (bits + 7) / 8; }
+static int passes(int bits) {
+    const int np = (bits + 9) / 10;
+    const int per = (bits + np - 1) / np;
+    return (bits + per - 1) / per;
+}
 
 // ---------------------------------------------------------------- binning kernels
 
@@ -338,8 +367,8 @@ BinLayout bin_layout(int64_t n_items, int64_t cap) {
     L.ikB = o; o += al(4 * (size_t)cap);
     L.ivW = o; o += al(4 * (size_t)cap);
     int64_t nb = std::max((n_items + RS_TILE - 1) / RS_TILE, (cap + RS_TILE - 1) / RS_TILE);
-    L.hist = o; o += al(4 * (size_t)256 * (size_t)std::max<int64_t>(nb, 1));
-    int64_t np = std::max<int64_t>((256 * nb + SC_CHUNK - 1) / SC_CHUNK, (n_items + 1 + SC_CHUNK - 1) / SC_CHUNK);
+    L.hist = o; o += al(4 * (size_t)1024 * (size_t)std::max<int64_t>(nb, 1));
+    int64_t np = std::max<int64_t>((1024 * nb + SC_CHUNK - 1) / SC_CHUNK, (n_items + 1 + SC_CHUNK - 1) / SC_CHUNK);
     L.part32 = o; o += al(4 * (size_t)(np + 1));
     L.part64 = o; o += al(8 * (size_t)(np + 1));
     L.total = o;

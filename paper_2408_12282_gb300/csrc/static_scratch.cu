@@ -7,7 +7,7 @@
 // point uses a scratch array compiled into the library instead.
 //
 // The scratch is a file-scope __device__ array of SSSGS_STATIC_SCRATCH_BYTES
-// (8.5 MiB). Every GPU that loads the library holds it until the process
+// (9 MiB). Every GPU that loads the library holds it until the process
 // exits. In host code the array's name only stands for the symbol, not for a
 // device address, so its address is looked up with cudaGetSymbolAddress, once
 // per device, on the first call made while that device is current, and cached.
