@@ -516,13 +516,19 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
     }
 }
 
-
-// ---------------------------------------------------------------- composite backward, 2 px / thread
+// ---------------------------------------------------------------- composite backward, one warp per sub-tile
 //
-// 16 x 16 tiles with 128 threads: each warp owns an 8 x 8 sub-tile, each lane
-// two vertically adjacent pixels. Both pixels' gradient contributions to a
-// splat are summed in registers before the warp reduction, which halves the
-// shared-memory reduction traffic and the record broadcasts per pixel.
+// Used for 16 x 16 tiles with the fused upstream gradient. Each block is a
+// single warp that owns one 8 x 8 sub-tile of a 16 x 16 tile, each lane two
+// vertically adjacent pixels; both pixels' contributions to a splat are summed
+// in registers before the warp reduction. The hardware block scheduler
+// balances work at warp granularity and no warp ever waits for another. The
+// warp walks its tile's list back to front in batches of 32 splats. While it
+// processes batch i, the records of batch i+1 are in flight into the other
+// half of a shared-memory double buffer (cp.async, no registers held) and the
+// list entries of batch i+2 are being loaded. Each lane tests its splat
+// against the sub-tile with the exact padded ellipse/box test; the warp then
+// visits only the splats that passed (ballot bits, highest position first).
 
 struct PixBwd {
     float dF[SSSGS_NF];
@@ -595,8 +601,14 @@ __device__ __forceinline__ void bwd_pixel_setup(PixBwd& p, bool inside, int64_t 
     p.Q = 0.f;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <int MODE>
-__global__ void __launch_bounds__(128, 4) k_composite_bwd2(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+__global__ void __launch_bounds__(32, 16) k_composite_bwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                          int n_pairs, const float4* __restrict__ rec,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint2* __restrict__ ranges,
@@ -608,21 +620,22 @@ __global__ void __launch_bounds__(128, 4) k_composite_bwd2(sssgs_cfg cfg, const 
                                                          const float* __restrict__ weight, float l1_scale,
                                                          float* __restrict__ drec,
                                                          unsigned long long* __restrict__ stats) {
-    constexpr int TILE = 16, B = 128, NG = 6 + SSSGS_NF, RS = 36;
-    extern __shared__ float4 s_rec[];                       // [6][B], item ids, masks, reduction scratch
-    uint32_t* s_item = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
-    uint32_t* s_mask = s_item + B;
-    float* s_red = reinterpret_cast<float*>(s_mask + B) + (threadIdx.x >> 5) * (NG * RS);
+    constexpr int TILE = 16, NG = 6 + SSSGS_NF, RS = 36;
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
+    __shared__ __align__(16) float4 s_rec[2][6][32];
+    __shared__ uint32_t s_item[2][32];
+    __shared__ __align__(16) float s_red[NG * RS];
     __shared__ __align__(16) sssgs_pair sP;
-    __shared__ uint32_t s_max;
-    const int tile = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t wbit = 1u << warp;
-    if (threadIdx.x == 0) s_max = 0;
-    load_pair_shared(pairs, n_pairs, tile, &sP);
+    const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
+    const int lane = threadIdx.x;
+    if (lane < 8) {
+        const int pi = pair_of_tile(pairs, n_pairs, tile);
+        reinterpret_cast<float4*>(&sP)[lane] = reinterpret_cast<const float4*>(pairs + pi)[lane];
+    }
+    __syncwarp();
     const int lt = tile - sP.tile_offset;
-    const int i = (lt % sP.tiles_x) * TILE + (warp & 1) * 8 + (lane & 7);
-    const int j0 = (lt / sP.tiles_x) * TILE + (warp >> 1) * 8 + (lane >> 3) * 2;
+    const int bx = (lt % sP.tiles_x) * TILE + (sub & 1) * 8, by = (lt / sP.tiles_x) * TILE + (sub >> 1) * 8;
+    const int i = bx + (lane & 7), j0 = by + (lane >> 3) * 2;
     const uint2 rg = ranges[tile];
     PixBwd p[2];
 #pragma unroll
@@ -634,30 +647,50 @@ __global__ void __launch_bounds__(128, 4) k_composite_bwd2(sssgs_cfg cfg, const 
         p[q].fy = j + 0.5f;
         bwd_pixel_setup<MODE>(p[q], inside, pix, sP, cfg, gbuf, last, img, dimg, target, weight, l1_scale);
     }
-    const uint32_t mylast = max(p[0].lastc, p[1].lastc);
-    if (mylast > 0) atomicMax(&s_max, mylast);
-    __syncthreads();
-    const uint32_t maxlast = s_max;
+    const uint32_t wmax = __reduce_max_sync(SSSGS_FULL, max(p[0].lastc, p[1].lastc));
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
+    const float x0 = bx + 0.5f, y0 = by + 0.5f;
     uint32_t n_use = 0;
-    for (uint32_t b1 = maxlast; b1 > rg.x;) {
-        const uint32_t b0 = b1 - rg.x > (uint32_t)B ? b1 - B : rg.x;
-        __syncthreads();
-        const uint32_t idx = b0 + threadIdx.x;
-        if (idx < b1) {
-            const uint32_t item = vals[idx];
-            s_item[threadIdx.x] = item;
-            const float4* r = rec + 6 * (int64_t)item;
+    if (wmax > rg.x) {
+        const int nb = (int)((wmax - rg.x + 31) >> 5);
+        // Batch t covers list positions [lo(t), wmax - 32 t).
+        auto entry = [&](int t) -> uint32_t {
+            if (t >= nb) return NONE;
+            const int64_t hi = (int64_t)wmax - 32 * t, lo = max((int64_t)rg.x, hi - 32);
+            const int64_t idx = lo + lane;
+            return idx < hi ? vals[idx] : NONE;
+        };
+        auto fetch = [&](uint32_t item, int buf) {
+            if (item != NONE) {
+                const float4* r = rec + 6 * (int64_t)item;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
-            s_mask[threadIdx.x] = subtile_mask<TILE, 8, 8>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], a_min);
-        }
-        __syncthreads();
-        if (__any_sync(SSSGS_FULL, mylast > b0)) {
-            for (int k = (int)(b1 - b0) - 1; k >= 0; --k) {
-                if (!(s_mask[k] & wbit)) continue;
-                const uint32_t pos = b0 + k;
-                const float4 g0 = s_rec[k], g1 = s_rec[B + k];
+                for (int q = 0; q < 6; ++q) cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + q);
+            }
+            cp_async_commit();
+        };
+        uint32_t it0 = entry(0);
+        fetch(it0, 0);
+        uint32_t it1 = entry(1);
+        for (int t = 0; t < nb; ++t) {
+            const int buf = t & 1;
+            fetch(it1, buf ^ 1);
+            const uint32_t it2 = entry(t + 2);
+            cp_async_wait1();
+            bool pass = false;
+            if (it0 != NONE) {
+                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane];
+                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, logf(g1.y / a_min), x0, x0 + 7.f, y0,
+                                         y0 + 7.f);
+            }
+            s_item[buf][lane] = it0;
+            uint32_t bits = __ballot_sync(SSSGS_FULL, pass);
+            __syncwarp();
+            const uint32_t lo = (uint32_t)max((int64_t)rg.x, (int64_t)wmax - 32 * t - 32);
+            while (bits) {
+                const int k = 31 - __clz(bits);
+                bits ^= 1u << k;
+                const uint32_t pos = lo + k;
+                const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
                 const AlphaEval e0 = eval_alpha(g0, g1, p[0].fx, p[0].fy, a_min, a_max);
                 const AlphaEval e1 = eval_alpha(g0, g1, p[1].fx, p[1].fy, a_min, a_max);
                 const bool act0 = (pos < p[0].lastc) && e0.use;
@@ -667,8 +700,8 @@ __global__ void __launch_bounds__(128, 4) k_composite_bwd2(sssgs_cfg cfg, const 
 #pragma unroll
                 for (int c = 0; c < NG; ++c) acc[c] = 0.f;
                 if (act0 || act1) {
-                    const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
-                    const float g5 = s_rec[5 * B + k].x;
+                    const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
+                    const float g5 = s_rec[buf][5][k].x;
                     const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
                                                g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
                     if (act0) { bwd_contrib(p[0], e0, g0, g1, f, acc); ++n_use; }
@@ -685,12 +718,14 @@ __global__ void __launch_bounds__(128, 4) k_composite_bwd2(sssgs_cfg cfg, const 
                         const float4 bq = row[q];
                         a.x += bq.x; a.y += bq.y; a.z += bq.z; a.w += bq.w;
                     }
-                    atomicAdd(drec + (int64_t)SSSGS_REC * s_item[k] + lane, (a.x + a.y) + (a.z + a.w));
+                    atomicAdd(drec + (int64_t)SSSGS_REC * s_item[buf][k] + lane, (a.x + a.y) + (a.z + a.w));
                 }
                 __syncwarp();
             }
+            __syncwarp();
+            it0 = it1;
+            it1 = it2;
         }
-        b1 = b0;
     }
     if (stats) {
         unsigned long long u = n_use;
@@ -753,14 +788,12 @@ int launch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, cons
 }
 
 template <int MODE>
-int launch_bwd2(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
+int launch_bwd_warp(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
                 const uint32_t* ranges, const float* gbuf, const uint32_t* last, const float* img,
                 const float* dimg, const float* target, const float* weight, float l1, float* drec,
                 cudaStream_t st, unsigned long long* stats) {
-    const size_t sm = (size_t)6 * 128 * sizeof(float4) + (size_t)128 * 8 + (size_t)4 * (6 + SSSGS_NF) * 36 * 4;
-    cudaFuncSetAttribute(k_composite_bwd2<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_composite_bwd2<MODE><<<tiles, 128, sm, st>>>(*cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf,
-                                                   last, img, dimg, target, weight, l1, drec, stats);
+    k_composite_bwd_warp<MODE><<<4 * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf,
+                                                     last, img, dimg, target, weight, l1, drec, stats);
     sssgs::note_launches(1);
     return launch_status();
 }
@@ -775,8 +808,8 @@ int dispatch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, co
                                            target, weight, l1, drec, st, stats);
         case 16:
             if (MODE != UPSTREAM_DGBUF)
-                return launch_bwd2<MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, dimg, target, weight,
-                                         l1, drec, st, stats);
+                return launch_bwd_warp<MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, dimg, target,
+                                             weight, l1, drec, st, stats);
             return launch_bwd<16, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
                                         target, weight, l1, drec, st, stats);
         default: return SSSGS_ERR_UNSUPPORTED;   // 32x32 tiles: forward only
