@@ -254,7 +254,8 @@ int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const s
 
 /* Fused a3+a4 forward: composite then shade in one pass; writes gbuf, last, img.
  * d_stats (device uint64[2], may be NULL) accumulates the number of
- * contributions (pixel-Gaussian pairs composited) and of alpha evaluations. */
+ * contributions (pixel-Gaussian pairs composited) and the tile-list positions
+ * each pixel considered (up to the splat that stopped it, else the list end). */
 int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                      int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
                      float* gbuf, uint32_t* last, float* img, uint64_t* d_stats, sssgs_stream stream);
