@@ -146,6 +146,14 @@ __device__ __forceinline__ void shade_px(const float* F, float T, float u, float
 
 // ---------------------------------------------------------------- helpers
 
+// 1/x for x = 1 - alpha in [1 - alpha_max, 1]: the hardware reciprocal
+// estimate refined by one Newton-Raphson step r <- r + r (1 - x r), which
+// squares its relative error (well below one float32 ulp afterwards).
+__device__ __forceinline__ float rcp_newton(float x) {
+    const float r = __fdividef(1.f, x);
+    return __fmaf_rn(r, __fmaf_rn(-x, r, 1.f), r);
+}
+
 struct TilePix {
     int i, j;
     bool inside;
@@ -395,6 +403,27 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
             uint32_t bits = __ballot_sync(SSSGS_FULL, pass);
             __syncwarp();
             const uint32_t base = rg.x + 32u * t;
+            // Composite one splat (list slot k, alpha already evaluated) into pixel q.
+            auto apply = [&](int q, int k, const AlphaEval& e, float4 g1) {
+                if (done[q] || !e.use) return;
+                const float Tn = T[q] * (1.f - e.alpha);
+                if (Tn < T_min) {
+                    done[q] = true;
+                    stop[q] = base + k + 1;
+                    return;
+                }
+                ++n_use;
+                const float w = T[q] * e.alpha;
+                const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
+                const float g5 = s_rec[buf][5][k].x;
+                float* f = F[q];
+                f[0] += w * g1.z;  f[1] += w * g1.w;  f[2] += w * g2.x;  f[3] += w * g2.y;
+                f[4] += w * g2.z;  f[5] += w * g2.w;  f[6] += w * g3.x;  f[7] += w * g3.y;
+                f[8] += w * g3.z;  f[9] += w * g3.w;  f[10] += w * g4.x; f[11] += w * g4.y;
+                f[12] += w * g4.z; f[13] += w * g4.w; f[14] += w * g5;
+                T[q] = Tn;
+                lastc[q] = base + k + 1;
+            };
             while (bits) {
                 const int k = __ffs(bits) - 1;
                 bits &= bits - 1;
@@ -402,25 +431,7 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
 #pragma unroll
                 for (int q = 0; q < PX; ++q) {
                     if (done[q]) continue;
-                    const AlphaEval e = eval_alpha(g0, g1, (float)i + 0.5f, (float)(j0 + q) + 0.5f, a_min, a_max);
-                    if (!e.use) continue;
-                    const float Tn = T[q] * (1.f - e.alpha);
-                    if (Tn < T_min) {
-                        done[q] = true;
-                        stop[q] = base + k + 1;
-                        continue;
-                    }
-                    ++n_use;
-                    const float w = T[q] * e.alpha;
-                    const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
-                    const float g5 = s_rec[buf][5][k].x;
-                    float* f = F[q];
-                    f[0] += w * g1.z;  f[1] += w * g1.w;  f[2] += w * g2.x;  f[3] += w * g2.y;
-                    f[4] += w * g2.z;  f[5] += w * g2.w;  f[6] += w * g3.x;  f[7] += w * g3.y;
-                    f[8] += w * g3.z;  f[9] += w * g3.w;  f[10] += w * g4.x; f[11] += w * g4.y;
-                    f[12] += w * g4.z; f[13] += w * g4.w; f[14] += w * g5;
-                    T[q] = Tn;
-                    lastc[q] = base + k + 1;
+                    apply(q, k, eval_alpha(g0, g1, (float)i + 0.5f, (float)(j0 + q) + 0.5f, a_min, a_max), g1);
                 }
             }
             all_done = true;
@@ -619,7 +630,7 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
                     const float g5 = s_rec[5 * B + k].x;
                     const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
                                                g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
-                    const float ia = 1.f / (1.f - e.alpha);
+                    const float ia = rcp_newton(1.f - e.alpha);
                     const float Ti = T * ia;
                     const float w = e.alpha * Ti;
                     float dot = 0.f;
@@ -700,7 +711,7 @@ struct PixBwd {
 // pixel's replay state and adds its 21 gradient terms into acc.
 __device__ __forceinline__ void bwd_contrib(PixBwd& p, const AlphaEval& e, float4 g0, float4 g1, const float* f,
                                             float* acc) {
-    const float ia = 1.f / (1.f - e.alpha);
+    const float ia = rcp_newton(1.f - e.alpha);
     const float Ti = p.T * ia;
     const float w = e.alpha * Ti;
     float dot = 0.f;
