@@ -200,7 +200,8 @@ int sssgs_project_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sss
  * ranges[n_tiles*2] = [start, end) per global tile, d_count = number of
  * instances (device int64). If more than `capacity` instances arise,
  * SSSGS_STATUS_CAPACITY is set in *d_status and lists are truncated.
- * workspace: sssgs_bin_workspace_bytes(n_items, capacity, n_tiles). */
+ * workspace: sssgs_bin_workspace_bytes(n_items, capacity, n_tiles) bytes,
+ * 256-byte aligned (SSSGS_ERR_INVALID_ARG otherwise). */
 size_t sssgs_bin_workspace_bytes(int64_t n_items, int64_t capacity, int32_t n_tiles);
 int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                    int n_pairs, const float* rec, const int32_t* rect, int64_t capacity,

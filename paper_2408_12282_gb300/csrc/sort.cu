@@ -134,15 +134,21 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
     __shared__ uint32_t h[NB];
     for (int d = threadIdx.x; d < NB; d += RS_THREADS) h[d] = 0;
     __syncthreads();
-    int64_t n = eff_n(d_n, cap);
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    int lane = threadIdx.x & 31;
+    const int64_t n = eff_n(d_n, cap);
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int lane = threadIdx.x & 31;
+    // All loads first, so the block's keys are in flight together.
+    uint32_t dig[RS_ITEMS];
+#pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        int64_t idx = base + (int64_t)k * RS_THREADS + threadIdx.x;
-        bool ok = idx < n;
-        uint32_t d = ok ? ((uint32_t)(keys[idx] >> shift) & mask) : 0xFFFFu;
-        uint32_t peers = __match_any_sync(SSSGS_FULL, d);
-        if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        const int64_t idx = base + (int64_t)k * RS_THREADS + threadIdx.x;
+        dig[k] = idx < n ? ((uint32_t)(keys[idx] >> shift) & mask) : 0xFFFFu;
+    }
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const uint32_t d = dig[k];
+        const uint32_t peers = __match_any_sync(SSSGS_FULL, d);
+        if (d != 0xFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int d = threadIdx.x; d < NB; d += RS_THREADS) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
@@ -173,11 +179,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     K key[RS_ITEMS];
     uint32_t val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {   // all loads first, so they are in flight together
+        const int64_t idx = wbase + j * 32 + lane;
+        key[j] = idx < n ? kin[idx] : K(0);
+        val[j] = idx < n ? vin[idx] : 0u;
+    }
+#pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         int64_t idx = wbase + j * 32 + lane;
         bool ok = idx < n;
-        key[j] = ok ? kin[idx] : K(0);
-        val[j] = ok ? vin[idx] : 0u;
         uint32_t d = ok ? ((uint32_t)(key[j] >> shift) & mask) : 0xFFFFu;
         uint32_t peers = __match_any_sync(SSSGS_FULL, d);
         rank[j] = ok ? wcnt[warp * NB + d] + __popc(peers & lt) : 0u;
@@ -314,34 +324,73 @@ __global__ void k_set_count(const uint64_t* __restrict__ off, int64_t n_items, i
     if (total > (uint64_t)cap && d_status) atomicOr(d_status, SSSGS_STATUS_CAPACITY);
 }
 
-__global__ void k_emit(const sssgs_pair* __restrict__ pairs, int64_t n_items, const uint64_t* __restrict__ dkeys,
-                       const uint32_t* __restrict__ dvals, const int4* __restrict__ rect,
-                       const uint64_t* __restrict__ off, int64_t cap, uint32_t* __restrict__ ikeys,
-                       uint32_t* __restrict__ ivals) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_items) return;
-    uint32_t m = dvals[s];
-    int4 r = rect[m];
-    if (r.x > r.y || r.z > r.w) return;
-    const sssgs_pair& P = pairs[(int)(dkeys[s] >> 32)];
-    uint64_t pos = off[s];
-    for (int ty = r.z; ty <= r.w; ++ty) {
-        uint32_t row = (uint32_t)(P.tile_offset + ty * P.tiles_x);
-        for (int tx = r.x; tx <= r.y; ++tx, ++pos) {
-            if (pos >= (uint64_t)cap) return;
-            ikeys[pos] = row + (uint32_t)tx;
-            ivals[pos] = m;
+// Writes the instances of a block of 256 depth-ordered items. The block's
+// output is the contiguous range [off[s0], off[s0 + 256]), so the block fills
+// it position by position (coalesced stores): each position finds its item by
+// binary search over the block's offsets, then its tile inside the item's
+// rectangle (row-major order).
+__global__ void __launch_bounds__(256) k_emit(const sssgs_pair* __restrict__ pairs, int64_t n_items,
+                                              const uint64_t* __restrict__ dkeys, const uint32_t* __restrict__ dvals,
+                                              const int4* __restrict__ rect, const uint64_t* __restrict__ off,
+                                              int64_t cap, uint32_t* __restrict__ ikeys,
+                                              uint32_t* __restrict__ ivals) {
+    __shared__ uint32_t s_off[257], s_item[256], s_base[256], s_w[256], s_tx[256];
+    const int t = threadIdx.x;
+    const int64_t s0 = (int64_t)blockIdx.x * 256;
+    const int nb = (int)min((int64_t)256, n_items - s0);
+    const uint64_t B0 = off[s0];
+    if (t < nb) {
+        const int64_t s = s0 + t;
+        const uint32_t m = dvals[s];
+        const int4 r = rect[m];
+        s_off[t] = (uint32_t)(off[s] - B0);
+        s_item[t] = m;
+        if (r.x <= r.y && r.z <= r.w) {
+            const sssgs_pair& P = pairs[(int)(dkeys[s] >> 32)];
+            s_base[t] = (uint32_t)(P.tile_offset + r.z * P.tiles_x + r.x);
+            s_w[t] = (uint32_t)(r.y - r.x + 1);
+            s_tx[t] = (uint32_t)P.tiles_x;
+        } else {
+            s_base[t] = 0;
+            s_w[t] = 1;
+            s_tx[t] = 0;
         }
+    }
+    if (t == 0) s_off[nb] = (uint32_t)(off[s0 + nb] - B0);
+    __syncthreads();
+    const uint32_t total = s_off[nb];
+    for (uint32_t rel = t; rel < total; rel += 256) {
+        const uint64_t pos = B0 + rel;
+        if (pos >= (uint64_t)cap) break;
+        int lo = 0, hi = nb - 1;            // last item whose range starts at or before rel
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= rel) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t q = rel - s_off[lo], w = s_w[lo];
+        const uint32_t dy = q / w, dx = q - dy * w;
+        ikeys[pos] = s_base[lo] + dy * s_tx[lo] + dx;
+        ivals[pos] = s_item[lo];
     }
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* d_n, int64_t cap, uint2* __restrict__ ranges) {
-    int64_t n = eff_n(d_n, cap);
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Per-tile [start, end) from the sorted tile keys, four keys per thread.
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* d_n, int64_t cap,
+                         uint2* __restrict__ ranges) {
+    const int64_t n = eff_n(d_n, cap);
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (s >= n) return;
-    uint32_t k = keys[s];
-    if (s == 0 || keys[s - 1] != k) ranges[k].x = (uint32_t)s;
-    if (s == n - 1 || keys[s + 1] != k) ranges[k].y = (uint32_t)(s + 1);
+    const uint4 q = *reinterpret_cast<const uint4*>(keys + s);
+    const uint32_t k[6] = {s > 0 ? keys[s - 1] : 0xFFFFFFFFu, q.x, q.y, q.z, q.w,
+                           s + 4 < n ? keys[s + 4] : 0xFFFFFFFFu};
+#pragma unroll
+    for (int j = 1; j <= 4; ++j) {
+        const int64_t i = s + j - 1;
+        if (i >= n) break;
+        const uint32_t kj = k[j];
+        if (i == 0 || k[j - 1] != kj) ranges[kj].x = (uint32_t)i;
+        if (i == n - 1 || (j < 4 ? k[j + 1] : k[5]) != kj) ranges[kj].y = (uint32_t)(i + 1);
+    }
 }
 
 }  // namespace sssgs
@@ -402,6 +451,7 @@ extern "C" int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, c
     if (n_items >= ((int64_t)1 << 32)) return SSSGS_ERR_INVALID_ARG;
     BinLayout L = bin_layout(n_items, capacity);
     if (!workspace || workspace_bytes < L.total) return SSSGS_ERR_WORKSPACE;
+    if ((uintptr_t)workspace & 255) return SSSGS_ERR_INVALID_ARG;
     unsigned char* ws = (unsigned char*)workspace;
     uint64_t* dkA = (uint64_t*)(ws + L.dkA);
     uint64_t* dkB = (uint64_t*)(ws + L.dkB);
@@ -448,7 +498,7 @@ extern "C" int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, c
     int r2 = radix_sort<uint32_t>(ikA, v0, ikB, v1, d_count, capacity, tbits, hist, part32, st);
     uint32_t* ik = r2 ? ikB : ikA;
     // 5. per-tile ranges
-    unsigned gr = (unsigned)((capacity + 255) / 256);
+    unsigned gr = (unsigned)((capacity + 1023) / 1024);
     k_ranges<<<gr, 256, 0, st>>>(ik, d_count, capacity, (uint2*)ranges);
     sssgs::note_launches(1);
     return launch_status();
