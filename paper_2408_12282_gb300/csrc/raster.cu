@@ -707,31 +707,29 @@ struct PixBwd {
     uint32_t lastc;
 };
 
-// Back-to-front step for one contributing splat at one pixel: updates the
-// pixel's replay state and adds its 21 gradient terms into acc.
-__device__ __forceinline__ void bwd_contrib(PixBwd& p, const AlphaEval& e, float4 g0, float4 g1, const float* f,
-                                            float* acc) {
-    const float ia = rcp_newton(1.f - e.alpha);
-    const float Ti = p.T * ia;
-    const float w = e.alpha * Ti;
+// Branch-free back-to-front replay step of one splat at one pixel. `act`:
+// the pixel takes the splat (list position below its last contributor and
+// alpha test passed); otherwise the state is left as is and the returned
+// terms are 0. Returns w = alpha T_i (the pixel's weight of the splat's
+// features), dp = dL/dp (p the Gaussian exponent) and dg = dL/do.
+struct BwdStep {
+    float w, dp, dg;
+};
+__device__ __forceinline__ BwdStep bwd_step(PixBwd& p, const AlphaEval& e, bool act, const float* f) {
     float dot = 0.f;
 #pragma unroll
-    for (int c = 0; c < SSSGS_NF; ++c) {
-        dot += p.dF[c] * f[c];
-        acc[6 + c] += w * p.dF[c];
-    }
+    for (int c = 0; c < SSSGS_NF; ++c) dot += p.dF[c] * f[c];
+    const float ia = rcp_newton(1.f - e.alpha);
+    const float Ti = p.T * ia;
     const float da = Ti * dot - (p.Q + p.dTT) * ia;
-    p.Q += w * dot;
-    if (!e.clamped) {
-        const float dp = -da * e.alpha;
-        acc[0] += dp * (g0.z * e.dx + g0.w * e.dy);
-        acc[1] += dp * (g0.w * e.dx + g1.x * e.dy);
-        acc[2] += dp * 0.5f * e.dx * e.dx;
-        acc[3] += dp * e.dx * e.dy;
-        acc[4] += dp * 0.5f * e.dy * e.dy;
-        acc[5] += da * e.G;
-    }
-    p.T = Ti;
+    const bool geo = act && !e.clamped;
+    BwdStep r;
+    r.w = act ? e.alpha * Ti : 0.f;
+    r.dp = geo ? -da * e.alpha : 0.f;
+    r.dg = geo ? da * e.G : 0.f;
+    p.Q += r.w * dot;
+    p.T = act ? Ti : p.T;
+    return r;
 }
 
 template <int MODE>
@@ -862,19 +860,23 @@ __global__ void __launch_bounds__(32, 16) k_composite_bwd_warp(sssgs_cfg cfg, co
                 const bool act0 = (pos < p[0].lastc) && e0.use;
                 const bool act1 = (pos < p[1].lastc) && e1.use;
                 if (!__any_sync(SSSGS_FULL, act0 || act1)) continue;
-                float acc[NG];
-#pragma unroll
-                for (int c = 0; c < NG; ++c) acc[c] = 0.f;
-                if (act0 || act1) {
+                {   // both pixels' terms, summed, straight into this lane's reduction column
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
                     const float g5 = s_rec[buf][5][k].x;
                     const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
                                                g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
-                    if (act0) { bwd_contrib(p[0], e0, g0, g1, f, acc); ++n_use; }
-                    if (act1) { bwd_contrib(p[1], e1, g0, g1, f, acc); ++n_use; }
-                }
+                    const BwdStep s0 = bwd_step(p[0], e0, act0, f), s1 = bwd_step(p[1], e1, act1, f);
+                    n_use += (uint32_t)act0 + (uint32_t)act1;
+                    float* col = s_red + lane;
 #pragma unroll
-                for (int c = 0; c < NG; ++c) s_red[c * RS + lane] = acc[c];
+                    for (int c = 0; c < SSSGS_NF; ++c) col[(6 + c) * RS] = s0.w * p[0].dF[c] + s1.w * p[1].dF[c];
+                    col[0] = s0.dp * (g0.z * e0.dx + g0.w * e0.dy) + s1.dp * (g0.z * e1.dx + g0.w * e1.dy);
+                    col[RS] = s0.dp * (g0.w * e0.dx + g1.x * e0.dy) + s1.dp * (g0.w * e1.dx + g1.x * e1.dy);
+                    col[2 * RS] = 0.5f * (s0.dp * e0.dx * e0.dx + s1.dp * e1.dx * e1.dx);
+                    col[3 * RS] = s0.dp * e0.dx * e0.dy + s1.dp * e1.dx * e1.dy;
+                    col[4 * RS] = 0.5f * (s0.dp * e0.dy * e0.dy + s1.dp * e1.dy * e1.dy);
+                    col[5 * RS] = s0.dg + s1.dg;
+                }
                 __syncwarp();
                 if (lane < NG) {
                     const float4* row = reinterpret_cast<const float4*>(s_red + lane * RS);
