@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
             const sssgs_pair& P = pairs[p];
             float dx[7];
             input_backward(net, P, sc, P.g_begin + (m - P.item_offset), dcur + threadIdx.x * MLP_LDA, dx);
-            for (int k = 0; k < 7; ++k) dx_items[7 * m + k] += dx[k];
+            for (int k = 0; k < 7; ++k) dx_items[7 * m + k] = dx[k];
         }
         __syncthreads();   // the next tile overwrites the buffers read above
     }

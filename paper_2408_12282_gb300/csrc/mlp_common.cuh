@@ -91,67 +91,97 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
 
 // PE6 input (64 features, fixed layout) with compile-time indices, so the
 // row stays in registers.
-__device__ __forceinline__ void build_input_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g, float (&x)[64]) {
-    const float m0 = __ldg(sc.mu + 3 * g), m1 = __ldg(sc.mu + 3 * g + 1), m2 = __ldg(sc.mu + 3 * g + 2);
-    const float n0 = __ldg(sc.normal + 3 * g), n1 = __ldg(sc.normal + 3 * g + 1), n2 = __ldg(sc.normal + 3 * g + 2);
-    const float vv = __ldg(sc.vis + g);
-    const float3 C = cam_center(P);
-    const float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
-    const float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
-    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
-    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
-    const float mm[3] = {m0, m1, m2};
+// Fourier part of the PE6 input, frequencies k in [K0, K1): x[6 (k - K0) + c]
+// = sin(2^k pi mu_c), x[6 (k - K0) + 3 + c] = cos(2^k pi mu_c), i.e. x[0] is
+// input column 6 K0.
+template <int K0, int K1>
+__device__ __forceinline__ void pe6_fourier(const float (&mm)[3], float* x) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = K0; k < K1; ++k) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float sn, cs;
             sincospif(ldexpf(mm[c], k), &sn, &cs);
-            x[6 * k + c] = sn;
-            x[6 * k + 3 + c] = cs;
+            x[6 * (k - K0) + c] = sn;
+            x[6 * (k - K0) + 3 + c] = cs;
         }
     }
-    x[36] = m0; x[37] = m1; x[38] = m2;
-    x[39] = wo.x; x[40] = wo.y; x[41] = wo.z;
-    x[42] = wi.x; x[43] = wi.y; x[44] = wi.z;
-    x[45] = n0; x[46] = n1; x[47] = n2;
-    x[48] = li;
-    x[49] = vv;
-#pragma unroll
-    for (int k = 50; k < 64; ++k) x[k] = 0.f;
 }
 
-// Backward of build_input_pe6: dX (64) -> dx[7] = (d mu, d n, d v).
-__device__ __forceinline__ void input_backward_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g,
-                                                   const float (&dX)[64], float (&dx)[7]) {
-    const float m0 = __ldg(sc.mu + 3 * g), m1 = __ldg(sc.mu + 3 * g + 1), m2 = __ldg(sc.mu + 3 * g + 2);
+// Input columns [36, 64) (x[0] is column 36): mu, unit(camera - mu),
+// unit(light - mu), n, |light - mu|, v, zero padding.
+__device__ __forceinline__ void pe6_direct(const sssgs_pair& P, const float (&mm)[3], const float (&nn)[3], float vv,
+                                           float* x) {
     const float3 C = cam_center(P);
-    const float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
-    const float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
+    const float3 Vo = make_float3(C.x - mm[0], C.y - mm[1], C.z - mm[2]);
+    const float3 Vi = make_float3(P.light[0] - mm[0], P.light[1] - mm[1], P.light[2] - mm[2]);
     const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
     const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
-    const float mm[3] = {m0, m1, m2};
-    float dmu[3] = {dX[36], dX[37], dX[38]};
+    x[0] = mm[0]; x[1] = mm[1]; x[2] = mm[2];
+    x[3] = wo.x; x[4] = wo.y; x[5] = wo.z;
+    x[6] = wi.x; x[7] = wi.y; x[8] = wi.z;
+    x[9] = nn[0]; x[10] = nn[1]; x[11] = nn[2];
+    x[12] = li;
+    x[13] = vv;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 14; k < 28; ++k) x[k] = 0.f;
+}
+
+// The per-Gaussian network inputs of one item.
+struct Pe6Params {
+    float mu[3], n[3], v;
+};
+__device__ __forceinline__ Pe6Params load_pe6_params(const sssgs_scene& sc, int64_t g) {
+    Pe6Params q;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        q.mu[c] = __ldg(sc.mu + 3 * g + c);
+        q.n[c] = __ldg(sc.normal + 3 * g + c);
+    }
+    q.v = __ldg(sc.vis + g);
+    return q;
+}
+
+__device__ __forceinline__ void build_input_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g, float (&x)[64]) {
+    const Pe6Params q = load_pe6_params(sc, g);
+    pe6_fourier<0, 6>(q.mu, x);
+    pe6_direct(P, q.mu, q.n, q.v, x + 36);
+}
+
+// Backward of pe6_fourier<K0, K1>: adds the Fourier columns' contribution to
+// dL/dmu (dX[0] is input column 6 K0).
+template <int K0, int K1>
+__device__ __forceinline__ void pe6_fourier_bwd(const float (&mm)[3], const float* dX, float (&dmu)[3]) {
+#pragma unroll
+    for (int k = K0; k < K1; ++k) {
         const float f = ldexpf(kPi, k);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float sn, cs;
             sincospif(ldexpf(mm[c], k), &sn, &cs);
-            dmu[c] += f * (dX[6 * k + c] * cs - dX[6 * k + 3 + c] * sn);
+            dmu[c] += f * (dX[6 * (k - K0) + c] * cs - dX[6 * (k - K0) + 3 + c] * sn);
         }
     }
-    dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
-    const float3 go = make_float3(dX[39], dX[40], dX[41]);
-    const float3 gi = make_float3(dX[42], dX[43], dX[44]);
+}
+
+// Backward of pe6_direct (dX[0] is input column 36): dx = (dL/dmu from the
+// direct columns, dL/dn, dL/dv).
+__device__ __forceinline__ void pe6_direct_bwd(const sssgs_pair& P, const float (&mm)[3], const float* dX,
+                                               float (&dx)[7]) {
+    const float3 C = cam_center(P);
+    const float3 Vo = make_float3(C.x - mm[0], C.y - mm[1], C.z - mm[2]);
+    const float3 Vi = make_float3(P.light[0] - mm[0], P.light[1] - mm[1], P.light[2] - mm[2]);
+    const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
+    const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
+    const float3 go = make_float3(dX[3], dX[4], dX[5]);
+    const float3 gi = make_float3(dX[6], dX[7], dX[8]);
     const float3 bo = (-1.f / lo) * (go - dot3(wo, go) * wo);
     const float3 bi = (-1.f / li) * (gi - dot3(wi, gi) * wi);
-    dx[0] = dmu[0] + bo.x + bi.x;
-    dx[1] = dmu[1] + bo.y + bi.y;
-    dx[2] = dmu[2] + bo.z + bi.z;
-    dx[3] = dX[45]; dx[4] = dX[46]; dx[5] = dX[47];
-    dx[6] = dX[49];
+    dx[0] = dX[0] - dX[12] * wi.x + bo.x + bi.x;
+    dx[1] = dX[1] - dX[12] * wi.y + bo.y + bi.y;
+    dx[2] = dX[2] - dX[12] * wi.z + bo.z + bi.z;
+    dx[3] = dX[9]; dx[4] = dX[10]; dx[5] = dX[11];
+    dx[6] = dX[13];
 }
 
 }  // namespace sssgs

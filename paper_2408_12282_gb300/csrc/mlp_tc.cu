@@ -80,6 +80,11 @@ __device__ __forceinline__ void store8_bf16(uint8_t* base, int r, int c, int C, 
     *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
 }
 
+// Store one FP32 value of row r, column c as BF16.
+__device__ __forceinline__ void store1_bf16(uint8_t* base, int r, int c, int C, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + tc::blk_offset(r, c, C)) = __float2bfloat16_rn(v);
+}
+
 constexpr int TC_MAX_SMEM_PAIRS = 256;
 
 // Item -> pair lookup against a shared-memory copy of the pairs' item offsets
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_fwd_tc(MlpDev net, co
 
 struct TcBwdLayout {
     uint32_t offH[SSSGS_MAX_LAYERS];   // layer inputs (later dZ, in place)
-    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offBar, offPairs;
+    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offDx, offBar, offPairs;
     uint32_t total;
     uint32_t gW[SSSGS_MAX_LAYERS];     // weight image offsets in the global workspace
     uint32_t wbytes[SSSGS_MAX_LAYERS];
@@ -268,6 +273,7 @@ __host__ __device__ inline TcBwdLayout tc_bwd_layout(const MlpDev& net) {
     T.offW[1] = o; o += wmax;
     T.offBias = o; o += (uint32_t)(bo * 4);
     T.offDbL = o;  o += 16 * 4;
+    T.offDx = o;   o += 7 * TC_ROWS * 4;
     T.offBar = o;  o += 32;
     T.offPairs = o; o += 8 * 256;
     T.total = o;
@@ -314,6 +320,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     const uint32_t bar_w0 = bar_m + 8, bar_w1 = bar_m + 16;
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + T.offBar + 24);
     uint8_t* sDZL = smem + T.offDZL;
+    float* s_dx = reinterpret_cast<float*>(smem + T.offDx);   // [7][TC_ROWS]
 
     if (tid < 32) {
         tc::tmem_alloc(tc::smem_u32(s_tmem), 512);
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
     for (int j = 0; j < SSSGS_MAX_LAYERS; ++j) dbacc[j] = 0.f;
 
-    uint32_t ph_m = 0, ph_w[2] = {0u, 0u};
+    uint32_t ph_m = 0, ph_w0 = 0, ph_w1 = 0;
     uint32_t use = 0;            // weight-use counter (2L uses per tile)
     bool ok = true, any_tile = false;
     const int uses_per_tile = 2 * L;
@@ -375,10 +382,10 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 tc::mbar_arrive_expect_tx(nb, T.wbytes[ln]);
                 tc::bulk_g2s(tc::smem_u32(smem + T.offW[nu & 1]), gimg + T.gW[ln], T.wbytes[ln], nb);
             }
-            got = tc::mbar_wait((use & 1) ? bar_w1 : bar_w0, ph_w[use & 1]);
+            got = tc::mbar_wait((use & 1) ? bar_w1 : bar_w0, (use & 1) ? ph_w1 : ph_w0);
             tc::fence_after();
         }
-        ph_w[use & 1] ^= 1u;
+        if (use & 1) ph_w1 ^= 1u; else ph_w0 ^= 1u;
         return got;
     };
     auto wait_mma = [&]() -> bool {
@@ -393,22 +400,59 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         return __syncthreads_and(mine) != 0;
     };
 
+    // Per-row inputs (network parameters and upstream gradient) of a tile;
+    // those of the next tile are loaded while the current one is processed.
+    struct RowIn {
+        Pe6Params q;
+        float up[4];
+        int pidx;
+        bool valid;
+    };
+    auto load_row = [&](int64_t tl) -> RowIn {
+        RowIn r;
+        const int64_t mr = tl * TC_ROWS + t;
+        r.valid = tl < n_tiles && mr < n_items;
+        r.pidx = 0;
+        if (r.valid) {
+            r.pidx = pair_lookup(s_off, pairs, n_pairs, mr);
+            r.q = load_pe6_params(sc, pairs[r.pidx].g_begin + (mr - pairs[r.pidx].item_offset));
+            const float* u = drec + (int64_t)SSSGS_REC * mr + 16;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) r.up[c] = u[c];
+        }
+        return r;
+    };
+    RowIn cur = load_row(blockIdx.x);
+    float dmu_a[3] = {0.f, 0.f, 0.f};     // Fourier part of dL/dmu (frequencies 0..2, warpgroup 0)
+
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int64_t m = tile * TC_ROWS + t;
-        const bool valid = m < n_items;
-        int pidx = 0;
-        int64_t gidx = 0;
-        if (valid) {
-            pidx = pair_lookup(s_off, pairs, n_pairs, m);
-            gidx = pairs[pidx].g_begin + (m - pairs[pidx].item_offset);
-        }
-        if (wg == 0) {   // H_0: network input
-            float x[64];
+        const bool valid = cur.valid;
+        const int pidx = cur.pidx;
+        const RowIn nxt = load_row(tile + gridDim.x);
+        // H_0: network input, split between the warpgroups: columns [0, 18)
+        // (frequencies 0..2) on warpgroup 0, [18, 64) on warpgroup 1.
+        if (wg == 0) {
+            float x[18];
 #pragma unroll
-            for (int k = 0; k < 64; ++k) x[k] = 0.f;
-            if (valid) build_input_pe6(pairs[pidx], sc, gidx, x);
+            for (int k = 0; k < 18; ++k) x[k] = 0.f;
+            if (valid) pe6_fourier<0, 3>(cur.q.mu, x);
+            store8_bf16(smem + T.offH[0], t, 0, 64, x);
+            store8_bf16(smem + T.offH[0], t, 8, 64, x + 8);
+            store1_bf16(smem + T.offH[0], t, 16, 64, x[16]);
+            store1_bf16(smem + T.offH[0], t, 17, 64, x[17]);
+        } else {
+            float x[46];
 #pragma unroll
-            for (int c = 0; c < 64; c += 8) store8_bf16(smem + T.offH[0], t, c, 64, x + c);
+            for (int k = 0; k < 46; ++k) x[k] = 0.f;
+            if (valid) {
+                pe6_fourier<3, 6>(cur.q.mu, x);
+                pe6_direct(pairs[pidx], cur.q.mu, cur.q.n, cur.q.v, x + 18);
+            }
+#pragma unroll
+            for (int c = 18; c < 24; ++c) store1_bf16(smem + T.offH[0], t, c, 64, x[c - 18]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) store8_bf16(smem + T.offH[0], t, 24 + 8 * q, 64, x + 6 + 8 * q);
         }
         ok = sync_all(true);
         // ---------------- forward recompute
@@ -457,13 +501,12 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
                 for (int j = 0; j < 16; ++j) dz[j] = 0.f;
                 if (valid) {
-                    const float* up = drec + (int64_t)SSSGS_REC * m + 16;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const float s = 1.f / (1.f + expf(-(v[c] + bl[c])));
-                        dz[c] = up[c] * s * (1.f - s);
+                        dz[c] = cur.up[c] * s * (1.f - s);
                     }
-                    dz[3] = (v[3] + bl[3]) > 0.f ? up[3] : 0.f;
+                    dz[3] = (v[3] + bl[3]) > 0.f ? cur.up[3] : 0.f;
                 }
                 uint4 q0, q1;
                 q0.x = tc::pack_bf16(dz[0], dz[1]); q0.y = tc::pack_bf16(dz[2], dz[3]);
@@ -550,7 +593,9 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             } else if (wg == 0) {
                 float v[16];
                 tc::tmem_ld16(tmem + lane_off + 64, v);
-                dbacc[l] += v[0];
+#pragma unroll
+                for (int j = 0; j < SSSGS_MAX_LAYERS; ++j)
+                    if (j == l) dbacc[j] += v[0];
             }
             for (int h = 0; h < 2; ++h) {
                 if (h == 1) {
@@ -591,20 +636,32 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                             store8_bf16(hb, t, c, Kin, o8);
                         }
                     }
-                } else if (wg == 0) {
-                    // network-input gradient (64 columns) -> (d mu, d n, d v)
+                } else {
+                    // network-input gradient (64 columns) -> (d mu, d n, d v), split
+                    // like the input: warpgroup 0 keeps the Fourier part of
+                    // frequencies 0..2, warpgroup 1 leaves the rest in s_dx.
                     float dX[64];
                     tc::tmem_ld64(tmem + lane_off, dX);
-                    if (valid) {
-                        float dx[7];
-                        input_backward_pe6(pairs[pidx], sc, gidx, dX, dx);
+                    if (wg == 0) {
+                        dmu_a[0] = dmu_a[1] = dmu_a[2] = 0.f;
+                        if (valid) pe6_fourier_bwd<0, 3>(cur.q.mu, dX, dmu_a);
+                    } else if (valid) {
+                        float dm[3] = {0.f, 0.f, 0.f}, dx[7];
+                        pe6_fourier_bwd<3, 6>(cur.q.mu, dX + 18, dm);
+                        pe6_direct_bwd(pairs[pidx], cur.q.mu, dX + 36, dx);
+                        dx[0] += dm[0]; dx[1] += dm[1]; dx[2] += dm[2];
 #pragma unroll
-                        for (int k = 0; k < 7; ++k) dx_items[7 * m + k] += dx[k];
+                        for (int k = 0; k < 7; ++k) s_dx[k * TC_ROWS + t] = dx[k];
                     }
                 }
             }
             mine = sync_all(mine);
             if (l == 0) {   // db_0 = dZ_1^T 1 (its TMEM columns were busy above)
+                if (wg == 0 && valid) {   // combine the two halves of the input gradient
+#pragma unroll
+                    for (int k = 0; k < 7; ++k)
+                        dx_items[7 * m + k] = s_dx[k * TC_ROWS + t] + (k < 3 ? dmu_a[k] : 0.f);
+                }
                 if (tid == 0) {
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
                     const uint32_t ones = tc::smem_u32(smem + T.offOnes);
@@ -625,6 +682,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             ok = mine;
         }
         any_tile = true;
+        cur = nxt;
     }
     if (!ok) {
         if (tid == 0 && status) atomicOr(status, SSSGS_STATUS_TIMEOUT);
@@ -644,8 +702,9 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         if (wg == 0) {
             if (t < net.w[L - 1])
                 for (int c = 0; c < net.w[L]; ++c) atomicAdd(&gr.W[L - 1][c * net.w[L - 1] + t], accL[c]);
-            for (int l = 0; l <= L - 2; ++l)
-                if (gr.b[l] && t < net.w[l + 1]) atomicAdd(&gr.b[l][t], dbacc[l]);
+#pragma unroll
+            for (int j = 0; j < SSSGS_MAX_LAYERS; ++j)
+                if (j <= L - 2 && gr.b[j] && t < net.w[j + 1]) atomicAdd(&gr.b[j][t], dbacc[j]);
         }
         __syncthreads();
         if (gr.b[L - 1] && tid < net.w[L]) atomicAdd(&gr.b[L - 1][tid], sdbL[tid]);

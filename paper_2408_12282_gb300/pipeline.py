@@ -153,7 +153,6 @@ class Renderer:
 
     def zero_grads(self):
         self.drec.zero_()
-        self.dx_items.zero_()
         for g in self.grads.values():
             g.zero_()
         for g in self.dW + self.db:
