@@ -7,11 +7,13 @@
 // the order (tile, depth, item) with 8-bit digits over ~18 tile bits instead
 // of ~50 key bits over all instances.
 //
-// Each radix pass is reduce-then-scan: a per-block digit histogram, a device
-// scan of the (digit-major, block-minor) histogram, then a scatter in which
-// every warp ranks its keys with __match_any_sync, blocks stage keys in shared
-// memory in digit order and write each digit run contiguously. No kernel waits
-// on another block, so nothing can spin.
+// Each radix pass is reduce-then-scan: a per-block digit histogram (one
+// shared-memory histogram per warp, plain atomics), a device scan of the
+// (digit-major, block-minor) histogram, then a scatter in which every warp
+// ranks its keys stably (the lanes sharing a digit are found with one ballot
+// per digit bit), blocks stage keys in shared memory in digit order and write
+// each digit run contiguously. No kernel waits on another block, so nothing
+// can spin.
 #include <algorithm>
 
 #include "common.cuh"
@@ -131,13 +133,14 @@ template <typename K, int NB>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, const int64_t* d_n, int64_t cap,
                                                         int shift, uint32_t mask, uint32_t* __restrict__ hist,
                                                         int nblocks) {
-    __shared__ uint32_t h[NB];
-    for (int d = threadIdx.x; d < NB; d += RS_THREADS) h[d] = 0;
+    // One histogram per warp; plain shared-memory atomics (lanes with the
+    // same digit serialise only within their warp).
+    __shared__ uint32_t h[RS_WARPS * NB];
+    for (int d = threadIdx.x; d < RS_WARPS * NB; d += RS_THREADS) h[d] = 0;
     __syncthreads();
     const int64_t n = eff_n(d_n, cap);
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    const int lane = threadIdx.x & 31;
-    // All loads first, so the block's keys are in flight together.
+    uint32_t* hw = h + (threadIdx.x >> 5) * NB;
     uint32_t dig[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
@@ -145,13 +148,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
         dig[k] = idx < n ? ((uint32_t)(keys[idx] >> shift) & mask) : 0xFFFFu;
     }
 #pragma unroll
-    for (int k = 0; k < RS_ITEMS; ++k) {
-        const uint32_t d = dig[k];
-        const uint32_t peers = __match_any_sync(SSSGS_FULL, d);
-        if (d != 0xFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
+    for (int k = 0; k < RS_ITEMS; ++k)
+        if (dig[k] != 0xFFFFu) atomicAdd(&hw[dig[k]], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < NB; d += RS_THREADS) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < NB; d += RS_THREADS) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) c += h[w * NB + d];
+        hist[(int64_t)d * nblocks + blockIdx.x] = c;
+    }
 }
 
 template <typename K, int NB>
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     if (base >= n) return;                          // uniform over the block
     const int64_t wbase = base + (int64_t)warp * (RS_ITEMS * 32);
     const uint32_t lt = (1u << lane) - 1u;
+    const int nbits = 32 - __clz(mask);
     K key[RS_ITEMS];
     uint32_t val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
@@ -189,7 +195,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
         int64_t idx = wbase + j * 32 + lane;
         bool ok = idx < n;
         uint32_t d = ok ? ((uint32_t)(key[j] >> shift) & mask) : 0xFFFFu;
-        uint32_t peers = __match_any_sync(SSSGS_FULL, d);
+        // lanes with the same digit: one ballot per digit bit
+        uint32_t peers = __ballot_sync(SSSGS_FULL, ok);
+        for (int b = 0; b < nbits; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(SSSGS_FULL, bit);
+            peers &= bit ? bal : ~bal;
+        }
         rank[j] = ok ? wcnt[warp * NB + d] + __popc(peers & lt) : 0u;
         __syncwarp();
         if (ok && lane == __ffs(peers) - 1) wcnt[warp * NB + d] += __popc(peers);
