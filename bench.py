@@ -351,6 +351,9 @@ def run_ours(args):
             a = e_z if s == "render_bwd" else ev[i]
             stage_ms[s] += a.elapsed_time(ev[i + 1]) / reps
     n_items, n_pixels = table.n_items, table.n_pixels
+    # rows the network backward runs on: items with a nonzero upstream gradient
+    # (the others add exactly zero and are compacted out)
+    n_active = int((r.drec[:, 16:20] != 0).any(dim=1).sum().item())
     n_gauss = sum(sc.N for sc in wl.scenes)
     contrib_f, evals_f = (int(x) // reps for x in stats_f.tolist())
     contrib_b, evals_b = (int(x) // reps for x in stats_b.tolist())
@@ -361,7 +364,7 @@ def run_ours(args):
     dom = max(STAGES, key=lambda s: stage_ms[s])
     widths = [int(r._mlp_s.width[i]) for i in range(r._mlp_s.n_layers + 1)]
     if dom in ("mlp_fwd", "mlp_bwd") and precision == B.BF16:
-        fl = mlp_flops(widths, n_items) * (1 if dom == "mlp_fwd" else 2)
+        fl = mlp_flops(widths, n_items) if dom == "mlp_fwd" else 2 * mlp_flops(widths, n_active)
         ach = fl / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
                 "frac": ach / bf16_sus, "traffic": None, "peak_source": peak_src + " (bf16 sustained)"}
@@ -465,7 +468,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "bf16+f32" if precision == B.BF16 else "f32",
                 "data": "synthetic", "config": _config(args),
                 "roofline": roof, "step_hbm_frac_of_algorithmic": step_hbm_frac,
-                "stage_ms": stage_ms, "instances": n_inst, "items": n_items, "pixels": n_pixels,
+                "stage_ms": stage_ms, "instances": n_inst, "items": n_items, "mlp_bwd_rows": n_active, "pixels": n_pixels,
                 "contributions_per_step": {"forward": contrib_f, "backward": contrib_b},
                 "cuda_graph": graph is not None,
                 "plain_fp32": plain, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,

@@ -178,7 +178,10 @@ int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_p
 /* a5 -- network backward. Reads dL/d(L_SSS, L_in) from the gradient records
  * drec (fields 16..19), accumulates weight/bias gradients into grad and
  * writes (overwrites) the per-item input gradients
- * dx_items[n_items*7] = (dmu 3, dn 3, dv 1).
+ * dx_items[n_items*7] = (dmu 3, dn 3, dv 1). Items whose four upstream values
+ * are all exactly zero (Gaussians that reach no pixel of their view) add
+ * exactly zero to every gradient; the BF16 path leaves them out of the
+ * network and writes their dx_items as 0. BF16 path: n_items < 2^32.
  * workspace: sssgs_mlp_workspace_bytes(mlp, n_items) bytes (any alignment >= 256). */
 size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_items);
 int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,

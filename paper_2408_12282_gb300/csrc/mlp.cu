@@ -402,11 +402,11 @@ extern "C" int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
     return launch_status();
 }
 
-size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp);
+size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp, int64_t n_items);
 
 extern "C" size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_items) {
     if (!mlp_ok(mlp) || n_items < 0) return 0;
-    if (mlp->precision == SSSGS_BF16) return sssgs_mlp_workspace_bytes_tc(mlp);
+    if (mlp->precision == SSSGS_BF16) return sssgs_mlp_workspace_bytes_tc(mlp, n_items);
     int64_t chunk = std::min<int64_t>(std::max<int64_t>(n_items, 1), MLP_CHUNK);
     return (size_t)(chunk * floats_per_row(mlp) * 4) + 256;
 }

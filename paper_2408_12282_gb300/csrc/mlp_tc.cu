@@ -301,12 +301,96 @@ __device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c,
     return *reinterpret_cast<const uint4*>(base + tc::blk_offset(r, c, C));
 }
 
+// ---------------------------------------------------------------- active rows
+//
+// A row whose upstream gradient (drec fields 16..19) is exactly zero adds
+// exactly zero to every dW, db and to its own input gradient: all dZ of the
+// chain are 0 * finite = 0, and bf16(0) = 0. Gaussians hidden behind the
+// surface in a view never contribute to a pixel, so their rows are zero. The
+// backward therefore runs on the list of the other rows, in item order
+// (deterministic: count, scan, write), and writes dx_items = 0 for the rest.
+constexpr int ACT_BLOCK = 1024;
+
+__device__ __forceinline__ bool row_active(const float* __restrict__ drec, int64_t m) {
+    const float* u = drec + (int64_t)SSSGS_REC * m + 16;
+    return (u[0] != 0.f) | (u[1] != 0.f) | (u[2] != 0.f) | (u[3] != 0.f);
+}
+
+__global__ void __launch_bounds__(ACT_BLOCK) k_active_count(const float* __restrict__ drec, int64_t n,
+                                                            uint32_t* __restrict__ cnt, float* __restrict__ dx_items) {
+    const int64_t m = (int64_t)blockIdx.x * ACT_BLOCK + threadIdx.x;
+    const bool a = m < n && row_active(drec, m);
+    if (m < n && !a) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) dx_items[7 * m + k] = 0.f;
+    }
+    const int c = __syncthreads_count(a);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (uint32_t)c;
+}
+
+// Exclusive scan of the block counts (one block, carried over chunks of 1024);
+// n_active = the total.
+__global__ void __launch_bounds__(1024) k_active_scan(const uint32_t* __restrict__ cnt, int nb,
+                                                      uint32_t* __restrict__ off, uint32_t* __restrict__ n_active) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t v = b < nb ? cnt[b] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(SSSGS_FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(SSSGS_FULL, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t c = carry;
+        const uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u);
+        if (b < nb) off[b] = c + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_active = carry;
+}
+
+__global__ void __launch_bounds__(ACT_BLOCK) k_active_write(const float* __restrict__ drec, int64_t n,
+                                                            const uint32_t* __restrict__ off,
+                                                            uint32_t* __restrict__ active) {
+    __shared__ uint32_t wcnt[ACT_BLOCK / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t m = (int64_t)blockIdx.x * ACT_BLOCK + threadIdx.x;
+    const bool a = m < n && row_active(drec, m);
+    const uint32_t bal = __ballot_sync(SSSGS_FULL, a);
+    if (lane == 0) wcnt[warp] = (uint32_t)__popc(bal);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wcnt[w];
+    if (a) active[off[blockIdx.x] + before + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = (uint32_t)m;
+}
+
 __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdLayout T,
                                                               const uint8_t* __restrict__ gimg,
                                                               const sssgs_pair* __restrict__ pairs, int n_pairs,
                                                               int64_t n_items, sssgs_scene sc,
                                                               const float* __restrict__ drec, sssgs_mlp_grad gr,
                                                               float* __restrict__ dx_items,
+                                                              const uint32_t* __restrict__ active,
+                                                              const uint32_t* __restrict__ n_active,
                                                               int32_t* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     // 8 warps: warpgroup wg handles half of the columns of every column-parallel
@@ -364,7 +448,9 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         const int k = (int)(u % (uint32_t)uses_per_tile);
         return k < L ? k : 2 * L - 1 - k;
     };
-    const int64_t n_tiles = (n_items + TC_ROWS - 1) / TC_ROWS;
+    // rows = the active items (see k_active_count)
+    const int64_t n_rows = *n_active;
+    const int64_t n_tiles = (n_rows + TC_ROWS - 1) / TC_ROWS;
     if (tid == 0 && (int64_t)blockIdx.x < n_tiles) {   // first weights
         const int l0 = layer_of_use(0);
         tc::mbar_arrive_expect_tx(bar_w0, T.wbytes[l0]);
@@ -405,15 +491,19 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     struct RowIn {
         Pe6Params q;
         float up[4];
+        int64_t m;
         int pidx;
         bool valid;
     };
     auto load_row = [&](int64_t tl) -> RowIn {
         RowIn r;
-        const int64_t mr = tl * TC_ROWS + t;
-        r.valid = tl < n_tiles && mr < n_items;
+        const int64_t row = tl * TC_ROWS + t;
+        r.valid = tl < n_tiles && row < n_rows;
         r.pidx = 0;
+        r.m = 0;
         if (r.valid) {
+            const int64_t mr = active[row];
+            r.m = mr;
             r.pidx = pair_lookup(s_off, pairs, n_pairs, mr);
             r.q = load_pe6_params(sc, pairs[r.pidx].g_begin + (mr - pairs[r.pidx].item_offset));
             const float* u = drec + (int64_t)SSSGS_REC * mr + 16;
@@ -426,7 +516,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     float dmu_a[3] = {0.f, 0.f, 0.f};     // Fourier part of dL/dmu (frequencies 0..2, warpgroup 0)
 
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t m = tile * TC_ROWS + t;
+        const int64_t m = cur.m;
         const bool valid = cur.valid;
         const int pidx = cur.pidx;
         const RowIn nxt = load_row(tile + gridDim.x);
@@ -766,9 +856,30 @@ int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
 }
 
 
-size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp) {
+namespace {
+// Backward workspace: BF16 weight images, then the active-row list, the
+// per-block counts and offsets, and the active-row count.
+struct TcBwdWs {
+    size_t img, active, cnt, off, nact, total;
+};
+TcBwdWs tc_bwd_ws(const TcBwdLayout& T, int64_t n_items) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t nb = (size_t)((n_items + ACT_BLOCK - 1) / ACT_BLOCK);
+    TcBwdWs w;
+    size_t o = 0;
+    w.img = o;    o += al(T.gtotal);
+    w.active = o; o += al(4 * (size_t)n_items);
+    w.cnt = o;    o += al(4 * nb);
+    w.off = o;    o += al(4 * nb);
+    w.nact = o;   o += 256;
+    w.total = o + 256;    // room to align the base
+    return w;
+}
+}  // namespace
+
+size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp, int64_t n_items) {
     if (!tc_supported(mlp)) return 0;
-    return (size_t)tc_bwd_layout(to_dev_tc(mlp)).gtotal + 256;
+    return tc_bwd_ws(tc_bwd_layout(to_dev_tc(mlp)), n_items).total;
 }
 
 int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
@@ -782,16 +893,27 @@ int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
         if (net.w[l] != 128) return SSSGS_ERR_UNSUPPORTED;
     int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
     if (n == 0) return SSSGS_OK;
-    if (!workspace || workspace_bytes < (size_t)T.gtotal + 256) return SSSGS_ERR_WORKSPACE;
-    uint8_t* gimg = (uint8_t*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    if (n >= ((int64_t)1 << 32)) return SSSGS_ERR_INVALID_ARG;    // row list holds u32 item ids
+    const TcBwdWs W = tc_bwd_ws(T, n);
+    if (!workspace || workspace_bytes < W.total) return SSSGS_ERR_WORKSPACE;
+    uint8_t* base = (uint8_t*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    uint8_t* gimg = base + W.img;
+    uint32_t* active = (uint32_t*)(base + W.active);
+    uint32_t* cnt = (uint32_t*)(base + W.cnt);
+    uint32_t* off = (uint32_t*)(base + W.off);
+    uint32_t* nact = (uint32_t*)(base + W.nact);
     cudaStream_t st = (cudaStream_t)stream;
     k_mlp_weights_bf16<<<dim3(32, net.L), 256, 0, st>>>(net, T, gimg);
-    sssgs::note_launches(1);
+    const int nb = (int)((n + ACT_BLOCK - 1) / ACT_BLOCK);
+    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(drec, n, cnt, dx_items);
+    k_active_scan<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
+    k_active_write<<<nb, ACT_BLOCK, 0, st>>>(drec, n, off, active);
+    sssgs::note_launches(4);
     cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
     int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
     k_mlp_bwd_tc<<<grid, 2 * TC_THREADS, T.total, st>>>(net, T, gimg, d_pairs, n_pairs, n, *scene, drec, *grad,
-                                                    dx_items, d_status);
+                                                    dx_items, active, nact, d_status);
     sssgs::note_launches(1);
     return launch_status();
 }
