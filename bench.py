@@ -218,6 +218,28 @@ FLOP_SHADE_BWD = 300
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes (read + write) per 300K / 800x800 pair of the fused render kernels,
+# from one ncu capture of a single pair (profiles/k_composite_*_warp_300k_800_
+# single_pair.md). Valid only for the kernel source they were taken on (its
+# sha256) and for workloads made of such pairs; otherwise traffic is null.
+KERNEL_TRAFFIC = {
+    "render_bwd": ("raster.cu", "6707d509833062775f15bf8cf915c021f5fabb3ef2db3ea9a2c72ad147dbab22", 96.0e6),
+    "render_fwd": ("raster.cu", "6707d509833062775f15bf8cf915c021f5fabb3ef2db3ea9a2c72ad147dbab22", 27.8e6),
+}
+
+
+def kernel_traffic(stage, workload, n_pairs):
+    import hashlib
+    if stage not in KERNEL_TRAFFIC or workload not in ("c3", "c4"):
+        return None
+    src, sha, per_pair = KERNEL_TRAFFIC[stage]
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2408_12282_gb300", "csrc", src)
+    with open(path, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != sha:
+            return None
+    return per_pair * n_pairs
+
+
 def mlp_flops(widths, rows):
     f = 0
     for a, b in zip(widths[:-1], widths[1:]):
@@ -371,7 +393,8 @@ def run_ours(args):
     elif dom in alu_flops:
         ach = alu_flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / ALU_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / ALU_PEAK_TFLOPS, "traffic": kernel_traffic(dom, args.workload, n_pairs),
+                "traffic_unit": "DRAM bytes per launch (ncu, scaled from one pair)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
                 "work": {"contributions": contrib_b if dom == "render_bwd" else contrib_f,
                          "alpha_evaluations": evals_b if dom == "render_bwd" else evals_f},
