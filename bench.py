@@ -178,9 +178,12 @@ def _config(args):
         "c5": "8 blob scenes of 50K-1M Gaussians x 8 view/light pairs each, resolutions drawn from "
               "{400,800,1200,1600}^2, PE6 MLP 64-128x4-4",
     }
-    return {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
-            "loss": "L1 vs target rendered from perturbed parameters",
-            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
+    cfg = {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
+           "loss": "L1 vs target rendered from perturbed parameters",
+           "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
+    if args.pairs is not None:
+        cfg["pairs_override"] = args.pairs
+    return cfg
 
 
 # ---------------------------------------------------------------------------- our arm
@@ -219,12 +222,13 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes (read + write) per 300K / 800x800 pair of the fused render kernels,
-# from one ncu capture of a single pair (profiles/k_composite_*_warp_300k_800_
-# single_pair.md). Valid only for the kernel source they were taken on (its
-# sha256) and for workloads made of such pairs; otherwise traffic is null.
+# from one ncu capture of an 8-pair launch of the same scene
+# (profiles/k_composite_*_warp_300k_800_8pairs.md), divided by 8. Valid only
+# for the kernel source they were taken on (its sha256) and for workloads made
+# of such pairs; otherwise traffic is null.
 KERNEL_TRAFFIC = {
-    "render_bwd": ("raster.cu", "6707d509833062775f15bf8cf915c021f5fabb3ef2db3ea9a2c72ad147dbab22", 96.0e6),
-    "render_fwd": ("raster.cu", "6707d509833062775f15bf8cf915c021f5fabb3ef2db3ea9a2c72ad147dbab22", 27.8e6),
+    "render_bwd": ("raster.cu", "f916edb66ae511705e8da6ad99852265fd0e890b51df05ef39ebab98b7a5e026", 107.7e6),
+    "render_fwd": ("raster.cu", "f916edb66ae511705e8da6ad99852265fd0e890b51df05ef39ebab98b7a5e026", 70.85e6),
 }
 
 
@@ -265,7 +269,7 @@ def run_ours(args):
     B.load_library()
     hbm, bf16_burst, bf16_sus, peak_src = _peaks()
 
-    wl = sg.make_workload(args.workload, seed_offset=rank)
+    wl = sg.make_workload(args.workload, seed_offset=rank, n_pairs=args.pairs)
     precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
     try:
         r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
@@ -508,6 +512,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="override the number of view/light pairs (smaller cases for profiling)")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--fp32-mlp", action="store_true")
     ap.add_argument("--plain-pairs", type=int, default=4)

@@ -72,8 +72,10 @@ enum {
 
 /* Record layout (floats): 0 mx, 1 my, 2 ca, 3 cb, 4 cc, 5 opacity,
  * 6..20 features (6 depth, 7-9 n, 10-12 base, 13 rough, 14 metal, 15 sss,
- * 16-18 L_SSS, 19 L_in, 20 vis), 21..23 zero. The gradient record has the
- * same layout (d/dmx ... d/dvis). */
+ * 16-18 L_SSS, 19 L_in, 20 vis), 21 1/ca, 22 1/cc, 23 1.001 ln(o/alpha_min)
+ * + 0.01 (culling constants the render kernels read; sssgs_project_fwd
+ * writes them). The gradient record has the layout of fields 0..20
+ * (d/dmx ... d/dvis); its fields 21..23 stay zero. */
 
 /* Render conventions. Defaults (sssgs_cfg_default): tile 16, dilation 0.3 px^2,
  * det_eps 1e-6 px^4, z_near 0.2, alpha_min 1/255, alpha_max 0.99, T_min 1e-4,

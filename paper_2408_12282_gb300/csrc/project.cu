@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(256) k_project_fwd(sssgs_cfg cfg, const sssgs_
     o[2] = make_float4(n[1], n[2], b[0], b[1]);
     o[3] = make_float4(b[2], sc.rough[g], sc.metal[g], sc.sss[g]);
     o[4] = make_float4(mo[0], mo[1], mo[2], mo[3]);
-    o[5] = make_float4(sc.vis[g], 0.f, 0.f, 0.f);
+    // tile / sub-tile culling constants of the render kernels: 1/ca, 1/cc and
+    // the padded support level of {p <= ln(o / alpha_min)}
+    o[5] = make_float4(sc.vis[g], 1.f / ca, 1.f / cc, L * 1.001f + 0.01f);
 }
 
 // One thread per scene Gaussian; sums the gradient of every pair rendering it.

@@ -178,13 +178,13 @@ __device__ __forceinline__ TilePix tile_pixel(const sssgs_pair& P, int tile, int
 // Conservative test: does the support ellipse {p <= L} of a splat (mean m,
 // conic (a, b, c)) reach the box of pixel centres [x0,x1] x [y0,y1]? The
 // minimum of the convex p over the box is at the mean if it lies inside,
-// else on an edge (1-D minimum clamped to the edge). L is padded so float32
-// rounding of the per-pixel test can never pass where this one fails.
-__device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, float b, float c, float L,
-                                                  float x0, float x1, float y0, float y1) {
+// else on an edge (1-D minimum clamped to the edge). ia = 1/a, ic = 1/c and
+// lim = 1.001 L + 0.01 come precomputed in the record (fields 21..23); the
+// padding keeps float32 rounding of the per-pixel test from passing where
+// this one fails.
+__device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, float b, float c, float ia, float ic,
+                                                  float lim, float x0, float x1, float y0, float y1) {
     if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
-    const float lim = L * 1.001f + 0.01f;
-    const float ia = 1.f / a, ic = 1.f / c;
     float best = 3.0e38f;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -204,16 +204,16 @@ __device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, f
 // Bit w set: the splat can reach warp w's SW x SH sub-tile of this tile
 // (sub-tiles numbered row-major, TILE / SW across).
 template <int TILE, int SW = 8, int SH = 4>
-__device__ __forceinline__ uint32_t subtile_mask(const sssgs_pair& P, int tile, float4 g0, float4 g1, float a_min) {
+__device__ __forceinline__ uint32_t subtile_mask(const sssgs_pair& P, int tile, float4 g0, float4 g1, float4 g5) {
     constexpr int PER_ROW = TILE / SW, NW = (TILE / SW) * (TILE / SH);
     const int lt = tile - P.tile_offset;
     const float bx = (float)((lt % P.tiles_x) * TILE) + 0.5f, by = (float)((lt / P.tiles_x) * TILE) + 0.5f;
-    const float L = logf(g1.y / a_min);
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const float x0 = bx + (float)((w % PER_ROW) * SW), y0 = by + (float)((w / PER_ROW) * SH);
-        if (ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, L, x0, x0 + (float)(SW - 1), y0, y0 + (float)(SH - 1)))
+        if (ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + (float)(SW - 1), y0,
+                              y0 + (float)(SH - 1)))
             m |= 1u << w;
     }
     return m;
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, co
             const float4* r = rec + 6 * (int64_t)vals[idx];
 #pragma unroll
             for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
-            s_mask[threadIdx.x] = subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], a_min);
+            s_mask[threadIdx.x] =
+                subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], s_rec[5 * B + threadIdx.x]);
         }
         __syncthreads();
         const int nb = min(B, (int)(rg.y - b0));
@@ -396,8 +397,8 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
             cp_async_wait1();
             bool pass = false;
             if (it0 != NONE) {
-                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane];
-                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, logf(g1.y / a_min), x0, x0 + 7.f, y0,
+                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][5][lane];
+                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
                                          y0 + (float)(SH - 1));
             }
             uint32_t bits = __ballot_sync(SSSGS_FULL, pass);
@@ -612,7 +613,8 @@ __global__ void __launch_bounds__(TILE * TILE, SSSGS_BWD_MIN_BLOCKS) k_composite
             const float4* r = rec + 6 * (int64_t)item;
 #pragma unroll
             for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
-            s_mask[threadIdx.x] = subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], a_min);
+            s_mask[threadIdx.x] =
+                subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], s_rec[5 * B + threadIdx.x]);
         }
         __syncthreads();
         if (__any_sync(SSSGS_FULL, lastc > b0)) {
@@ -847,9 +849,8 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
             cp_async_wait1();
             bool pass = false;
             if (it0 != NONE) {
-                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane];
-                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, logf(g1.y / a_min), x0, x0 + 7.f, y0,
-                                         y0 + 7.f);
+                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][5][lane];
+                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0, y0 + 7.f);
             }
             s_item[buf][lane] = it0;
             uint32_t bits = __ballot_sync(SSSGS_FULL, pass);

@@ -56,6 +56,10 @@ def test_projection_records_match_oracle():
     orc = np.stack([rect[:, 0] // t, rect[:, 1] // t, rect[:, 2] // t, rect[:, 3] // t], 1)
     assert np.all(grect[valid, 0] <= orc[valid, 0]) and np.all(grect[valid, 1] >= orc[valid, 1])
     assert np.all(grect[valid, 2] <= orc[valid, 2]) and np.all(grect[valid, 3] >= orc[valid, 3])
+    # culling constants: 1/ca, 1/cc, padded support level ln(o / alpha_min)
+    np.testing.assert_allclose(rec[valid, 21], 1.0 / proj[valid, 2], rtol=2e-4)
+    np.testing.assert_allclose(rec[valid, 22], 1.0 / proj[valid, 4], rtol=2e-4)
+    np.testing.assert_allclose(rec[valid, 23], 1.001 * proj[valid, 7] + 0.01, rtol=1e-5, atol=1e-5)
     # features copied verbatim
     np.testing.assert_array_equal(rec[:, 7:10], wl.scenes[0].normal)
     np.testing.assert_array_equal(rec[:, 13], wl.scenes[0].rough)
