@@ -712,31 +712,6 @@ struct PixBwd {
     uint32_t lastc;
 };
 
-// Branch-free back-to-front replay step of one splat at one pixel. `act`:
-// the pixel takes the splat (list position below its last contributor and
-// alpha test passed); otherwise the state is left as is and the returned
-// terms are 0. Returns w = alpha T_i (the pixel's weight of the splat's
-// features), dp = dL/dp (p the Gaussian exponent) and dg = dL/do.
-struct BwdStep {
-    float w, dp, dg;
-};
-__device__ __forceinline__ BwdStep bwd_step(PixBwd& p, const AlphaEval& e, bool act, const float* f) {
-    float dot = 0.f;
-#pragma unroll
-    for (int c = 0; c < SSSGS_NF; ++c) dot += p.dF[c] * f[c];
-    const float ia = rcp_newton(1.f - e.alpha);
-    const float Ti = p.T * ia;
-    const float da = Ti * dot - p.Q * ia;
-    const bool geo = act && !e.clamped;
-    BwdStep r;
-    r.w = act ? e.alpha * Ti : 0.f;
-    r.dp = geo ? -da * e.alpha : 0.f;
-    r.dg = geo ? da * e.G : 0.f;
-    p.Q += r.w * dot;
-    p.T = act ? Ti : p.T;
-    return r;
-}
-
 template <int MODE>
 __device__ __forceinline__ void bwd_pixel_setup(PixBwd& p, bool inside, int64_t pix, float fx, float fy,
                                                 const sssgs_pair& P,
@@ -820,6 +795,19 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
     const uint32_t wmax = __reduce_max_sync(SSSGS_FULL, max(p[0].lastc, p[1].lastc));
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
     const float px_x = i + 0.5f, px_y0 = j0 + 0.5f;     // centres of this lane's two pixels (y and y + 1)
+    // The two pixels' replay state in float2 form for the paired FP32
+    // instructions: dF of each pixel as component pairs (2k, 2k+1), the last
+    // pair padded with 0; T and Q as (pixel 0, pixel 1).
+    float2 dF0[8], dF1[8];
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk) {
+        dF0[kk] = make_float2(p[0].dF[2 * kk], p[0].dF[2 * kk + 1]);
+        dF1[kk] = make_float2(p[1].dF[2 * kk], p[1].dF[2 * kk + 1]);
+    }
+    dF0[7] = make_float2(p[0].dF[14], 0.f);
+    dF1[7] = make_float2(p[1].dF[14], 0.f);
+    float2 Tp = make_float2(p[0].T, p[1].T), Qp = make_float2(p[0].Q, p[1].Q);
+    const uint32_t last0 = p[0].lastc, last1 = p[1].lastc;
     const float x0 = bx + 0.5f, y0 = by + 0.5f;
     uint32_t n_use = 0;
     if (wmax > rg.x) {
@@ -863,36 +851,78 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                 const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
                 const AlphaEval e0 = eval_alpha(g0, g1, px_x, px_y0, a_min, a_max);
                 const AlphaEval e1 = eval_alpha(g0, g1, px_x, px_y0 + 1.f, a_min, a_max);
-                const bool act0 = (pos < p[0].lastc) && e0.use;
-                const bool act1 = (pos < p[1].lastc) && e1.use;
+                const bool act0 = (pos < last0) && e0.use;
+                const bool act1 = (pos < last1) && e1.use;
                 if (!__any_sync(SSSGS_FULL, act0 || act1)) continue;
                 {   // both pixels' terms, summed, straight into this lane's reduction column
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
                     const float g5 = s_rec[buf][5][k].x;
-                    const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
-                                               g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
-                    const BwdStep s0 = bwd_step(p[0], e0, act0, f), s1 = bwd_step(p[1], e1, act1, f);
+                    const float2 fp[8] = {make_float2(g1.z, g1.w), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w),
+                                          make_float2(g3.x, g3.y), make_float2(g3.z, g3.w), make_float2(g4.x, g4.y),
+                                          make_float2(g4.z, g4.w), make_float2(g5, 0.f)};
+                    // dF . f of each pixel (even and odd components summed separately)
+                    float2 d0 = __fmul2_rn(dF0[0], fp[0]), d1 = __fmul2_rn(dF1[0], fp[0]);
+#pragma unroll
+                    for (int kk = 1; kk < 8; ++kk) {
+                        d0 = __ffma2_rn(dF0[kk], fp[kk], d0);
+                        d1 = __ffma2_rn(dF1[kk], fp[kk], d1);
+                    }
+                    const float2 dot = make_float2(d0.x + d0.y, d1.x + d1.y);
+                    // replay step: T_i = T_{i+1} / (1 - alpha), dL/dalpha = T_i dot - Q / (1 - alpha)
+                    const float2 ia = make_float2(rcp_newton(1.f - e0.alpha), rcp_newton(1.f - e1.alpha));
+                    const float2 alp = make_float2(e0.alpha, e1.alpha);
+                    const float2 Ti = __fmul2_rn(Tp, ia);
+                    const float2 qa = __fmul2_rn(Qp, ia);
+                    const float2 da = __ffma2_rn(Ti, dot, make_float2(-qa.x, -qa.y));
+                    const float2 wr = __fmul2_rn(alp, Ti);
+                    const float2 dpr = __fmul2_rn(make_float2(-da.x, -da.y), alp);
+                    const float2 dgr = __fmul2_rn(da, make_float2(e0.G, e1.G));
+                    const bool geo0 = act0 && !e0.clamped, geo1 = act1 && !e1.clamped;
+                    const float2 w = make_float2(act0 ? wr.x : 0.f, act1 ? wr.y : 0.f);
+                    const float2 dp = make_float2(geo0 ? dpr.x : 0.f, geo1 ? dpr.y : 0.f);
+                    const float2 dg = make_float2(geo0 ? dgr.x : 0.f, geo1 ? dgr.y : 0.f);
+                    Qp = __ffma2_rn(w, dot, Qp);
+                    Tp = make_float2(act0 ? Ti.x : Tp.x, act1 ? Ti.y : Tp.y);
                     n_use += (uint32_t)act0 + (uint32_t)act1;
                     float* col = s_red + lane;
+                    // features: w0 dF0 + w1 dF1, component pairs
+                    const float2 w0b = make_float2(w.x, w.x), w1b = make_float2(w.y, w.y);
 #pragma unroll
-                    for (int c = 0; c < SSSGS_NF; ++c) col[(6 + c) * RS] = s0.w * p[0].dF[c] + s1.w * p[1].dF[c];
-                    col[0] = s0.dp * (g0.z * e0.dx + g0.w * e0.dy) + s1.dp * (g0.z * e1.dx + g0.w * e1.dy);
-                    col[RS] = s0.dp * (g0.w * e0.dx + g1.x * e0.dy) + s1.dp * (g0.w * e1.dx + g1.x * e1.dy);
-                    col[2 * RS] = 0.5f * (s0.dp * e0.dx * e0.dx + s1.dp * e1.dx * e1.dx);
-                    col[3 * RS] = s0.dp * e0.dx * e0.dy + s1.dp * e1.dx * e1.dy;
-                    col[4 * RS] = 0.5f * (s0.dp * e0.dy * e0.dy + s1.dp * e1.dy * e1.dy);
-                    col[5 * RS] = s0.dg + s1.dg;
+                    for (int kk = 0; kk < 7; ++kk) {
+                        const float2 cv = __ffma2_rn(w1b, dF1[kk], __fmul2_rn(w0b, dF0[kk]));
+                        col[(6 + 2 * kk) * RS] = cv.x;
+                        col[(7 + 2 * kk) * RS] = cv.y;
+                    }
+                    col[20 * RS] = w.x * dF0[7].x + w.y * dF1[7].x;
+                    // geometry: the two pixels share dx (same column)
+                    const float dx = e0.dx;
+                    const float2 dy = make_float2(e0.dy, e1.dy);
+                    const float ca = g0.z, cb = g0.w, cc = g1.x;
+                    const float2 u = __ffma2_rn(make_float2(cb, cb), dy, make_float2(ca * dx, ca * dx));
+                    const float2 v = __ffma2_rn(make_float2(cc, cc), dy, make_float2(cb * dx, cb * dx));
+                    const float2 pdy = __fmul2_rn(dp, dy);
+                    col[0] = dp.x * u.x + dp.y * u.y;
+                    col[RS] = dp.x * v.x + dp.y * v.y;
+                    col[2 * RS] = 0.5f * dx * dx * (dp.x + dp.y);
+                    col[3 * RS] = dx * (pdy.x + pdy.y);
+                    col[4 * RS] = 0.5f * (pdy.x * dy.x + pdy.y * dy.y);
+                    col[5 * RS] = dg.x + dg.y;
                 }
                 __syncwarp();
-                if (lane < NG) {
+                if (lane < NG) {   // sum of the 32 lanes' terms, in pairs
                     const float4* row = reinterpret_cast<const float4*>(s_red + lane * RS);
-                    float4 a = row[0];
+                    float2 a[16];
 #pragma unroll
-                    for (int q = 1; q < 8; ++q) {
-                        const float4 bq = row[q];
-                        a.x += bq.x; a.y += bq.y; a.z += bq.z; a.w += bq.w;
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 v = row[q];
+                        a[2 * q] = make_float2(v.x, v.y);
+                        a[2 * q + 1] = make_float2(v.z, v.w);
                     }
-                    atomicAdd(drec + (int64_t)SSSGS_REC * s_item[buf][k] + lane, (a.x + a.y) + (a.z + a.w));
+#pragma unroll
+                    for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+                        for (int q = 0; q < h; ++q) a[q] = __fadd2_rn(a[q], a[q + h]);
+                    atomicAdd(drec + (int64_t)SSSGS_REC * s_item[buf][k] + lane, a[0].x + a[0].y);
                 }
                 __syncwarp();
             }
@@ -903,7 +933,7 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
     }
     if (stats) {
         unsigned long long u = n_use;
-        unsigned long long v = (p[0].lastc > rg.x ? p[0].lastc - rg.x : 0) + (p[1].lastc > rg.x ? p[1].lastc - rg.x : 0);
+        unsigned long long v = (last0 > rg.x ? last0 - rg.x : 0) + (last1 > rg.x ? last1 - rg.x : 0);
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
             u += __shfl_xor_sync(SSSGS_FULL, u, o);
