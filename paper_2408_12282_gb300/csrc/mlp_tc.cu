@@ -314,7 +314,8 @@ __device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c,
 // chain are 0 * finite = 0, and bf16(0) = 0. Gaussians hidden behind the
 // surface in a view never contribute to a pixel, so their rows are zero. The
 // backward therefore runs on the list of the other rows, in item order
-// (deterministic: count, scan, write), and writes dx_items = 0 for the rest.
+// (deterministic: count with a flag byte per item, scan, write), and writes
+// dx_items = 0 for the rest.
 constexpr int ACT_BLOCK = 1024;
 
 __device__ __forceinline__ bool row_active(const float* __restrict__ drec, int64_t m) {
@@ -323,9 +324,11 @@ __device__ __forceinline__ bool row_active(const float* __restrict__ drec, int64
 }
 
 __global__ void __launch_bounds__(ACT_BLOCK) k_active_count(const float* __restrict__ drec, int64_t n,
-                                                            uint32_t* __restrict__ cnt, float* __restrict__ dx_items) {
+                                                            uint32_t* __restrict__ cnt, uint8_t* __restrict__ flag,
+                                                            float* __restrict__ dx_items) {
     const int64_t m = (int64_t)blockIdx.x * ACT_BLOCK + threadIdx.x;
     const bool a = m < n && row_active(drec, m);
+    if (m < n) flag[m] = a ? 1 : 0;
     if (m < n && !a) {
 #pragma unroll
         for (int k = 0; k < 7; ++k) dx_items[7 * m + k] = 0.f;
@@ -374,13 +377,13 @@ __global__ void __launch_bounds__(1024) k_active_scan(const uint32_t* __restrict
     if (threadIdx.x == 0) *n_active = carry;
 }
 
-__global__ void __launch_bounds__(ACT_BLOCK) k_active_write(const float* __restrict__ drec, int64_t n,
+__global__ void __launch_bounds__(ACT_BLOCK) k_active_write(const uint8_t* __restrict__ flag, int64_t n,
                                                             const uint32_t* __restrict__ off,
                                                             uint32_t* __restrict__ active) {
     __shared__ uint32_t wcnt[ACT_BLOCK / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t m = (int64_t)blockIdx.x * ACT_BLOCK + threadIdx.x;
-    const bool a = m < n && row_active(drec, m);
+    const bool a = m < n && flag[m] != 0;
     const uint32_t bal = __ballot_sync(SSSGS_FULL, a);
     if (lane == 0) wcnt[warp] = (uint32_t)__popc(bal);
     __syncthreads();
@@ -866,7 +869,7 @@ namespace {
 // Backward workspace: BF16 weight images, then the active-row list, the
 // per-block counts and offsets, and the active-row count.
 struct TcBwdWs {
-    size_t img, active, cnt, off, nact, total;
+    size_t img, active, flag, cnt, off, nact, total;
 };
 TcBwdWs tc_bwd_ws(const TcBwdLayout& T, int64_t n_items) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -875,6 +878,7 @@ TcBwdWs tc_bwd_ws(const TcBwdLayout& T, int64_t n_items) {
     size_t o = 0;
     w.img = o;    o += al(T.gtotal);
     w.active = o; o += al(4 * (size_t)n_items);
+    w.flag = o;   o += al((size_t)n_items);
     w.cnt = o;    o += al(4 * nb);
     w.off = o;    o += al(4 * nb);
     w.nact = o;   o += 256;
@@ -905,15 +909,16 @@ int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     uint8_t* base = (uint8_t*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
     uint8_t* gimg = base + W.img;
     uint32_t* active = (uint32_t*)(base + W.active);
+    uint8_t* flag = base + W.flag;
     uint32_t* cnt = (uint32_t*)(base + W.cnt);
     uint32_t* off = (uint32_t*)(base + W.off);
     uint32_t* nact = (uint32_t*)(base + W.nact);
     cudaStream_t st = (cudaStream_t)stream;
     k_mlp_weights_bf16<<<dim3(32, net.L), 256, 0, st>>>(net, T, gimg);
     const int nb = (int)((n + ACT_BLOCK - 1) / ACT_BLOCK);
-    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(drec, n, cnt, dx_items);
+    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(drec, n, cnt, flag, dx_items);
     k_active_scan<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
-    k_active_write<<<nb, ACT_BLOCK, 0, st>>>(drec, n, off, active);
+    k_active_write<<<nb, ACT_BLOCK, 0, st>>>(flag, n, off, active);
     sssgs::note_launches(4);
     cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
     int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
