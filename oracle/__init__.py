@@ -121,18 +121,32 @@ def _normalize(v):
     return v / n, n
 
 
-def mlp_inputs(kind, mu, normal, vis, cam_center, light):
+LRELU_SLOPE = 0.01      # Leaky-ReLU negative slope of the paper's network (not stated; PyTorch default)
+
+
+def mlp_inputs(kind, mu, normal, vis, cam_center, light, quat=None, log_s=None):
     """Per-Gaussian network input for one view/light pair.
 
     basic: [mu, w_out, w_in] (9)
     pe6:   [sin(2^k pi mu), cos(2^k pi mu) for k < 6 (36), mu (3), w_out (3),
             w_in (3), n (3), |light - mu| (1), v (1)] = 50, zero-padded to 64.
+    paper: [n (3), unit(q) (4), exp(log_s) (3), w_in (3), w_out (3),
+            |light - mu| (1), v (1), sin(2^k pi mu), cos(2^k pi mu) for k < 4
+            (24)] = 42, zero-padded to 48 (App. E "Network").
     w_out = unit(camera - mu), w_in = unit(light - mu).
     """
     wo, _ = _normalize(np.asarray(cam_center)[None, :] - mu)
     wi, dl = _normalize(np.asarray(light)[None, :] - mu)
     if kind == "basic":
         return np.concatenate([mu, wo, wi], axis=1)
+    if kind == "paper":
+        qn, _ = _normalize(np.asarray(quat, np.float64))
+        feats = [normal, qn, np.exp(log_s), wi, wo, dl, vis[:, None]]
+        for k in range(4):
+            feats.append(np.sin((2.0 ** k) * math.pi * mu))
+            feats.append(np.cos((2.0 ** k) * math.pi * mu))
+        X = np.concatenate(feats, axis=1)
+        return np.concatenate([X, np.zeros((X.shape[0], 6))], axis=1)
     feats = []
     for k in range(6):
         feats.append(np.sin((2.0 ** k) * math.pi * mu))
@@ -141,9 +155,40 @@ def mlp_inputs(kind, mu, normal, vis, cam_center, light):
     return np.concatenate([X, np.zeros((X.shape[0], 14))], axis=1)
 
 
+def _lrelu(z):
+    return np.where(z > 0, z, LRELU_SLOPE * z)
+
+
+def _dlrelu(a):
+    """Leaky-ReLU derivative from the activation (same sign as the input)."""
+    return np.where(a > 0, 1.0, LRELU_SLOPE)
+
+
 def mlp_forward(spec, X, bf16=False):
-    """Linear/ReLU chain; heads: sigmoid -> L_SSS (3), ReLU -> L_in (1)."""
+    """basic / pe6: Linear/ReLU chain; heads: sigmoid -> L_SSS (3), ReLU -> L_in (1).
+    paper: trunk of three Linear + Leaky-ReLU layers (W0..W2); incident head
+    Linear + Leaky-ReLU (W3) then Linear + ReLU -> L_in (W4); SSS head
+    Linear + sigmoid -> L_SSS (W5), both on the trunk output. Returns the
+    layer inputs `acts`, the head pre-activations y = [SSS (3), incident (1)]
+    and the outputs."""
     rnd = bf16_round if bf16 else (lambda a: a)
+    if spec.kind == "paper":
+        W = [rnd(np.asarray(w, np.float64)) for w in spec.weights]
+        b = [np.asarray(v, np.float64) for v in spec.biases]
+        h = rnd(X)
+        acts = [h]
+        for l in range(3):
+            h = rnd(_lrelu(h @ W[l].T + b[l]))
+            acts.append(h)
+        t = h
+        hid = rnd(_lrelu(t @ W[3].T + b[3]))
+        acts.append(hid)
+        zi = hid @ W[4].T + b[4]
+        zs = t @ W[5].T + b[5]
+        y = np.concatenate([zs, zi], axis=1)
+        Ls = 1.0 / (1.0 + np.exp(-y[:, :3]))
+        Lin = np.maximum(y[:, 3], 0.0)
+        return acts, y, Ls, Lin
     h = rnd(X)
     acts = [h]
     nl = len(spec.weights)
@@ -169,6 +214,8 @@ def mlp_backward(spec, acts, y, Ls, dLs, dLin, bf16=False):
     bias gradient db = sum over rows of dz, i.e. every use of dz sees the same
     bf16 value, as when dz is stored in bf16 once."""
     rnd = bf16_round if bf16 else (lambda a: a)
+    if spec.kind == "paper":
+        return _paper_backward(spec, acts, y, Ls, dLs, dLin, rnd)
     nl = len(spec.weights)
     dz = np.zeros_like(y)
     dz[:, :3] = dLs * Ls * (1.0 - Ls)
@@ -188,8 +235,34 @@ def mlp_backward(spec, acts, y, Ls, dLs, dLin, bf16=False):
     return dWs, dbs, dX
 
 
-def input_grads(kind, dX, mu, cam_center, light):
-    """Map dLoss/dX to (dmu, dn, dv) through the input encoding."""
+def _paper_backward(spec, acts, y, Ls, dLs, dLin, rnd):
+    """Backward of the paper network (same bf16 convention as the chain:
+    every pre-activation gradient is rounded once and used everywhere)."""
+    W = [rnd(np.asarray(w, np.float64)) for w in spec.weights]
+    X, h1, h2, t, hid = acts
+    dWs, dbs = [None] * 6, [None] * 6
+    dzs = rnd(dLs * Ls * (1.0 - Ls))                       # SSS head
+    dzi = rnd((dLin * (y[:, 3] > 0))[:, None])              # incident output
+    dWs[5], dbs[5] = dzs.T @ t, dzs.sum(axis=0)
+    dWs[4], dbs[4] = dzi.T @ hid, dzi.sum(axis=0)
+    dzh = rnd((dzi @ W[4]) * _dlrelu(hid))                 # incident hidden
+    dWs[3], dbs[3] = dzh.T @ t, dzh.sum(axis=0)
+    dt = dzs @ W[5] + dzh @ W[3]
+    hs = [X, h1, h2, t]
+    dz = rnd(dt * _dlrelu(t))
+    for l in range(2, -1, -1):
+        dWs[l], dbs[l] = dz.T @ hs[l], dz.sum(axis=0)
+        dh = dz @ W[l]
+        if l > 0:
+            dz = rnd(dh * _dlrelu(hs[l]))
+        else:
+            dX = dh
+    return dWs, dbs, dX
+
+
+def input_grads(kind, dX, mu, cam_center, light, quat=None, log_s=None):
+    """Map dLoss/dX to (dmu, dn, dv) through the input encoding; for the
+    paper network also (dquat, dlog_s): (dmu, dn, dv, dq, dls)."""
     Vo = np.asarray(cam_center)[None, :] - mu
     Vi = np.asarray(light)[None, :] - mu
     wo, lo = _normalize(Vo)
@@ -201,6 +274,21 @@ def input_grads(kind, dX, mu, cam_center, light):
     if kind == "basic":
         dmu = dX[:, 0:3] + back_unit(wo, lo, dX[:, 3:6]) + back_unit(wi, li, dX[:, 6:9])
         return dmu, np.zeros_like(mu), np.zeros(mu.shape[0])
+    if kind == "paper":
+        q = np.asarray(quat, np.float64)
+        qn, ql = _normalize(q)
+        gq = dX[:, 3:7]
+        dq = (gq - qn * np.sum(qn * gq, axis=1, keepdims=True)) / ql
+        dls = dX[:, 7:10] * np.exp(log_s)
+        dmu = back_unit(wi, li, dX[:, 10:13]) + back_unit(wo, lo, dX[:, 13:16]) - dX[:, 16:17] * wi
+        col = 18
+        for k in range(4):
+            f = (2.0 ** k) * math.pi
+            dmu += dX[:, col:col + 3] * f * np.cos(f * mu)
+            col += 3
+            dmu -= dX[:, col:col + 3] * f * np.sin(f * mu)
+            col += 3
+        return dmu, dX[:, 0:3].copy(), dX[:, 17].copy(), dq, dls
     dmu = np.zeros_like(mu)
     col = 0
     for k in range(6):
@@ -252,7 +340,7 @@ def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=No
     N = scene.N
     C = pair.center
     kind = spec.kind
-    X = mlp_inputs(kind, scene.mu, scene.normal, scene.vis, C, pair.light)
+    X = mlp_inputs(kind, scene.mu, scene.normal, scene.vis, C, pair.light, scene.quat, scene.log_s)
     acts, y, Ls, Lin = mlp_forward(spec, X, bf16=bf16)
     if mlp_out is not None:      # external network output (tests of the raster alone)
         Ls, Lin = mlp_out[:, :3], mlp_out[:, 3]
@@ -299,10 +387,13 @@ def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=No
     out["dmlp_out"] = np.concatenate([dLs, dLin[:, None]], axis=1)
     if mlp_out is None:
         dWs, dbs, dX = mlp_backward(spec, acts, y, Ls, dLs, dLin, bf16=bf16)
-        dmu, dn, dv = input_grads(kind, dX, scene.mu, C, pair.light)
-        g["mu"] += dmu
-        g["normal"] += dn
-        g["vis"] += dv
+        gi = input_grads(kind, dX, scene.mu, C, pair.light, scene.quat, scene.log_s)
+        g["mu"] += gi[0]
+        g["normal"] += gi[1]
+        g["vis"] += gi[2]
+        if kind == "paper":
+            g["quat"] += gi[3]
+            g["log_s"] += gi[4]
         out["dW"], out["db"] = dWs, dbs
     out["dgeom"], out["dfeat"] = dgeom, dfeat
     out["grads"] = g

@@ -92,7 +92,7 @@ class Pair:
 @dataclass
 class MLPSpec:
     """Residual / incident-light MLP: layer weights W[l] (out x in) and b[l]."""
-    kind: str                 # "basic" (9 inputs) or "pe6" (50 inputs padded to 64)
+    kind: str                 # "basic" (9 inputs), "pe6" (50 padded to 64) or "paper" (42 padded to 48)
     n_in: int                 # input width seen by the first layer
     widths: list              # hidden widths
     weights: list = field(default_factory=list)
@@ -265,8 +265,24 @@ def perturbed(scene: Scene, seed: int) -> Scene:
 def mlp_spec(seed: int, kind: str, widths, precision="fp32", std=None) -> MLPSpec:
     """Weights ~ N(0, std) (0.1 by default, He-scaled for 128-wide layers);
     biases 0 except the incident-light output, biased +0.5 so most Gaussians
-    receive light at initialisation."""
+    receive light at initialisation.
+
+    kind "paper" (widths ignored): the six matrices of the paper's network in
+    the order W0 64x48, W1 32x64, W2 32x32 (trunk), W3 32x32 (incident
+    hidden), W4 1x32 (incident output), W5 3x32 (SSS output), He-scaled."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "paper":
+        shapes = [(64, 48), (32, 64), (32, 32), (32, 32), (1, 32), (3, 32)]
+        fan_in = [42, 64, 32, 32, 32, 32]
+        Ws, bs = [], []
+        for (o, i), fi in zip(shapes, fan_in):
+            W = rng.normal(0.0, std if std is not None else math.sqrt(2.0 / fi), (o, i))
+            if i == 48:
+                W[:, 42:] = 0.0      # padded inputs carry no weight
+            Ws.append(f32(W))
+            bs.append(f32(np.zeros(o)))
+        bs[4] = f32(np.full(1, 0.5))
+        return MLPSpec(kind=kind, n_in=48, widths=[64, 32, 32], weights=Ws, biases=bs, precision=precision)
     n_in = 9 if kind == "basic" else 64
     dims = [n_in] + list(widths) + [4]
     Ws, bs = [], []
@@ -297,9 +313,20 @@ def _hemisphere_dir(rng, zmin=0.15):
 
 
 def make_workload(name: str, *, N: int | None = None, res=None,
-                  n_pairs: int | None = None, seed_offset: int = 0) -> Workload:
+                  n_pairs: int | None = None, seed_offset: int = 0, net: str | None = None) -> Workload:
     """Build configuration `name` ("c1".."c5"); N/res/n_pairs shrink it for tests.
-    For c5, `res` may be a tuple of resolutions to draw from."""
+    For c5, `res` may be a tuple of resolutions to draw from. net="paper"
+    replaces the configuration's network by the paper's (App. E), FP32."""
+    wl = _make_workload(name, N=N, res=res, n_pairs=n_pairs, seed_offset=seed_offset)
+    if net == "paper":
+        wl.mlp = mlp_spec(int(name[1]) * 1000 + seed_offset + 13, "paper", [])
+    elif net is not None:
+        raise ValueError(f"unknown network {net!r}")
+    return wl
+
+
+def _make_workload(name: str, *, N: int | None = None, res=None,
+                   n_pairs: int | None = None, seed_offset: int = 0) -> Workload:
     idx = int(name[1])
     seed = idx * 1000 + seed_offset
     rng = np.random.Generator(np.random.PCG64(seed + 7))

@@ -117,6 +117,31 @@ def test_fd_pe6_mlp_inputs_and_weights():
     assert not bad, bad[:5]
 
 
+def test_fd_paper_mlp_inputs_and_weights():
+    """The paper's network (Leaky-ReLU trunk, two heads): its inputs include
+    the rotation and scale, so quat and log_s gradients combine the projection
+    path and the network path."""
+    sc, pair, _ = _tiny(6)
+    spec = sg.mlp_spec(10, "paper", [])
+    dimg = sg.random_dimg(56, pair.W * pair.H)
+    r = O.render_pair(sc, pair, spec)
+    live = np.flatnonzero(r["rect"][:, 0] <= r["rect"][:, 1])
+    rng = np.random.default_rng(6)
+    picks = [("mu", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(6)]
+    picks += [("quat", (int(rng.choice(live)), int(rng.integers(4)))) for _ in range(6)]
+    picks += [("log_s", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(6)]
+    picks += [("normal", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(3)]
+    picks += [("vis", (int(rng.choice(live)),)) for _ in range(3)]
+    picks += [("W0", (int(rng.integers(64)), int(rng.integers(42)))) for _ in range(3)]
+    picks += [("W3", (int(rng.integers(32)), int(rng.integers(32)))) for _ in range(3)]
+    picks += [("W4", (0, int(rng.integers(32)))) for _ in range(2)]
+    picks += [("W5", (int(rng.integers(3)), int(rng.integers(32)))) for _ in range(3)]
+    picks += [("b4", (0,)), ("b5", (1,))]
+    used, bad = _fd_check(sc, pair, spec, picks, dimg)
+    assert used >= 0.8 * len(picks)
+    assert not bad, bad[:5]
+
+
 def test_fd_with_clamped_alpha_and_stop():
     """Dense, opaque Gaussians: alpha clamps at 0.99 and T-stops are common."""
     sc, pair, spec = _tiny(5, N=40, log_s_mean=-1.6)

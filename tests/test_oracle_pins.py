@@ -394,6 +394,74 @@ def test_input_encoding_gradients_match_autograd():
     assert np.allclose(vv.grad.numpy(), dv)
 
 
+def _paper_torch(spec):
+    """The paper's network (App. E "Network") assembled from torch.nn modules."""
+    import torch
+
+    def lin(W, b):
+        m = torch.nn.Linear(W.shape[1], W.shape[0]).double()
+        with torch.no_grad():
+            m.weight.copy_(torch.from_numpy(np.asarray(W, np.float64)))
+            m.bias.copy_(torch.from_numpy(np.asarray(b, np.float64)))
+        return m
+
+    L = [lin(W, b) for W, b in zip(spec.weights, spec.biases)]
+    act = torch.nn.LeakyReLU(O.LRELU_SLOPE)
+    trunk = torch.nn.Sequential(L[0], act, L[1], act, L[2], act)
+    incident = torch.nn.Sequential(L[3], act, L[4], torch.nn.ReLU())
+    sss = torch.nn.Sequential(L[5], torch.nn.Sigmoid())
+    return L, trunk, incident, sss
+
+
+def test_paper_mlp_matches_torch_modules_fp64():
+    import torch
+    spec = sg.mlp_spec(6, "paper", [])
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((300, 48))
+    acts, y, Ls, Lin = O.mlp_forward(spec, X)
+    L, trunk, incident, sss = _paper_torch(spec)
+    Xt = torch.from_numpy(X).requires_grad_(True)
+    t = trunk(Xt)
+    Lin_t, Ls_t = incident(t)[:, 0], sss(t)
+    assert np.allclose(Ls_t.detach().numpy(), Ls, rtol=1e-12, atol=1e-14)
+    assert np.allclose(Lin_t.detach().numpy(), Lin, rtol=1e-12, atol=1e-14)
+    dLs = rng.standard_normal((300, 3))
+    dLin = rng.standard_normal(300)
+    dWs, dbs, dX = O.mlp_backward(spec, acts, y, Ls, dLs, dLin)
+    ((Ls_t * torch.from_numpy(dLs)).sum() + (Lin_t * torch.from_numpy(dLin)).sum()).backward()
+    assert np.allclose(Xt.grad.numpy(), dX, rtol=1e-10, atol=1e-12)
+    for l, m in enumerate(L):
+        assert np.allclose(m.weight.grad.numpy(), dWs[l], rtol=1e-10, atol=1e-12), l
+        assert np.allclose(m.bias.grad.numpy(), dbs[l], rtol=1e-10, atol=1e-12), l
+
+
+def test_paper_input_encoding_and_gradients_match_autograd():
+    import math as m
+    import torch
+    wl = sg.make_workload("c3", N=60, res=32, net="paper")
+    sc, pair = wl.scenes[0], wl.pairs[0]
+    dX = np.random.default_rng(5).standard_normal((60, 48))
+    dmu, dn, dv, dq, dls = O.input_grads("paper", dX, sc.mu, pair.center, pair.light, sc.quat, sc.log_s)
+    mu = torch.from_numpy(sc.mu.astype(np.float64)).requires_grad_(True)
+    nn_ = torch.from_numpy(sc.normal.astype(np.float64)).requires_grad_(True)
+    vv = torch.from_numpy(sc.vis.astype(np.float64)).requires_grad_(True)
+    q = torch.from_numpy(sc.quat.astype(np.float64)).requires_grad_(True)
+    ls = torch.from_numpy(sc.log_s.astype(np.float64)).requires_grad_(True)
+    C, Lp = torch.from_numpy(pair.center), torch.from_numpy(pair.light)
+    wo = (C - mu) / (C - mu).norm(dim=1, keepdim=True)
+    wi = (Lp - mu) / (Lp - mu).norm(dim=1, keepdim=True)
+    feats = [nn_, q / q.norm(dim=1, keepdim=True), torch.exp(ls), wi, wo,
+             (Lp - mu).norm(dim=1, keepdim=True), vv[:, None]]
+    for k in range(4):
+        feats += [torch.sin((2.0 ** k) * m.pi * mu), torch.cos((2.0 ** k) * m.pi * mu)]
+    X = torch.cat(feats + [torch.zeros(60, 6, dtype=torch.float64)], 1)
+    assert np.allclose(X.detach().numpy(), O.mlp_inputs("paper", sc.mu, sc.normal, sc.vis, pair.center,
+                                                        pair.light, sc.quat, sc.log_s), atol=1e-14)
+    (X * torch.from_numpy(dX)).sum().backward()
+    for got, ref in [(dmu, mu), (dn, nn_), (dv, vv), (dq, q), (dls, ls)]:
+        assert np.allclose(ref.grad.numpy(), got, rtol=1e-11, atol=1e-12)
+
+
 # ---------------------------------------------------------------- binning / sort
 
 def test_bin_sort_equals_python_stable_sort():
