@@ -108,7 +108,7 @@ import json, sys, time
 sys.path.insert(0, ROOT)
 import numpy as np
 import scenegen as sg, oracle as O
-wl = sg.make_workload(WORKLOAD)
+wl = sg.make_workload(WORKLOAD, net=NET)
 pair = wl.pairs[0]
 sc = wl.scenes[pair.scene]
 stride = STRIDE
@@ -117,7 +117,7 @@ sel = pix[(pix[:, 1] % stride == 0)]
 dimg = sg.random_dimg(7, sel.shape[0])
 O.lib()
 t0 = time.perf_counter()
-X = O.mlp_inputs(wl.mlp.kind, sc.mu, sc.normal, sc.vis, pair.center, pair.light)
+X = O.mlp_inputs(wl.mlp.kind, sc.mu, sc.normal, sc.vis, pair.center, pair.light, sc.quat, sc.log_s)
 acts, y, Ls, Lin = O.mlp_forward(wl.mlp, X)
 dW = O.mlp_backward(wl.mlp, acts, y, Ls, np.ones_like(Ls), np.ones_like(Lin))
 t_mlp = time.perf_counter() - t0
@@ -130,12 +130,13 @@ print(json.dumps({"t_mlp": t_mlp, "t_sample": t_all, "t_full_est": full, "pixels
 """
 
 
-def cpu_oracle_sample(workload: str, stride: int, threads: int):
+def cpu_oracle_sample(workload: str, stride: int, threads: int, net=None):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = _CPU_SAMPLE.replace("ROOT", repr(ROOT)).replace("WORKLOAD", repr(workload)).replace("STRIDE", str(stride))
+    code = (_CPU_SAMPLE.replace("ROOT", repr(ROOT)).replace("WORKLOAD", repr(workload)).replace("STRIDE", str(stride))
+            .replace("NET", repr(net)))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -152,7 +153,7 @@ def run_reference(args):
     stride = 16
     times = []
     for i in range(args.warmup + args.steps):
-        d = cpu_oracle_sample(args.workload, stride, threads)
+        d = cpu_oracle_sample(args.workload, stride, threads, args.net)
         if i >= args.warmup:
             times.append(d["t_full_est"])
     t = sum(times) / len(times)
@@ -183,6 +184,9 @@ def _config(args):
            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
     if args.pairs is not None:
         cfg["pairs_override"] = args.pairs
+    if args.net is not None:
+        cfg["network"] = ("the paper's network (App. E): 42 inputs padded to 48, Leaky-ReLU trunk 64-32-32, "
+                          "incident head 32-1, SSS head 3, FP32 CUDA cores")
     return cfg
 
 
@@ -269,14 +273,9 @@ def run_ours(args):
     B.load_library()
     hbm, bf16_burst, bf16_sus, peak_src = _peaks()
 
-    wl = sg.make_workload(args.workload, seed_offset=rank, n_pairs=args.pairs)
+    wl = sg.make_workload(args.workload, seed_offset=rank, n_pairs=args.pairs, net=args.net)
     precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
-    try:
-        r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
-        r.forward_front()
-    except B.SSSGSError:
-        precision = B.FP32
-        r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
+    r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
     n_inst = r.fit_capacity()
     table = r.table
     n_pairs = table.n
@@ -481,7 +480,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         try:
-            d = cpu_oracle_sample(args.workload, 16, 1)
+            d = cpu_oracle_sample(args.workload, 16, 1, args.net)
             cpu = {"value": 1.0 / d["t_full_est"], "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": (f"one pair of {args.workload}: network fwd+bwd over all {n_gauss} Gaussians "
                               f"({d['t_mlp']:.1f} s) + raster fwd+bwd on every 16th pixel row "
@@ -512,6 +511,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
+    ap.add_argument("--net", default=None, choices=[None, "paper"],
+                    help="replace the workload's network by the paper's (App. E)")
     ap.add_argument("--pairs", type=int, default=None,
                     help="override the number of view/light pairs (smaller cases for profiling)")
     ap.add_argument("--tile", type=int, default=16)

@@ -69,6 +69,7 @@ enum {
 #define SSSGS_REC 24         /* floats per packed (pair, Gaussian) record (96 B, 16-B aligned) */
 #define SSSGS_GBUF 16        /* floats per G-buffer pixel: 15 features + final transmittance T */
 #define SSSGS_MAX_LAYERS 8
+#define SSSGS_DX 14          /* floats per item of the network-input gradient: dmu 3, dn 3, dv 1, dquat 4, dlog_s 3 */
 
 /* Record layout (floats): 0 mx, 1 my, 2 ca, 3 cb, 4 cc, 5 opacity,
  * 6..20 features (6 depth, 7-9 n, 10-12 base, 13 rough, 14 metal, 15 sss,
@@ -132,7 +133,7 @@ typedef struct sssgs_scene_grad {
     float *mu, *log_s, *quat, *logit_o, *normal, *base, *rough, *metal, *sss, *vis;
 } sssgs_scene_grad;
 
-enum { SSSGS_MLP_BASIC = 0, SSSGS_MLP_PE6 = 1 };
+enum { SSSGS_MLP_BASIC = 0, SSSGS_MLP_PE6 = 1, SSSGS_MLP_PAPER = 2 };
 enum { SSSGS_FP32 = 0, SSSGS_BF16 = 1 };
 
 /* Residual / incident-light MLP (Eq. 6; Appendix E "Network"). Input per
@@ -140,10 +141,19 @@ enum { SSSGS_FP32 = 0, SSSGS_BF16 = 1 };
  *   BASIC: [mu, w_out, w_in] (width[0] = 9)
  *   PE6:   [sin(2^k pi mu), cos(2^k pi mu) (k<6, 36), mu, w_out, w_in, n,
  *           |light - mu|, v] = 50, zero-padded (width[0] = 64)
- * Linear layers W[l] (width[l+1] x width[l], row-major, float32) + b[l], ReLU
- * between layers; width[n_layers] = 4: sigmoid -> L_SSS (3), ReLU -> L_in. */
+ * BASIC / PE6: linear layers W[l] (width[l+1] x width[l], row-major, float32)
+ * + b[l], ReLU between layers; width[n_layers] = 4: sigmoid -> L_SSS (3),
+ * ReLU -> L_in.
+ *   PAPER (the network of Appendix E): input [n, q/|q| (4), exp(log_s) (3),
+ *           w_in, w_out, |light - mu|, v, sin(2^k pi mu), cos(2^k pi mu)
+ *           (k<4, 24)] = 42, zero-padded to 48. n_layers = 6 and width =
+ *           {48, 64, 32, 32, 32, 1, 3} (checked); the matrices by role:
+ *           W[0] 64x48, W[1] 32x64, W[2] 32x32 (trunk, Leaky-ReLU slope 0.01
+ *           after each), W[3] 32x32 (incident hidden, Leaky-ReLU), W[4] 1x32
+ *           (incident output, ReLU -> L_in), W[5] 3x32 on the trunk output
+ *           (sigmoid -> L_SSS). FP32 precision only. */
 typedef struct sssgs_mlp {
-    int32_t kind;        /* SSSGS_MLP_BASIC or SSSGS_MLP_PE6 */
+    int32_t kind;        /* SSSGS_MLP_BASIC, SSSGS_MLP_PE6 or SSSGS_MLP_PAPER */
     int32_t n_layers;    /* 2 .. SSSGS_MAX_LAYERS */
     int32_t precision;   /* SSSGS_FP32 (CUDA cores) or SSSGS_BF16 (tensor cores, FP32 accumulate) */
     int32_t width[SSSGS_MAX_LAYERS + 1];
@@ -180,7 +190,8 @@ int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_p
 /* a5 -- network backward. Reads dL/d(L_SSS, L_in) from the gradient records
  * drec (fields 16..19), accumulates weight/bias gradients into grad and
  * writes (overwrites) the per-item input gradients
- * dx_items[n_items*7] = (dmu 3, dn 3, dv 1). Items whose four upstream values
+ * dx_items[n_items*SSSGS_DX] = (dmu 3, dn 3, dv 1, dquat 4, dlog_s 3); the
+ * last two are nonzero only for SSSGS_MLP_PAPER. Items whose four upstream values
  * are all exactly zero (Gaussians that reach no pixel of their view) add
  * exactly zero to every gradient; the BF16 path leaves them out of the
  * network and writes their dx_items as 0. BF16 path: n_items < 2^32.
@@ -281,7 +292,8 @@ int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
 /* a5 -- projection backward. For every Gaussian of the scene, sums over the
  * pairs that render it: the gradient records drec (geometry via Eq. 2 and the
  * covariance parameterisation, features directly) and, if dx_items != NULL,
- * the network-input gradients from sssgs_mlp_bwd. Accumulates into grad. */
+ * the network-input gradients from sssgs_mlp_bwd (dx_items[n_items*SSSGS_DX]).
+ * Accumulates into grad. */
 int sssgs_project_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                       int n_pairs, const sssgs_scene* scene, const float* drec,
                       const float* dx_items, const sssgs_scene_grad* grad, sssgs_stream stream);

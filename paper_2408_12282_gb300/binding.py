@@ -15,8 +15,8 @@ from . import build as _build
 
 c_i32, c_i64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 MAX_LAYERS = 8
-NF, REC, GBUF = 15, 24, 16
-MLP_BASIC, MLP_PE6 = 0, 1
+NF, REC, GBUF, DX = 15, 24, 16, 14
+MLP_BASIC, MLP_PE6, MLP_PAPER = 0, 1, 2
 FP32, BF16 = 0, 1
 STATUS_CAPACITY = 1
 STATUS_TIMEOUT = 2

@@ -8,6 +8,14 @@
 // 4 x (N/16) register micro-tile per thread. Heads: sigmoid -> L_SSS (rgb),
 // ReLU -> L_in (Appendix E "Network").
 //
+// The paper's network (SSSGS_MLP_PAPER) runs on the same chain machinery as
+// five chain layers built while staging: the three trunk layers; a 32 -> 64
+// layer holding the incident hidden units (Leaky-ReLU, columns 0..31) next to
+// the SSS logits (identity, columns 32..34); and a final layer that copies the
+// three logits through (weights exactly 1 and 0, so the copy is exact) and
+// forms the incident output in column 3. Gradients of the packed layers are
+// scattered back to the six matrices.
+//
 // Backward, per chunk of rows: phase A recomputes the forward of a 32-row tile,
 // back-propagates to every layer's pre-activation gradient dZ and to the
 // network input (mapped to d mu, d n, d v per item), storing H and dZ in the
@@ -27,11 +35,28 @@ constexpr int BWD_ROWS = 32;
 constexpr int64_t MLP_CHUNK = 131072;
 
 
-// out[r][j] = bias[j] + sum_i in[r][i] * M[i*J + j] over a ROWS-row tile
-// (act 1: ReLU; mask != null: out *= (mask[r][j] > 0)). J multiple of 16.
+// Activation codes of a chain layer's output: 0 none, 1 ReLU, 2 Leaky-ReLU,
+// 3 Leaky-ReLU on columns < 32 and none above (the paper network's packed
+// head layer).
+__device__ __forceinline__ float activate(float v, int act, int col) {
+    if (act == 1) return fmaxf(v, 0.f);
+    if (act == 2 || (act == 3 && col < 32)) return v > 0.f ? v : kLReluSlope * v;
+    return v;
+}
+
+// Backward of activation `act` at an output whose activated value is h (same
+// sign as the pre-activation): dh -> dz.
+__device__ __forceinline__ float activate_bwd(float dh, float h, int act, int col) {
+    if (act == 1) return h > 0.f ? dh : 0.f;
+    if (act == 2 || (act == 3 && col < 32)) return h > 0.f ? dh : kLReluSlope * dh;
+    return dh;
+}
+
+// out[r][j] = act(bias[j] + sum_i in[r][i] * M[i*J + j]) over a ROWS-row tile;
+// with mask != null, out = activate_bwd(out, mask[r][j], mact). J multiple of 16.
 template <int ROWS, int CJ>
 __device__ __forceinline__ void tile_gemm16(const float* in, int I, const float* M, const float* bias, float* out,
-                                            int act, const float* mask) {
+                                            int act, const float* mask, int mact) {
     constexpr int J = 16 * CJ;
     constexpr int RR = ROWS / 16;
     const int t = threadIdx.x, rg = t >> 4, cg = t & 15;
@@ -56,9 +81,8 @@ __device__ __forceinline__ void tile_gemm16(const float* in, int I, const float*
 #pragma unroll
         for (int c = 0; c < CJ; ++c) {
             const int row = rg * RR + r, col = cg * CJ + c;
-            float v = acc[r][c];
-            if (act == 1) v = fmaxf(v, 0.f);
-            if (mask && !(mask[row * MLP_LDA + col] > 0.f)) v = 0.f;
+            float v = activate(acc[r][c], act, col);
+            if (mask) v = activate_bwd(v, mask[row * MLP_LDA + col], mact, col);
             out[row * MLP_LDA + col] = v;
         }
 }
@@ -66,35 +90,71 @@ __device__ __forceinline__ void tile_gemm16(const float* in, int I, const float*
 // Generic (any J) variant: one output per thread-iteration.
 template <int ROWS>
 __device__ __forceinline__ void tile_gemm_any(const float* in, int I, const float* M, int J, const float* bias,
-                                              float* out, int act, const float* mask) {
+                                              float* out, int act, const float* mask, int mact) {
     for (int o = threadIdx.x; o < ROWS * J; o += MLP_THREADS) {
         const int row = o / J, col = o % J;
         float v = bias ? bias[col] : 0.f;
         for (int i = 0; i < I; ++i) v = fmaf(in[row * MLP_LDA + i], M[i * J + col], v);
-        if (act == 1) v = fmaxf(v, 0.f);
-        if (mask && !(mask[row * MLP_LDA + col] > 0.f)) v = 0.f;
+        v = activate(v, act, col);
+        if (mask) v = activate_bwd(v, mask[row * MLP_LDA + col], mact, col);
         out[row * MLP_LDA + col] = v;
     }
 }
 
 template <int ROWS>
 __device__ __forceinline__ void tile_gemm(const float* in, int I, const float* M, int J, const float* bias,
-                                          float* out, int act, const float* mask) {
-    switch (J) {
-        case 16: tile_gemm16<ROWS, 1>(in, I, M, bias, out, act, mask); break;
-        case 32: tile_gemm16<ROWS, 2>(in, I, M, bias, out, act, mask); break;
-        case 64: tile_gemm16<ROWS, 4>(in, I, M, bias, out, act, mask); break;
-        case 128: tile_gemm16<ROWS, 8>(in, I, M, bias, out, act, mask); break;
-        default: tile_gemm_any<ROWS>(in, I, M, J, bias, out, act, mask); break;
+                                          float* out, int act, const float* mask, int mact = 1) {
+    switch (J) {   // every multiple of 16 up to MLP_MAXW has its register-tiled form
+        case 16: tile_gemm16<ROWS, 1>(in, I, M, bias, out, act, mask, mact); break;
+        case 32: tile_gemm16<ROWS, 2>(in, I, M, bias, out, act, mask, mact); break;
+        case 48: tile_gemm16<ROWS, 3>(in, I, M, bias, out, act, mask, mact); break;
+        case 64: tile_gemm16<ROWS, 4>(in, I, M, bias, out, act, mask, mact); break;
+        case 80: tile_gemm16<ROWS, 5>(in, I, M, bias, out, act, mask, mact); break;
+        case 96: tile_gemm16<ROWS, 6>(in, I, M, bias, out, act, mask, mact); break;
+        case 112: tile_gemm16<ROWS, 7>(in, I, M, bias, out, act, mask, mact); break;
+        case 128: tile_gemm16<ROWS, 8>(in, I, M, bias, out, act, mask, mact); break;
+        default: tile_gemm_any<ROWS>(in, I, M, J, bias, out, act, mask, mact); break;
     }
 }
 
-// Stage layer weights in shared memory: transposed (K x N, for H W^T) or
-// as stored (N x K, for dZ W).
-__device__ __forceinline__ void stage_weights(const float* __restrict__ W, int N, int K, bool transpose, float* sW) {
+// Activation code of chain layer l's output (the last layer feeds the heads).
+__device__ __forceinline__ int layer_act(const MlpDev& net, int l) {
+    if (l == net.L - 1) return 0;
+    if (net.kind != SSSGS_MLP_PAPER) return 1;
+    return l < 3 ? 2 : 3;
+}
+
+// Weight (n, k) and bias n of chain layer l (N x K): the user's matrices, or
+// for the paper network the packed head layers described above.
+__device__ __forceinline__ float chain_w(const MlpDev& net, int l, int n, int k, int K) {
+    if (net.kind != SSSGS_MLP_PAPER || l < 3) return net.W[l][n * K + k];
+    if (l == 3) return n < 32 ? net.W[3][n * 32 + k] : (n < 35 ? net.W[5][(n - 32) * 32 + k] : 0.f);
+    if (n < 3) return k == 32 + n ? 1.f : 0.f;
+    return k < 32 ? net.W[4][k] : 0.f;
+}
+__device__ __forceinline__ float chain_b(const MlpDev& net, int l, int n) {
+    if (net.kind != SSSGS_MLP_PAPER || l < 3) return net.b[l][n];
+    if (l == 3) return n < 32 ? net.b[3][n] : (n < 35 ? net.b[5][n - 32] : 0.f);
+    return n == 3 ? net.b[4][0] : 0.f;
+}
+// Where the gradient of chain weight (n, k) / bias n goes (null: a fixed entry).
+__device__ __forceinline__ float* chain_dw(const MlpDev& net, const sssgs_mlp_grad& gr, int l, int n, int k, int K) {
+    if (net.kind != SSSGS_MLP_PAPER || l < 3) return gr.W[l] + n * K + k;
+    if (l == 3) return n < 32 ? gr.W[3] + n * 32 + k : (n < 35 ? gr.W[5] + (n - 32) * 32 + k : nullptr);
+    return (n == 3 && k < 32) ? gr.W[4] + k : nullptr;
+}
+__device__ __forceinline__ float* chain_db(const MlpDev& net, const sssgs_mlp_grad& gr, int l, int n) {
+    if (net.kind != SSSGS_MLP_PAPER || l < 3) return gr.b[l] ? gr.b[l] + n : nullptr;
+    if (l == 3) return n < 32 ? (gr.b[3] ? gr.b[3] + n : nullptr) : (n < 35 && gr.b[5] ? gr.b[5] + n - 32 : nullptr);
+    return (n == 3 && gr.b[4]) ? gr.b[4] : nullptr;
+}
+
+// Stage chain layer l's weights in shared memory: transposed (K x N, for
+// H W^T) or as stored (N x K, for dZ W).
+__device__ __forceinline__ void stage_weights(const MlpDev& net, int l, int N, int K, bool transpose, float* sW) {
     for (int i = threadIdx.x; i < N * K; i += MLP_THREADS) {
         const int n = i / K, k = i - n * K;
-        const float v = W[i];
+        const float v = chain_w(net, l, n, k, K);
         if (transpose) sW[k * N + n] = v; else sW[i] = v;
     }
 }
@@ -125,10 +185,10 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpDev net, const sssgs
         for (int l = 0; l < net.L; ++l) {
             const int K = net.w[l], N = net.w[l + 1];
             __syncthreads();
-            stage_weights(net.W[l], N, K, true, sW);
-            for (int i = threadIdx.x; i < N; i += MLP_THREADS) sb[i] = net.b[l][i];
+            stage_weights(net, l, N, K, true, sW);
+            for (int i = threadIdx.x; i < N; i += MLP_THREADS) sb[i] = chain_b(net, l, i);
             __syncthreads();
-            tile_gemm<FWD_ROWS>(cur, K, sW, N, sb, nxt, l < net.L - 1 ? 1 : 0, nullptr);
+            tile_gemm<FWD_ROWS>(cur, K, sW, N, sb, nxt, layer_act(net, l), nullptr);
             float* t = cur; cur = nxt; nxt = t;
         }
         __syncthreads();
@@ -180,11 +240,11 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
         for (int l = 0; l < net.L; ++l) {
             const int K = net.w[l], N = net.w[l + 1];
             __syncthreads();
-            stage_weights(net.W[l], N, K, true, sW);
-            for (int i = threadIdx.x; i < N; i += MLP_THREADS) sb[i] = net.b[l][i];
+            stage_weights(net, l, N, K, true, sW);
+            for (int i = threadIdx.x; i < N; i += MLP_THREADS) sb[i] = chain_b(net, l, i);
             __syncthreads();
             float* dst = (l < net.L - 1) ? sH + (l + 1) * BWD_ROWS * MLP_LDA : sD0;
-            tile_gemm<BWD_ROWS>(sH + l * BWD_ROWS * MLP_LDA, K, sW, N, sb, dst, l < net.L - 1 ? 1 : 0, nullptr);
+            tile_gemm<BWD_ROWS>(sH + l * BWD_ROWS * MLP_LDA, K, sW, N, sb, dst, layer_act(net, l), nullptr);
         }
         __syncthreads();
         // heads: dZ_L from dL/d(L_SSS, L_in)
@@ -217,11 +277,11 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
                 const int r = o / N, n = o - r * N;
                 if (r0 + r < rows) ws[offD[l] + (r0 + r) * N + n] = dcur[r * MLP_LDA + n];
             }
-            stage_weights(net.W[l], N, K, false, sW);
+            stage_weights(net, l, N, K, false, sW);
             __syncthreads();
-            // dH_l = dZ_{l+1} W_l ; dZ_l = dH_l * [H_l > 0] (l > 0)
+            // dH_l = dZ_{l+1} W_l ; dZ_l = dH_l * act'(H_l) (l > 0)
             tile_gemm<BWD_ROWS>(dcur, N, sW, K, nullptr, dnxt, 0,
-                                l > 0 ? sH + l * BWD_ROWS * MLP_LDA : nullptr);
+                                l > 0 ? sH + l * BWD_ROWS * MLP_LDA : nullptr, l > 0 ? layer_act(net, l - 1) : 1);
             float* t = dcur; dcur = dnxt; dnxt = t;
         }
         __syncthreads();
@@ -229,9 +289,9 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
             const int64_t m = row_begin + r0 + threadIdx.x;
             const int p = pair_of_item(pairs, n_pairs, m);
             const sssgs_pair& P = pairs[p];
-            float dx[7];
+            float dx[SSSGS_DX];
             input_backward(net, P, sc, P.g_begin + (m - P.item_offset), dcur + threadIdx.x * MLP_LDA, dx);
-            for (int k = 0; k < 7; ++k) dx_items[7 * m + k] = dx[k];
+            for (int k = 0; k < SSSGS_DX; ++k) dx_items[(int64_t)SSSGS_DX * m + k] = dx[k];
         }
         __syncthreads();   // the next tile overwrites the buffers read above
     }
@@ -240,7 +300,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
 // Phase B: dW_l += sum_rows dZ_{l+1}^T H_l, db_l += sum_rows dZ_{l+1}.
 template <int TN, int TK>
 __device__ __forceinline__ void reduce_dw16(const float* sD, const float* sHt, int rows_here, int N, int K,
-                                            float* __restrict__ dW) {
+                                            const MlpDev& net, const sssgs_mlp_grad& gr, int l) {
     const int t = threadIdx.x, ng = t >> 4, kg = t & 15;
     float acc[TN][TK];
 #pragma unroll
@@ -261,16 +321,24 @@ __device__ __forceinline__ void reduce_dw16(const float* sD, const float* sHt, i
 #pragma unroll
     for (int a = 0; a < TN; ++a)
 #pragma unroll
-        for (int b = 0; b < TK; ++b) atomicAdd(&dW[(ng * TN + a) * K + kg * TK + b], acc[a][b]);
+        for (int b = 0; b < TK; ++b) {
+            float* dst = chain_dw(net, gr, l, ng * TN + a, kg * TK + b, K);
+            if (dst) atomicAdd(dst, acc[a][b]);
+        }
 }
 
 template <int TN>
-__device__ __forceinline__ void reduce_dw_tk(const float* sD, const float* sH, int rows_here, int N, int K, float* dW) {
-    switch (K) {
-        case 16: reduce_dw16<TN, 1>(sD, sH, rows_here, N, K, dW); break;
-        case 32: reduce_dw16<TN, 2>(sD, sH, rows_here, N, K, dW); break;
-        case 64: reduce_dw16<TN, 4>(sD, sH, rows_here, N, K, dW); break;
-        default: reduce_dw16<TN, 8>(sD, sH, rows_here, N, K, dW); break;
+__device__ __forceinline__ void reduce_dw_tk(const float* sD, const float* sH, int rows_here, int N, int K,
+                                             const MlpDev& net, const sssgs_mlp_grad& gr, int l) {
+    switch (K / 16) {   // K is a multiple of 16 in 16..MLP_MAXW here (tiled layers)
+        case 1: reduce_dw16<TN, 1>(sD, sH, rows_here, N, K, net, gr, l); break;
+        case 2: reduce_dw16<TN, 2>(sD, sH, rows_here, N, K, net, gr, l); break;
+        case 3: reduce_dw16<TN, 3>(sD, sH, rows_here, N, K, net, gr, l); break;
+        case 4: reduce_dw16<TN, 4>(sD, sH, rows_here, N, K, net, gr, l); break;
+        case 5: reduce_dw16<TN, 5>(sD, sH, rows_here, N, K, net, gr, l); break;
+        case 6: reduce_dw16<TN, 6>(sD, sH, rows_here, N, K, net, gr, l); break;
+        case 7: reduce_dw16<TN, 7>(sD, sH, rows_here, N, K, net, gr, l); break;
+        default: reduce_dw16<TN, 8>(sD, sH, rows_here, N, K, net, gr, l); break;
     }
 }
 
@@ -309,11 +377,15 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_b(MlpDev net, int64_t r
         if (threadIdx.x < N)
             for (int r = 0; r < rows_here; ++r) dbias += sD[r * MLP_LDA + threadIdx.x];
         if (tiled) {
-            switch (N) {
-                case 16: reduce_dw_tk<1>(sD, sHs, rows_here, N, K, gr.W[l]); break;
-                case 32: reduce_dw_tk<2>(sD, sHs, rows_here, N, K, gr.W[l]); break;
-                case 64: reduce_dw_tk<4>(sD, sHs, rows_here, N, K, gr.W[l]); break;
-                default: reduce_dw_tk<8>(sD, sHs, rows_here, N, K, gr.W[l]); break;
+            switch (N / 16) {
+                case 1: reduce_dw_tk<1>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                case 2: reduce_dw_tk<2>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                case 3: reduce_dw_tk<3>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                case 4: reduce_dw_tk<4>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                case 5: reduce_dw_tk<5>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                case 6: reduce_dw_tk<6>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                case 7: reduce_dw_tk<7>(sD, sHs, rows_here, N, K, net, gr, l); break;
+                default: reduce_dw_tk<8>(sD, sHs, rows_here, N, K, net, gr, l); break;
             }
         } else {
             for (int q = 0; q < GQ; ++q) {
@@ -329,9 +401,14 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_b(MlpDev net, int64_t r
     if (!tiled)
         for (int q = 0; q < GQ; ++q) {
             const int o = threadIdx.x + q * MLP_THREADS;
-            if (o < N * K) atomicAdd(&gr.W[l][o], accs[q]);
+            if (o >= N * K) break;
+            float* dst = chain_dw(net, gr, l, o / K, o % K, K);
+            if (dst) atomicAdd(dst, accs[q]);
         }
-    if (threadIdx.x < N && gr.b[l]) atomicAdd(&gr.b[l][threadIdx.x], dbias);
+    if (threadIdx.x < N) {
+        float* dst = chain_db(net, gr, l, threadIdx.x);
+        if (dst) atomicAdd(dst, dbias);
+    }
 }
 
 }  // namespace sssgs
@@ -339,8 +416,20 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_b(MlpDev net, int64_t r
 using namespace sssgs;
 
 namespace {
+bool paper_ok(const sssgs_mlp* m) {
+    static const int w[7] = {48, 64, 32, 32, 32, 1, 3};
+    if (m->n_layers != 6) return false;
+    for (int l = 0; l < 7; ++l)
+        if (m->width[l] != w[l]) return false;
+    for (int l = 0; l < 6; ++l)
+        if (!m->W[l] || !m->b[l]) return false;
+    return true;
+}
+
 bool mlp_ok(const sssgs_mlp* m) {
-    if (!m || m->n_layers < 2 || m->n_layers > SSSGS_MAX_LAYERS) return false;
+    if (!m) return false;
+    if (m->kind == SSSGS_MLP_PAPER) return paper_ok(m);
+    if (m->n_layers < 2 || m->n_layers > SSSGS_MAX_LAYERS) return false;
     if (m->kind == SSSGS_MLP_BASIC && m->width[0] != 9) return false;
     if (m->kind == SSSGS_MLP_PE6 && m->width[0] != 64) return false;
     if (m->kind != SSSGS_MLP_BASIC && m->kind != SSSGS_MLP_PE6) return false;
@@ -355,11 +444,18 @@ bool mlp_ok(const sssgs_mlp* m) {
     return true;
 }
 
+// Device view of the network: the chain the kernels run (for the paper network
+// five packed layers 48-64-32-32-64-4) over the user's matrices.
 MlpDev to_dev(const sssgs_mlp* m) {
     MlpDev d;
     d.kind = m->kind;
     d.L = m->n_layers;
     for (int l = 0; l <= SSSGS_MAX_LAYERS; ++l) d.w[l] = l <= m->n_layers ? m->width[l] : 0;
+    if (m->kind == SSSGS_MLP_PAPER) {
+        static const int w[6] = {48, 64, 32, 32, 64, 4};
+        d.L = 5;
+        for (int l = 0; l <= SSSGS_MAX_LAYERS; ++l) d.w[l] = l < 6 ? w[l] : 0;
+    }
     for (int l = 0; l < SSSGS_MAX_LAYERS; ++l) {
         d.W[l] = l < m->n_layers ? m->W[l] : nullptr;
         d.b[l] = l < m->n_layers ? m->b[l] : nullptr;
@@ -368,8 +464,9 @@ MlpDev to_dev(const sssgs_mlp* m) {
 }
 
 int64_t floats_per_row(const sssgs_mlp* m) {
+    const MlpDev d = to_dev(m);
     int64_t f = 0;
-    for (int l = 0; l < m->n_layers; ++l) f += m->width[l] + m->width[l + 1];
+    for (int l = 0; l < d.L; ++l) f += d.w[l] + d.w[l + 1];
     return f;
 }
 
@@ -388,6 +485,7 @@ extern "C" int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
                              int n_pairs, const sssgs_scene* scene, float* out, int32_t* d_status,
                              sssgs_stream stream) {
     if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !out) return SSSGS_ERR_INVALID_ARG;
+    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER) return SSSGS_ERR_UNSUPPORTED;
     if (mlp->precision == SSSGS_BF16)
         return sssgs_mlp_fwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, out, d_status, stream);
     if (mlp->precision != SSSGS_FP32) return SSSGS_ERR_INVALID_ARG;
@@ -423,6 +521,7 @@ extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
         return SSSGS_ERR_INVALID_ARG;
     for (int l = 0; l < mlp->n_layers; ++l)
         if (!grad->W[l]) return SSSGS_ERR_INVALID_ARG;
+    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER) return SSSGS_ERR_UNSUPPORTED;
     if (mlp->precision == SSSGS_BF16)
         return sssgs_mlp_bwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
                                 workspace_bytes, d_status, stream);
@@ -433,7 +532,7 @@ extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
     float* ws = (float*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
     cudaStream_t st = (cudaStream_t)stream;
     MlpDev net = to_dev(mlp);
-    size_t smA = (size_t)((mlp->n_layers + 2) * BWD_ROWS * MLP_LDA + MLP_MAXW * MLP_MAXW + MLP_MAXW) * 4;
+    size_t smA = (size_t)((net.L + 2) * BWD_ROWS * MLP_LDA + MLP_MAXW * MLP_MAXW + MLP_MAXW) * 4;
     size_t smB = (size_t)(2 * 32 * MLP_LDA) * 4;
     cudaFuncSetAttribute(k_mlp_bwd_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
     int sms = num_sms();
@@ -444,8 +543,8 @@ extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
         k_mlp_bwd_a<<<grid, MLP_THREADS, smA, st>>>(net, d_pairs, n_pairs, r0, rows, *scene, drec, ws, chunk,
                                                     dx_items);
         sssgs::note_launches(1);
-        int splits = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, (int64_t)(2 * sms / mlp->n_layers + 1)));
-        dim3 gb((unsigned)splits, (unsigned)mlp->n_layers);
+        int splits = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, (int64_t)(2 * sms / net.L + 1)));
+        dim3 gb((unsigned)splits, (unsigned)net.L);
         k_mlp_bwd_b<<<gb, MLP_THREADS, smB, st>>>(net, rows, ws, chunk, *grad);
         sssgs::note_launches(1);
     }

@@ -4,6 +4,10 @@
 
 namespace sssgs {
 
+// Leaky-ReLU negative slope of the paper's network (App. E; the slope is not
+// stated, 0.01 is taken).
+constexpr float kLReluSlope = 0.01f;
+
 struct MlpDev {
     int kind, L;
     int w[SSSGS_MAX_LAYERS + 1];
@@ -24,6 +28,30 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
         x[0] = m0; x[1] = m1; x[2] = m2;
         x[3] = wo.x; x[4] = wo.y; x[5] = wo.z;
         x[6] = wi.x; x[7] = wi.y; x[8] = wi.z;
+        return;
+    }
+    if (net.kind == SSSGS_MLP_PAPER) {   // [n, q/|q|, exp(log_s), w_in, w_out, |light - mu|, v, PE4(mu)]
+        const float* q = sc.quat + 4 * g;
+        const float iq = 1.f / sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        x[0] = sc.normal[3 * g]; x[1] = sc.normal[3 * g + 1]; x[2] = sc.normal[3 * g + 2];
+        x[3] = q[0] * iq; x[4] = q[1] * iq; x[5] = q[2] * iq; x[6] = q[3] * iq;
+        x[7] = expf(sc.log_s[3 * g]); x[8] = expf(sc.log_s[3 * g + 1]); x[9] = expf(sc.log_s[3 * g + 2]);
+        x[10] = wi.x; x[11] = wi.y; x[12] = wi.z;
+        x[13] = wo.x; x[14] = wo.y; x[15] = wo.z;
+        x[16] = li;
+        x[17] = sc.vis[g];
+        const float mm[3] = {m0, m1, m2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s, co;
+                sincospif(ldexpf(mm[c], k), &s, &co);
+                x[18 + 6 * k + c] = s;
+                x[21 + 6 * k + c] = co;
+            }
+        }
+        for (int k = 42; k < net.w[0]; ++k) x[k] = 0.f;
         return;
     }
     const float mm[3] = {m0, m1, m2};
@@ -47,7 +75,8 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
     for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
 }
 
-// Input gradient dX (row) -> (dmu, dn, dv) of item m, written to dx[7].
+// Input gradient dX (row) -> (dmu, dn, dv, dquat, dlog_s) of item m, written
+// to dx[SSSGS_DX] (the last 7 are zero for the BASIC and PE6 inputs).
 __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
                                                int64_t g, const float* dX, float* dx) {
     const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
@@ -56,11 +85,38 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
     float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
     const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
     const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
-    int o_mu, o_wo, o_wi;
+    int o_mu = -1, o_wo, o_wi;
     float dmu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 7; k < SSSGS_DX; ++k) dx[k] = 0.f;
     if (net.kind == SSSGS_MLP_BASIC) {
         o_mu = 0; o_wo = 3; o_wi = 6;
         dx[3] = dx[4] = dx[5] = dx[6] = 0.f;
+    } else if (net.kind == SSSGS_MLP_PAPER) {
+        o_wi = 10; o_wo = 13;
+        const float mm[3] = {m0, m1, m2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float f = ldexpf(kPi, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s, co;
+                sincospif(ldexpf(mm[c], k), &s, &co);
+                dmu[c] += f * (dX[18 + 6 * k + c] * co - dX[21 + 6 * k + c] * s);
+            }
+        }
+        dmu[0] -= dX[16] * wi.x; dmu[1] -= dX[16] * wi.y; dmu[2] -= dX[16] * wi.z;
+        dx[3] = dX[0]; dx[4] = dX[1]; dx[5] = dX[2];
+        dx[6] = dX[17];
+        // q/|q|: dq = (g - qn (qn . g)) / |q| ; exp(log_s): dlog_s = g * s
+        const float* q = sc.quat + 4 * g;
+        const float iq = 1.f / sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float qn[4] = {q[0] * iq, q[1] * iq, q[2] * iq, q[3] * iq};
+        const float qg = qn[0] * dX[3] + qn[1] * dX[4] + qn[2] * dX[5] + qn[3] * dX[6];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dx[7 + k] = (dX[3 + k] - qn[k] * qg) * iq;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dx[11 + k] = dX[7 + k] * expf(sc.log_s[3 * g + k]);
     } else {
         o_mu = 36; o_wo = 39; o_wi = 42;
         const float mm[3] = {m0, m1, m2};
@@ -78,7 +134,9 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
         dx[6] = dX[49];
         dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
     }
-    dmu[0] += dX[o_mu]; dmu[1] += dX[o_mu + 1]; dmu[2] += dX[o_mu + 2];
+    if (o_mu >= 0) {
+        dmu[0] += dX[o_mu]; dmu[1] += dX[o_mu + 1]; dmu[2] += dX[o_mu + 2];
+    }
     // d unit(P - mu) / d mu applied to g:  -(g - w (w.g)) / |P - mu|
     const float3 go = make_float3(dX[o_wo], dX[o_wo + 1], dX[o_wo + 2]);
     const float3 gi = make_float3(dX[o_wi], dX[o_wi + 1], dX[o_wi + 2]);

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(ACT_BLOCK) k_active_count(const float* __restr
     if (m < n) flag[m] = a ? 1 : 0;
     if (m < n && !a) {
 #pragma unroll
-        for (int k = 0; k < 7; ++k) dx_items[7 * m + k] = 0.f;
+        for (int k = 0; k < SSSGS_DX; ++k) dx_items[SSSGS_DX * m + k] = 0.f;
     }
     const int c = __syncthreads_count(a);
     if (threadIdx.x == 0) cnt[blockIdx.x] = (uint32_t)c;
@@ -759,7 +759,9 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 if (wg == 0 && valid) {   // combine the two halves of the input gradient
 #pragma unroll
                     for (int k = 0; k < 7; ++k)
-                        dx_items[7 * m + k] = s_dx[k * TC_ROWS + t] + (k < 3 ? dmu_a[k] : 0.f);
+                        dx_items[SSSGS_DX * m + k] = s_dx[k * TC_ROWS + t] + (k < 3 ? dmu_a[k] : 0.f);
+#pragma unroll
+                    for (int k = 7; k < SSSGS_DX; ++k) dx_items[SSSGS_DX * m + k] = 0.f;   // no q, log_s inputs
                 }
                 if (tid == 0) {
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);

@@ -136,10 +136,12 @@ __global__ void __launch_bounds__(128) k_project_bwd(sssgs_cfg cfg, const sssgs_
         int64_t m = P.item_offset + (g - P.g_begin);
         const float* d = drec + (int64_t)SSSGS_REC * m;
         if (dx_items) {
-            const float* x = dx_items + 7 * m;
+            const float* x = dx_items + SSSGS_DX * m;
             dmu[0] += x[0]; dmu[1] += x[1]; dmu[2] += x[2];
             dn[0] += x[3]; dn[1] += x[4]; dn[2] += x[5];
             dv += x[6];
+            dq[0] += x[7]; dq[1] += x[8]; dq[2] += x[9]; dq[3] += x[10];
+            dls[0] += x[11]; dls[1] += x[12]; dls[2] += x[13];
         }
         dn[0] += d[7]; dn[1] += d[8]; dn[2] += d[9];
         db[0] += d[10]; db[1] += d[11]; db[2] += d[12];

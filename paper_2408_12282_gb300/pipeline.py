@@ -97,7 +97,7 @@ class Renderer:
         self.img = torch.zeros(P, 3, **f32)
         self.dgbuf = None if fused else torch.zeros(P, B.GBUF, **f32)
         self.drec = torch.zeros(n, B.REC, **f32)
-        self.dx_items = torch.zeros(n, 7, **f32)
+        self.dx_items = torch.zeros(n, B.DX, **f32)
         self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
         self.dW = [torch.zeros_like(w) for w in mlp.W]
         self.db = [torch.zeros_like(b) for b in mlp.b]
@@ -250,7 +250,7 @@ def concat_scenes(scenes, device="cuda"):
 
 
 def mlp_to_device(spec, precision=None, device="cuda") -> MLPParams:
-    kind = B.MLP_BASIC if spec.kind == "basic" else B.MLP_PE6
+    kind = {"basic": B.MLP_BASIC, "pe6": B.MLP_PE6, "paper": B.MLP_PAPER}[spec.kind]
     prec = precision if precision is not None else (B.BF16 if spec.precision == "bf16" else B.FP32)
     W = [torch.from_numpy(np.ascontiguousarray(w, np.float32)).to(device) for w in spec.weights]
     b = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(device) for x in spec.biases]
