@@ -480,12 +480,21 @@ int num_sms() {
 
 int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
                      const sssgs_scene* scene, float* out, int32_t* d_status, sssgs_stream stream);
+namespace sssgs {
+size_t paper_tc_workspace_bytes(int64_t n_items);
+int paper_tc_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                 const sssgs_scene* scene, float* out, int32_t* d_status, cudaStream_t st);
+int paper_tc_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                 const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
+                 void* workspace, size_t workspace_bytes, int32_t* d_status, cudaStream_t st);
+}  // namespace sssgs
 
 extern "C" int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                              int n_pairs, const sssgs_scene* scene, float* out, int32_t* d_status,
                              sssgs_stream stream) {
     if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !out) return SSSGS_ERR_INVALID_ARG;
-    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER) return SSSGS_ERR_UNSUPPORTED;
+    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER)
+        return sssgs::paper_tc_fwd(mlp, h_pairs, d_pairs, n_pairs, scene, out, d_status, (cudaStream_t)stream);
     if (mlp->precision == SSSGS_BF16)
         return sssgs_mlp_fwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, out, d_status, stream);
     if (mlp->precision != SSSGS_FP32) return SSSGS_ERR_INVALID_ARG;
@@ -504,6 +513,7 @@ size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp, int64_t n_items);
 
 extern "C" size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_items) {
     if (!mlp_ok(mlp) || n_items < 0) return 0;
+    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER) return sssgs::paper_tc_workspace_bytes(n_items);
     if (mlp->precision == SSSGS_BF16) return sssgs_mlp_workspace_bytes_tc(mlp, n_items);
     int64_t chunk = std::min<int64_t>(std::max<int64_t>(n_items, 1), MLP_CHUNK);
     return (size_t)(chunk * floats_per_row(mlp) * 4) + 256;
@@ -521,7 +531,9 @@ extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
         return SSSGS_ERR_INVALID_ARG;
     for (int l = 0; l < mlp->n_layers; ++l)
         if (!grad->W[l]) return SSSGS_ERR_INVALID_ARG;
-    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER) return SSSGS_ERR_UNSUPPORTED;
+    if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER)
+        return sssgs::paper_tc_bwd(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
+                                   workspace_bytes, d_status, (cudaStream_t)stream);
     if (mlp->precision == SSSGS_BF16)
         return sssgs_mlp_bwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
                                 workspace_bytes, d_status, stream);

@@ -14,7 +14,7 @@
 // Numerics: inputs, weights and hidden activations are rounded to BF16 (round
 // to nearest even); products accumulate in FP32; biases and heads in FP32.
 #include "mlp_common.cuh"
-#include "tc.cuh"
+#include "mlp_tc_util.cuh"
 
 namespace sssgs {
 
@@ -74,39 +74,6 @@ __device__ __forceinline__ void stage_weights_bf16(const MlpDev& net, const TcLa
     }
 }
 
-// Store 8 consecutive FP32 values of row r (columns c..c+7) as BF16.
-__device__ __forceinline__ void store8_bf16(uint8_t* base, int r, int c, int C, const float* v) {
-    uint4 q;
-    q.x = tc::pack_bf16(v[0], v[1]);
-    q.y = tc::pack_bf16(v[2], v[3]);
-    q.z = tc::pack_bf16(v[4], v[5]);
-    q.w = tc::pack_bf16(v[6], v[7]);
-    *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
-}
-
-// Store one FP32 value of row r, column c as BF16.
-__device__ __forceinline__ void store1_bf16(uint8_t* base, int r, int c, int C, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(base + tc::blk_offset(r, c, C)) = __float2bfloat16_rn(v);
-}
-
-constexpr int TC_MAX_SMEM_PAIRS = 256;
-
-// Item -> pair lookup against a shared-memory copy of the pairs' item offsets
-// (falls back to the global table for very large batches).
-__device__ __forceinline__ int pair_lookup(const int64_t* s_off, const sssgs_pair* __restrict__ pairs, int n_pairs,
-                                           int64_t item) {
-    if (n_pairs > TC_MAX_SMEM_PAIRS) return pair_of_item(pairs, n_pairs, item);
-    int lo = 0, hi = n_pairs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 // TC_FWD_LANES independent tile lanes per CTA: warpgroup g (4 warps) owns
 // activation buffer g, TMEM columns [128 g, 128 g + 128) and mbarrier g, and
@@ -298,14 +265,6 @@ __global__ void k_mlp_weights_bf16(MlpDev net, TcBwdLayout T, uint8_t* __restric
     }
 }
 
-// Store 8 consecutive BF16 values (already packed) of row r.
-__device__ __forceinline__ void store8_packed(uint8_t* base, int r, int c, int C, uint4 q) {
-    *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
-}
-
-__device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c, int C) {
-    return *reinterpret_cast<const uint4*>(base + tc::blk_offset(r, c, C));
-}
 
 // ---------------------------------------------------------------- active rows
 //
@@ -390,6 +349,15 @@ __global__ void __launch_bounds__(ACT_BLOCK) k_active_write(const uint8_t* __res
     uint32_t before = 0;
     for (int w = 0; w < warp; ++w) before += wcnt[w];
     if (a) active[off[blockIdx.x] + before + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = (uint32_t)m;
+}
+
+int launch_active_rows(const float* drec, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off, uint32_t* nact,
+                       uint32_t* active, float* dx_items, cudaStream_t st) {
+    const int nb = (int)((n + ACT_BLOCK - 1) / ACT_BLOCK);
+    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(drec, n, cnt, flag, dx_items);
+    k_active_scan<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
+    k_active_write<<<nb, ACT_BLOCK, 0, st>>>(flag, n, off, active);
+    return 3;
 }
 
 __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdLayout T,
@@ -917,11 +885,7 @@ int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     uint32_t* nact = (uint32_t*)(base + W.nact);
     cudaStream_t st = (cudaStream_t)stream;
     k_mlp_weights_bf16<<<dim3(32, net.L), 256, 0, st>>>(net, T, gimg);
-    const int nb = (int)((n + ACT_BLOCK - 1) / ACT_BLOCK);
-    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(drec, n, cnt, flag, dx_items);
-    k_active_scan<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
-    k_active_write<<<nb, ACT_BLOCK, 0, st>>>(flag, n, off, active);
-    sssgs::note_launches(4);
+    sssgs::note_launches(1 + launch_active_rows(drec, n, flag, cnt, off, nact, active, dx_items, st));
     cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
     int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());

@@ -1,0 +1,73 @@
+// Helpers shared by the tensor-core network kernels: BF16 operand tiles in
+// the core-matrix blocked layout of tc.cuh, per-warpgroup named barriers, the
+// item -> pair lookup, and the list of rows with a nonzero upstream gradient.
+#pragma once
+#include "mlp_common.cuh"
+#include "tc.cuh"
+
+namespace sssgs {
+
+// Store 8 consecutive FP32 values of row r (columns c..c+7) as BF16.
+__device__ __forceinline__ void store8_bf16(uint8_t* base, int r, int c, int C, const float* v) {
+    uint4 q;
+    q.x = tc::pack_bf16(v[0], v[1]);
+    q.y = tc::pack_bf16(v[2], v[3]);
+    q.z = tc::pack_bf16(v[4], v[5]);
+    q.w = tc::pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
+}
+
+// Store one FP32 value of row r, column c as BF16.
+__device__ __forceinline__ void store1_bf16(uint8_t* base, int r, int c, int C, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + tc::blk_offset(r, c, C)) = __float2bfloat16_rn(v);
+}
+
+constexpr int TC_MAX_SMEM_PAIRS = 256;
+
+// Item -> pair lookup against a shared-memory copy of the pairs' item offsets
+// (falls back to the global table for very large batches).
+__device__ __forceinline__ int pair_lookup(const int64_t* s_off, const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                           int64_t item) {
+    if (n_pairs > TC_MAX_SMEM_PAIRS) return pair_of_item(pairs, n_pairs, item);
+    int lo = 0, hi = n_pairs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Store 8 consecutive BF16 values (already packed) of row r.
+__device__ __forceinline__ void store8_packed(uint8_t* base, int r, int c, int C, uint4 q) {
+    *reinterpret_cast<uint4*>(base + tc::blk_offset(r, c, C)) = q;
+}
+
+__device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c, int C) {
+    return *reinterpret_cast<const uint4*>(base + tc::blk_offset(r, c, C));
+}
+
+// Write n TMEM columns [col, col + n) of this warp's 32 lanes with zeros
+// (n a multiple of 32); the whole warp calls it.
+__device__ __forceinline__ void tmem_zero(uint32_t taddr, int n) {
+    for (int c = 0; c < n; c += 32) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+            "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+            "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr + (uint32_t)c), "r"(0u)
+            : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Rows of the network backward: the items whose upstream gradient (drec
+// fields 16..19) is not all zero, in item order, into active[] with their
+// count in *nact; dx_items of the other items is set to 0. Scratch: flag[n],
+// cnt/off[ceil(n / 1024)]. Returns the number of launches made.
+int launch_active_rows(const float* drec, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off, uint32_t* nact,
+                       uint32_t* active, float* dx_items, cudaStream_t st);
+
+}  // namespace sssgs

@@ -316,10 +316,10 @@ def make_workload(name: str, *, N: int | None = None, res=None,
                   n_pairs: int | None = None, seed_offset: int = 0, net: str | None = None) -> Workload:
     """Build configuration `name` ("c1".."c5"); N/res/n_pairs shrink it for tests.
     For c5, `res` may be a tuple of resolutions to draw from. net="paper"
-    replaces the configuration's network by the paper's (App. E), FP32."""
+    replaces the configuration's network by the paper's (App. E)."""
     wl = _make_workload(name, N=N, res=res, n_pairs=n_pairs, seed_offset=seed_offset)
-    if net == "paper":
-        wl.mlp = mlp_spec(int(name[1]) * 1000 + seed_offset + 13, "paper", [])
+    if net == "paper":   # keeps the configuration's precision (BF16 tensor cores for c3-c5)
+        wl.mlp = mlp_spec(int(name[1]) * 1000 + seed_offset + 13, "paper", [], precision=wl.mlp.precision)
     elif net is not None:
         raise ValueError(f"unknown network {net!r}")
     return wl

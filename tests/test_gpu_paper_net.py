@@ -6,8 +6,8 @@ through the C ABI, against the FP64 oracle.
 * whole step: image and every scene / network gradient, with the network's
   rotation and scale inputs adding to the projection's quat and log_s
   gradients;
-* the BF16 tensor-core path does not take this network: it reports
-  SSSGS_ERR_UNSUPPORTED instead of running something else.
+* the BF16 tensor-core kernels (mlp_tc_paper.cu): forward and backward
+  against the oracle's BF16-emulating network.
 """
 import numpy as np
 import pytest
@@ -118,9 +118,80 @@ def test_paper_network_whole_step_image_and_gradients():
     assert all(v < 1e-3 for v in errs.values()), errs
 
 
-def test_paper_network_has_no_bf16_path():
-    wl = sg.make_workload("c1", net="paper")
+@pytest.mark.parametrize("N,n_pairs", [(3000, 3), (20000, 2)])
+def test_paper_network_bf16_forward_matches_bf16_oracle(N, n_pairs):
+    """Tensor-core forward vs the oracle's BF16-emulating network, with the
+    gates of the other BF16 network (bf16 rounding flips of hidden units)."""
+    wl = sg.make_workload("c4", N=N, res=64, n_pairs=n_pairs, net="paper")
     r = PL.renderer_for_workload(wl, precision=B.BF16)
     t = r.table
-    with pytest.raises(B.SSSGSError, match=str(-3)):
-        B.mlp_fwd(r._mlp_s, t.h, t.d, r._scene_s, r.mlp_out, r.status)
+    B.mlp_fwd(r._mlp_s, t.h, t.d, r._scene_s, r.mlp_out, r.status)
+    torch.cuda.synchronize()
+    r.check_status()
+    got = r.mlp_out.double().cpu().numpy()
+    ref = []
+    for pair in wl.pairs:
+        sc = wl.scenes[pair.scene]
+        X = O.mlp_inputs("paper", sc.mu, sc.normal, sc.vis, pair.center, pair.light, sc.quat, sc.log_s)
+        _, _, Ls, Lin = O.mlp_forward(wl.mlp, X, bf16=True)
+        ref.append(np.concatenate([Ls, Lin[:, None]], 1))
+    err = np.abs(got - np.concatenate(ref))
+    print(f"\npaper net bf16 N={N}: max {err.max():.3e} mean {err.mean():.3e} frac>1e-4 {(err > 1e-4).mean():.4f}")
+    assert (err > 1e-4).mean() < 0.01
+    assert err.max() < 2e-2
+    assert err.mean() < 1e-4
+
+
+@pytest.mark.parametrize("N,n_pairs,zero_frac", [(3000, 3, 0.0), (20000, 2, 0.0), (20000, 2, 0.6)])
+def test_paper_network_bf16_backward_matches_bf16_oracle(N, n_pairs, zero_frac):
+    """Tensor-core backward (runs on the rows with a nonzero upstream
+    gradient) vs the BF16-emulating oracle: gates of the other BF16 network's
+    backward (per tensor rel-L2 <= 2e-3 at >= 40K rows; with fewer rows at
+    most 0.1% of rows off by > 1e-2 relative and rel-L2 <= 1e-2). Rows with a
+    zero upstream gradient must get exactly zero input gradients."""
+    wl = sg.make_workload("c4", N=N, res=64, n_pairs=n_pairs, net="paper")
+    r = PL.renderer_for_workload(wl, precision=B.BF16)
+    n = r.table.n_items
+    rng = np.random.default_rng(N + 1)
+    up = rng.uniform(-1, 1, (n, 4)).astype(np.float32)
+    zero = rng.uniform(size=n) < zero_frac
+    up[zero] = 0.0
+    r.zero_grads()
+    r.drec[:, 16:20] = torch.from_numpy(up).cuda()
+    r.dx_items.fill_(float("nan"))
+    t = r.table
+    B.mlp_bwd(r._mlp_s, t.h, t.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp, r.status)
+    torch.cuda.synchronize()
+    r.check_status()
+    dW = [w.double().cpu().numpy() for w in r.dW]
+    db = [b.double().cpu().numpy() for b in r.db]
+    dx = r.dx_items.double().cpu().numpy()
+    rdW = [np.zeros_like(w) for w in dW]
+    rdb = [np.zeros_like(b) for b in db]
+    rdx = np.zeros_like(dx)
+    off = 0
+    for pair in wl.pairs:
+        sc = wl.scenes[pair.scene]
+        X = O.mlp_inputs("paper", sc.mu, sc.normal, sc.vis, pair.center, pair.light, sc.quat, sc.log_s)
+        acts, y, Ls, Lin = O.mlp_forward(wl.mlp, X, bf16=True)
+        u = up[off:off + sc.N].astype(np.float64)
+        gW, gb, gX = O.mlp_backward(wl.mlp, acts, y, Ls, u[:, :3], u[:, 3], bf16=True)
+        for l in range(6):
+            rdW[l] += gW[l]
+            rdb[l] += gb[l]
+        dmu, dn, dv, dq, dls = O.input_grads("paper", gX, sc.mu, pair.center, pair.light, sc.quat, sc.log_s)
+        rdx[off:off + sc.N] = np.concatenate([dmu, dn, dv[:, None], dq, dls], 1)
+        off += sc.N
+    assert np.all(dx[zero] == 0.0) and np.isfinite(dx).all()
+    errs = {f"W{l}": _rel(dW[l], rdW[l]) for l in range(6)}
+    errs.update({f"b{l}": _rel(db[l], rdb[l]) for l in range(6)})
+    errs["dx"] = _rel(dx, rdx)
+    row_rel = np.abs(dx - rdx).max(1) / np.maximum(np.abs(rdx).max(1), 1e-12)
+    frac_bad = float((row_rel > 1e-2).mean())
+    print("\npaper net bf16 backward rel-L2:", {k: f"{v:.2e}" for k, v in errs.items()},
+          f"rows >1e-2: {frac_bad:.4%}")
+    if int((~zero).sum()) >= 40000:
+        assert all(v < 2e-3 for v in errs.values()), errs
+    else:
+        assert frac_bad <= 1e-3
+        assert all(v < 1e-2 for v in errs.values()), errs
