@@ -28,6 +28,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import build as _build
+from .losses import image_loss, incident_loss, ssim, ssim_map  # noqa: F401  (training losses)
 
 __all__ = ["Cfg", "lib", "render_pair", "render_workload_pair", "mlp_inputs",
            "mlp_forward", "mlp_backward", "input_grads", "brdf", "bin_sort",

@@ -462,6 +462,65 @@ def test_paper_input_encoding_and_gradients_match_autograd():
         assert np.allclose(ref.grad.numpy(), got, rtol=1e-11, atol=1e-12)
 
 
+# ---------------------------------------------------------------- training losses (App. E "Losses")
+
+def test_ssim_equals_brute_force_window_sums():
+    """Separable windowed moments == explicit 11 x 11 window sums with zero
+    padding, pixel by pixel (tiny image)."""
+    rng = np.random.default_rng(11)
+    H, W = 9, 12
+    x, y = rng.uniform(0, 1, (H, W, 3)), rng.uniform(0, 1, (H, W, 3))
+    w1 = O.losses.gaussian_window()
+    w2 = np.outer(w1, w1)
+    S = np.zeros((H, W, 3))
+    for i in range(H):
+        for j in range(W):
+            acc = np.zeros((5, 3))
+            for a in range(-5, 6):
+                for b in range(-5, 6):
+                    ii, jj = i + a, j + b
+                    if 0 <= ii < H and 0 <= jj < W:
+                        wt = w2[a + 5, b + 5]
+                        xv, yv = x[ii, jj], y[ii, jj]
+                        acc += wt * np.stack([xv, yv, xv * xv, yv * yv, xv * yv])
+            mx, my, exx, eyy, exy = acc
+            sx, sy, sxy = exx - mx * mx, eyy - my * my, exy - mx * my
+            C1, C2 = O.losses.SSIM_C1, O.losses.SSIM_C2
+            S[i, j] = (2 * mx * my + C1) * (2 * sxy + C2) / ((mx * mx + my * my + C1) * (sx + sy + C2))
+    assert np.allclose(O.ssim_map(x, y), S, rtol=1e-12, atol=1e-14)
+    assert np.isclose(O.ssim(x, y)[0], S.mean(), rtol=1e-12)
+
+
+def test_ssim_closed_forms():
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0, 1, (20, 24, 3))
+    assert np.isclose(O.ssim(x, x)[0], 1.0, atol=1e-12)
+    c, d = 0.3, 0.7                      # constant images: interior S = (2cd + C1) / (c^2 + d^2 + C1)
+    S = O.ssim_map(np.full((20, 24, 3), c), np.full((20, 24, 3), d))
+    C1 = O.losses.SSIM_C1
+    assert np.allclose(S[5:-5, 5:-5], (2 * c * d + C1) / (c * c + d * d + C1), rtol=1e-12)
+
+
+def test_image_and_incident_loss_gradients_match_finite_differences():
+    rng = np.random.default_rng(13)
+    x, y = rng.uniform(0, 1, (10, 13, 3)), rng.uniform(0, 1, (10, 13, 3))
+    loss, g = O.image_loss(x, y)
+    for _ in range(12):
+        i, j, c = rng.integers(10), rng.integers(13), rng.integers(3)
+        h = 1e-6
+        xp, xm = x.copy(), x.copy()
+        xp[i, j, c] += h
+        xm[i, j, c] -= h
+        fd = (O.image_loss(xp, y)[0] - O.image_loss(xm, y)[0]) / (2 * h)
+        assert abs(fd - g[i, j, c]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (fd, g[i, j, c])
+    L_in = np.array([0.2, 1.5, 0.7, 0.95])
+    v = np.array([0.5, 0.1, 0.7 - 0.25, 0.95 + 0.01])
+    val, dl, dv = O.incident_loss(L_in, v)
+    assert np.isclose(val, 0.02 * (0.3 + 0.9 + 0.25 + 0.01) / 4)
+    assert np.allclose(dl, 0.02 / 4 * np.array([-1, 0, 1, -1]))     # clamped entry: no gradient to L_in
+    assert np.allclose(dv, -0.02 / 4 * np.array([-1, 1, 1, -1]))
+
+
 # ---------------------------------------------------------------- binning / sort
 
 def test_bin_sort_equals_python_stable_sort():
