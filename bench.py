@@ -180,7 +180,9 @@ def _config(args):
               "{400,800,1200,1600}^2, PE6 MLP 64-128x4-4",
     }
     cfg = {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
-           "loss": "L1 vs target rendered from perturbed parameters",
+           "loss": ("App. E: 0.8 L1 + 0.2 D-SSIM vs target rendered from perturbed parameters "
+                    "+ 0.02 incident-light constraint" if args.loss == "paper"
+                    else "L1 vs target rendered from perturbed parameters"),
            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
     if args.pairs is not None:
         cfg["pairs_override"] = args.pairs
@@ -296,7 +298,7 @@ def run_ours(args):
     graph_launches = 0
     if not args.no_graph:
         c0 = B.launch_count()
-        graph = r.capture(target=target, l1_scale=l1_scale)
+        graph = r.capture(target=target, l1_scale=l1_scale, loss=args.loss)
         graph_launches = (B.launch_count() - c0) // 2      # capture() runs the step once eagerly, once captured
 
     def step():
@@ -304,7 +306,7 @@ def run_ours(args):
             graph.replay()
         else:
             r.forward()
-            r.backward(target=target, l1_scale=l1_scale)
+            r.backward(target=target, l1_scale=l1_scale, loss=args.loss)
         if world > 1:
             PL.allreduce_gradients(grads_flat)
 
@@ -346,7 +348,8 @@ def run_ours(args):
     value = world * n_pairs * 1000.0 / ms_max
 
     # ---------------- per-stage timing (separate pass, events between calls)
-    stage_ms = {s: 0.0 for s in STAGES}
+    stages = STAGES + (("loss",) if args.loss == "paper" else ())
+    stage_ms = {s: 0.0 for s in stages}
     reps = max(2, min(args.steps, 5))
     stats_f = torch.zeros(2, dtype=torch.int64, device="cuda")
     stats_b = torch.zeros(2, dtype=torch.int64, device="cuda")
@@ -363,9 +366,22 @@ def run_ours(args):
         ev[4].record(st)
         r.zero_grads()
         e_z = torch.cuda.Event(enable_timing=True)
+        e_l = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        if args.loss == "paper":
+            e_l[0].record(st)
+            r.loss.zero_()
+            B.image_loss(r.cfg, table.h, table.d, r.img, target, 0.2, r.dimg_loss, r.loss, r.ws_loss)
+            e_l[1].record(st)
         e_z.record(st)
-        B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, None, target, None,
-                     l1_scale, r.drec, stats_b)
+        if args.loss == "paper":
+            B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, r.dimg_loss,
+                         None, None, 1.0, r.drec, stats_b)
+            e_l[2].record(st)
+            B.incident_loss(table.h, table.d, r.rec, 0.02, r.drec, r.loss)
+            e_l[3].record(st)
+        else:
+            B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, None, target,
+                         None, l1_scale, r.drec, stats_b)
         ev[5].record(st)
         B.mlp_bwd(r._mlp_s, table.h, table.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp, r.status)
         ev[6].record(st)
@@ -374,7 +390,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         for i, s in enumerate(STAGES):
             a = e_z if s == "render_bwd" else ev[i]
-            stage_ms[s] += a.elapsed_time(ev[i + 1]) / reps
+            b = e_l[2] if (s == "render_bwd" and args.loss == "paper") else ev[i + 1]
+            stage_ms[s] += a.elapsed_time(b) / reps
+        if args.loss == "paper":
+            stage_ms["loss"] += (e_l[0].elapsed_time(e_l[1]) + e_l[2].elapsed_time(e_l[3])) / reps
     n_items, n_pixels = table.n_items, table.n_pixels
     # rows the network backward runs on: items with a nonzero upstream gradient
     # (the others add exactly zero and are compacted out)
@@ -449,6 +468,10 @@ def run_ours(args):
         host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in r.grads.items()}
         h2d = sum(v.numel() * 4 for v in host_in.values()) + host_tgt.numel() * 4
         d2h = sum(v.numel() * 4 for v in host_out.values())
+        loss_host = None
+        if args.loss == "paper":
+            loss_host = torch.empty(n_pairs, dtype=torch.float32).pin_memory()
+            d2h += n_pairs * 4
 
         def e2e_step():
             for k2, v in host_in.items():
@@ -458,9 +481,11 @@ def run_ours(args):
                 graph.replay()
             else:
                 r.forward()
-                r.backward(target=target, l1_scale=l1_scale)
+                r.backward(target=target, l1_scale=l1_scale, loss=args.loss)
             if world > 1:
                 PL.allreduce_gradients(grads_flat)
+            if loss_host is not None:
+                loss_host.copy_(r.loss, non_blocking=True)
             for k2, v in host_out.items():
                 v.copy_(r.grads[k2], non_blocking=True)
         e2e_step()
@@ -516,6 +541,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=None,
                     help="override the number of view/light pairs (smaller cases for profiling)")
     ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--loss", default="l1", choices=["l1", "paper"],
+                    help="paper: the training losses of App. E (L1 + D-SSIM image loss, incident constraint)")
     ap.add_argument("--fp32-mlp", action="store_true")
     ap.add_argument("--plain-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")

@@ -289,6 +289,28 @@ int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
                      const float* dimg, const float* target, const float* weight, float l1_scale,
                      float* drec, uint64_t* d_stats, sssgs_stream stream);
 
+/* Training losses (Appendix E "Losses"; NEXT-4 of the build plan).
+ * Image loss per pair p: L_img = (1 - lambda_dssim) L1 + lambda_dssim (1 - SSIM)
+ * over the pair's pixels and channels (L1: mean |img - target|; SSIM: Wang et
+ * al. 2004, 11 x 11 Gaussian window with sigma 1.5, zero padding, C1 = 0.01^2,
+ * C2 = 0.03^2, mean over pixels and channels). Writes (overwrites)
+ * dimg[n_pixels*3] = dL/dimg (sum over pairs of L_img) for sssgs_render_bwd
+ * with a dimg upstream, and adds each pair's L_img to d_loss[p] (device
+ * float[n_pairs], caller-zeroed). workspace: sssgs_image_loss_workspace_bytes
+ * (9 floats per pixel). lambda_dssim in [0, 1] (the paper uses 0.2). */
+size_t sssgs_image_loss_workspace_bytes(int64_t n_pixels);
+int sssgs_image_loss(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                     const float* img, const float* target, float lambda_dssim, float* dimg, float* d_loss,
+                     void* workspace, size_t workspace_bytes, sssgs_stream stream);
+
+/* Incident-light constraint per pair p (App. E): L_inc = lambda_incident *
+ * mean over the pair's items of |min(L_in, 1) - v|, with L_in and v read from
+ * the records (fields 19, 20). Adds dL/dL_in to drec field 19 and dL/dv to
+ * field 20 (call after sssgs_render_bwd, before sssgs_mlp_bwd) and L_inc to
+ * d_loss[p]. The paper uses lambda_incident = 0.02. */
+int sssgs_incident_loss(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const float* rec,
+                        float lambda_incident, float* drec, float* d_loss, sssgs_stream stream);
+
 /* a5 -- projection backward. For every Gaussian of the scene, sums over the
  * pairs that render it: the gradient records drec (geometry via Eq. 2 and the
  * covariance parameterisation, features directly) and, if dx_items != NULL,

@@ -329,14 +329,17 @@ def all_pixels(W, H):
 
 
 def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=None,
-                bf16=False, mlp_out=None):
+                bf16=False, mlp_out=None, dlin_extra=None, dvis_extra=None):
     """Forward (and, if dimg is given, backward) of one view/light pair.
 
     pixels: (P x 2) int array of (i, j) to evaluate; default all, row-major.
     dimg:   (P x 3) upstream gradient on those pixels' image values.
     Returns a dict with gbuf (P x 16), img (P x 3), ncontrib, margin (P x 3),
     the per-Gaussian MLP output, and, with dimg, gradients of every parameter
-    and of the MLP weights."""
+    and of the MLP weights.
+    dlin_extra, dvis_extra (N): gradients of further loss terms on the
+    predicted incident light L_in and the visibility v of each Gaussian (the
+    incident-light constraint of App. E), added before the network backward."""
     L = lib()
     N = scene.N
     C = pair.center
@@ -384,7 +387,11 @@ def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=No
     g["metal"] += dfeat[:, 8]
     g["sss"] += dfeat[:, 9]
     g["vis"] += dfeat[:, 14]
-    dLs, dLin = dfeat[:, 10:13], dfeat[:, 13]
+    dLs, dLin = dfeat[:, 10:13], dfeat[:, 13].copy()
+    if dlin_extra is not None:
+        dLin += dlin_extra
+    if dvis_extra is not None:
+        g["vis"] += dvis_extra
     out["dmlp_out"] = np.concatenate([dLs, dLin[:, None]], axis=1)
     if mlp_out is None:
         dWs, dbs, dX = mlp_backward(spec, acts, y, Ls, dLs, dLin, bf16=bf16)

@@ -100,6 +100,10 @@ _SIGS = {
                           c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_project_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
                            c_vp, c_vp, ctypes.POINTER(SceneGrad), c_vp], ctypes.c_int),
+    "sssgs_image_loss_workspace_bytes": ([c_i64], ctypes.c_size_t),
+    "sssgs_image_loss": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp,
+                          c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
+    "sssgs_incident_loss": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -294,3 +298,19 @@ def project_bwd(cfg: Cfg, pairs, d_pairs, scene: Scene, drec, dx_items, grad: Sc
     _check(load_library().sssgs_project_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
                                             _p(drec), _p(dx_items), ctypes.byref(grad), _stream(stream)),
            "sssgs_project_bwd")
+
+
+def image_loss_workspace_bytes(n_pixels: int) -> int:
+    return int(load_library().sssgs_image_loss_workspace_bytes(n_pixels))
+
+
+def image_loss(cfg: Cfg, pairs, d_pairs, img, target, lambda_dssim, dimg, d_loss, workspace, stream=None):
+    _check(load_library().sssgs_image_loss(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), _p(img), _p(target),
+                                           float(lambda_dssim), _p(dimg), _p(d_loss), _p(workspace),
+                                           workspace.numel() * workspace.element_size(), _stream(stream)),
+           "sssgs_image_loss")
+
+
+def incident_loss(pairs, d_pairs, rec, lambda_incident, drec, d_loss, stream=None):
+    _check(load_library().sssgs_incident_loss(pairs, _p(d_pairs), len(pairs), _p(rec), float(lambda_incident),
+                                              _p(drec), _p(d_loss), _stream(stream)), "sssgs_incident_loss")

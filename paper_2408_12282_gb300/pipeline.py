@@ -158,10 +158,35 @@ class Renderer:
         for g in self.dW + self.db:
             g.zero_()
 
-    def backward(self, dimg=None, target=None, weight=None, l1_scale=1.0, stream=None):
+    def _loss_buffers(self):
+        if getattr(self, "loss", None) is None:
+            n, P = self.table.n_items, self.table.n_pixels
+            self.loss = torch.zeros(self.table.n, device=self.device, dtype=torch.float32)
+            self.dimg_loss = torch.zeros(P, 3, device=self.device, dtype=torch.float32)
+            self.ws_loss = torch.empty(B.image_loss_workspace_bytes(P), device=self.device, dtype=torch.uint8)
+
+    def backward(self, dimg=None, target=None, weight=None, l1_scale=1.0, stream=None, loss="l1",
+                 lambda_dssim=0.2, lambda_incident=0.02):
+        """Backward of one step. loss="l1": the upstream gradient is dimg, or
+        (dimg None) the fused L1 loss against target. loss="paper": the training
+        losses of App. E: image loss (1 - lambda_dssim) L1 + lambda_dssim
+        (1 - SSIM) against target plus the incident-light constraint; the
+        per-pair loss values land in self.loss."""
         t = self.table
         self.zero_grads()
-        if self.fused:
+        if loss == "paper":
+            if target is None or not self.fused:
+                raise ValueError("the paper's losses take a target and the fused path")
+            self._loss_buffers()
+            self.loss.zero_()
+            B.image_loss(self.cfg, t.h, t.d, self.img, target, lambda_dssim, self.dimg_loss, self.loss,
+                         self.ws_loss, stream)
+            B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
+                         self.dimg_loss, None, None, 1.0, self.drec, self.stats_bwd, stream)
+            B.incident_loss(t.h, t.d, self.rec, lambda_incident, self.drec, self.loss, stream)
+        elif loss != "l1":
+            raise ValueError(f"unknown loss {loss!r}")
+        elif self.fused:
             B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
                          dimg, target, weight, l1_scale, self.drec, self.stats_bwd, stream)
         else:
@@ -174,7 +199,7 @@ class Renderer:
                   self.status, stream)
         B.project_bwd(self.cfg, t.h, t.d, self._scene_s, self.drec, self.dx_items, self._grad_s, stream)
 
-    def capture(self, dimg=None, target=None, weight=None, l1_scale=1.0):
+    def capture(self, dimg=None, target=None, weight=None, l1_scale=1.0, loss="l1"):
         """Capture one forward + backward step as a CUDA graph and return it.
 
         The step has no host synchronisation (instance buffers are sized by
@@ -185,13 +210,13 @@ class Renderer:
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             self.forward()
-            self.backward(dimg=dimg, target=target, weight=weight, l1_scale=l1_scale)
+            self.backward(dimg=dimg, target=target, weight=weight, l1_scale=l1_scale, loss=loss)
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, capture_error_mode="thread_local"):
             self.forward()
-            self.backward(dimg=dimg, target=target, weight=weight, l1_scale=l1_scale)
+            self.backward(dimg=dimg, target=target, weight=weight, l1_scale=l1_scale, loss=loss)
         torch.cuda.synchronize()
         return g
 

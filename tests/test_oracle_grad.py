@@ -161,3 +161,69 @@ def test_fd_with_clamped_alpha_and_stop():
     used, bad = _fd_check(sc, pair, spec, picks, dimg)
     assert used >= 0.7 * len(picks)
     assert not bad, bad[:5]
+
+
+def test_fd_training_objective_of_app_e():
+    """The whole training objective of App. E, image loss (0.8 L1 + 0.2 D-SSIM)
+    plus the incident-light constraint, through the renderer and the paper's
+    network: the gradient that render_pair returns given the image loss's
+    dL/dimg and the constraint's dL/dL_in, dL/dv, against central differences
+    of the objective. Samples that flip an L1 sign or a clamp of L_in straddle
+    a kink and are skipped like the discrete decisions."""
+    sc, pair, _ = _tiny(7)
+    spec = sg.mlp_spec(11, "paper", [])
+    H, W = pair.H, pair.W
+    r0 = O.render_pair(sc, pair, spec)
+    target = np.clip(r0["img"].reshape(H, W, 3) + np.random.default_rng(70).normal(0, 0.05, (H, W, 3)), 0, 1)
+
+    def objective():
+        r = O.render_pair(sc, pair, spec)
+        li, _ = O.image_loss(r["img"].reshape(H, W, 3), target)
+        lc, _, _ = O.incident_loss(r["Lin"], sc.vis)
+        kinks = (np.sign(r["img"].reshape(H, W, 3) - target), np.sign(np.minimum(r["Lin"], 1.0) - sc.vis),
+                 r["Lin"] < 1.0)
+        return li + lc, r["ncontrib"].copy(), r["margin"][:, 2].copy(), kinks
+
+    _, gimg = O.image_loss(r0["img"].reshape(H, W, 3), target)
+    _, dl, dv = O.incident_loss(r0["Lin"], sc.vis)
+    r = O.render_pair(sc, pair, spec, dimg=gimg.reshape(-1, 3), dlin_extra=dl, dvis_extra=dv)
+    J0, nc0, cl0, k0 = objective()
+    live = np.flatnonzero(r["rect"][:, 0] <= r["rect"][:, 1])
+    rng = np.random.default_rng(7)
+    picks = [("mu", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(6)]
+    picks += [("log_s", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(4)]
+    picks += [("vis", (int(rng.integers(sc.N)),)) for _ in range(6)]
+    picks += [("base", (int(rng.choice(live)), int(rng.integers(3)))) for _ in range(3)]
+    picks += [("W0", (int(rng.integers(64)), int(rng.integers(42)))) for _ in range(4)]
+    picks += [("W4", (0, int(rng.integers(32)))) for _ in range(3)]
+    picks += [("b4", (0,)), ("b5", (2,))]
+    used, bad = 0, []
+    for name, idx in picks:
+        if name[0] in "Wb" and name[1:].isdigit():
+            l = int(name[1:])
+            arr = (spec.weights if name[0] == "W" else spec.biases)[l]
+            ana = (r["dW"] if name[0] == "W" else r["db"])[l][idx]
+        else:
+            arr = getattr(sc, name)
+            ana = r["grads"][name][idx]
+        x0 = float(arr[idx])
+        h = 1e-6 * max(1.0, abs(x0))
+        arr[idx] = x0 + h
+        Jp, ncp, clp, kp = objective()
+        arr[idx] = x0 - h
+        Jm, ncm, clm, km = objective()
+        arr[idx] = x0
+        same = all(np.array_equal(a, b) and np.array_equal(a, c) for a, b, c in zip(k0, kp, km))
+        if not (same and np.array_equal(ncp, nc0) and np.array_equal(ncm, nc0)
+                and np.array_equal(clp, cl0) and np.array_equal(clm, cl0)):
+            continue
+        fd = (Jp - Jm) / (2 * h)
+        used += 1
+        if abs(fd - ana) > 2e-5 * max(abs(fd), abs(ana), 1e-4):
+            bad.append((name, idx, fd, ana))
+    assert used >= 0.8 * len(picks), used
+    assert not bad, bad[:5]
+    # the constraint reaches the visibility of Gaussians that no pixel sees
+    hidden = np.setdiff1d(np.arange(sc.N), live)
+    if hidden.size:
+        assert np.allclose(r["grads"]["vis"][hidden], dv[hidden])
