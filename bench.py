@@ -233,8 +233,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # for the kernel source they were taken on (its sha256) and for workloads made
 # of such pairs; otherwise traffic is null.
 KERNEL_TRAFFIC = {
-    "render_bwd": ("raster.cu", "f916edb66ae511705e8da6ad99852265fd0e890b51df05ef39ebab98b7a5e026", 107.7e6),
-    "render_fwd": ("raster.cu", "f916edb66ae511705e8da6ad99852265fd0e890b51df05ef39ebab98b7a5e026", 70.85e6),
+    "render_bwd": ("raster.cu", "c8048417a3babf99b2513a7d4cdf6b34c9e2c344b35addebb0bd29a23b470ba1", 107.50e6),
+    "render_fwd": ("raster.cu", "c8048417a3babf99b2513a7d4cdf6b34c9e2c344b35addebb0bd29a23b470ba1", 70.51e6),
 }
 
 
@@ -416,7 +416,7 @@ def run_ours(args):
         ach = alu_flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / ALU_PEAK_TFLOPS, "traffic": kernel_traffic(dom, args.workload, n_pairs),
-                "traffic_unit": "DRAM bytes per launch (ncu, scaled from one pair)",
+                "traffic_unit": "DRAM bytes per launch (ncu on an 8-pair launch, scaled per pair)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
                 "work": {"contributions": contrib_b if dom == "render_bwd" else contrib_f,
                          "alpha_evaluations": evals_b if dom == "render_bwd" else evals_f},
@@ -428,6 +428,15 @@ def run_ours(args):
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "peak_source": peak_src + " (hbm copy)"}
     total_bytes = sum(algorithmic_bytes(s, n_items, n_pixels, n_inst, n_gauss, n_pairs) for s in STAGES)
+    loss_roof = None
+    if args.loss == "paper":
+        # SSIM pass A: img + target in, 9 coefficient floats out; pass B: the
+        # coefficients + img + target in, dimg out; incident: L_in, v in and
+        # their two gradient slots read-modify-written
+        by = 132 * n_pixels + 24 * n_items
+        ach = by / (stage_ms["loss"] * 1e-3) / 1e9
+        loss_roof = {"bound": "hbm", "kernels": "k_ssim_moments + k_ssim_grad + k_incident", "achieved": ach,
+                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "algorithmic_bytes": by}
     step_hbm_frac = total_bytes / (ms_max * 1e-3) / 1e9 / hbm
 
     # ---------------- plain unbatched FP32 path (per-pair launches, unfused, CUDA-core network)
@@ -519,7 +528,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "bf16+f32" if precision == B.BF16 else "f32",
                 "data": "synthetic", "config": _config(args),
                 "roofline": roof, "step_hbm_frac_of_algorithmic": step_hbm_frac,
-                "stage_ms": stage_ms, "instances": n_inst, "items": n_items, "mlp_bwd_rows": n_active, "pixels": n_pixels,
+                "stage_ms": stage_ms, "loss_roofline": loss_roof, "instances": n_inst, "items": n_items, "mlp_bwd_rows": n_active, "pixels": n_pixels,
                 "contributions_per_step": {"forward": contrib_f, "backward": contrib_b},
                 "cuda_graph": graph is not None,
                 "plain_fp32": plain, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,

@@ -15,6 +15,14 @@ constexpr float kPi = 3.14159265358979323846f;
 void note_launches(int n);
 
 // Launch-status helper used by every entry point.
+// Number of SMs of the current device (at least 1).
+static inline int device_sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
 static inline int launch_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SSSGS_OK : SSSGS_ERR_CUDA;

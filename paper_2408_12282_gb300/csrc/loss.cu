@@ -5,13 +5,14 @@
 // normalised), zero padding outside the image, C1 = 0.01^2, C2 = 0.03^2,
 // averaged over the pair's pixels and channels.
 //
-// Image loss, two passes over every pair's tiles (the render tile grid, one
-// pixel per thread, the window halo of 5 pixels staged in shared memory):
-//   A: windowed moments mu_x, mu_y, E[x^2], E[y^2], E[xy] (separable: rows,
-//      then columns), the per-pixel SSIM and L1 terms of the loss, and the
-//      three coefficient maps of the gradient (dS/dmu_x, dS/dE[x^2],
-//      dS/dE[xy] for the mean over the pair) into the workspace;
-//   B: the windowed sums of those maps give
+// Image loss, two passes over every pair's tiles (the render tile grid; the
+// tile, its 5-pixel window halo and all three channels staged in shared
+// memory; separable windowed sums, rows then columns):
+//   A: windowed moments mu_x, mu_y, E[x^2], E[y^2], E[xy], the per-pixel SSIM
+//      and L1 terms of the loss, and three coefficient planes per channel of
+//      the gradient (dS/dmu_x, dS/dE[x^2], dS/dE[xy] for the mean over the
+//      pair) into the workspace (9 planes of n_pixels floats);
+//   B: the windowed sums of those planes give
 //      dSSIM/dx = W*a + 2 x (W*b) + y (W*c)  (the window is symmetric);
 //      dimg = (1 - lambda) sign(x - y) / n - lambda dSSIM/dx.
 #include <cmath>
@@ -28,173 +29,361 @@ struct Win {
 };
 
 template <int TILE>
-struct LossTile {
-    static constexpr int E = TILE + 2 * R;     // staged edge
+struct SsimTile {
+    static constexpr int E = TILE + 2 * R;          // staged edge (tile + halo)
+    static constexpr int ES = E + (E & 1);          // even row stride: float2 pairs stay 16-B aligned
+    static constexpr int NT = TILE * TILE;          // threads per block
+    static constexpr int NW = NT / 32;
+    static constexpr int KH = TILE == 32 ? 4 : 2;   // outputs per item of the row pass
+    static constexpr int KV = 4;                    // outputs per item of the column pass
+    static constexpr int GH = TILE / KH, GV = TILE / KV;
+    static constexpr int STAGE = 3 * E * ES;        // staged elements per buffer
+    static constexpr int HSZ = 3 * E * TILE;        // row-pass outputs per plane
+    // shared memory of the two passes (bytes): staging buffer + row-pass planes
+    static constexpr int SMEM_A = 8 * STAGE + (8 + 8 + 4) * HSZ + 4 * NW;
+    static constexpr int SMEM_B = (8 + 4) * STAGE + (8 + 4) * HSZ;
 };
 
-// Pixel (i, j) of this block's tile and the staged window origin.
+// Where a tile lies: its pair, pixel origin and the pair's image.
+struct TileGeo {
+    int pair, x0, y0, W, H;
+    int64_t pix0;
+    bool first;
+};
+
 template <int TILE>
-__device__ __forceinline__ void tile_origin(const sssgs_pair& P, int tile, int& x0, int& y0) {
+__device__ __forceinline__ TileGeo tile_geo(const sssgs_pair* __restrict__ pairs, int n_pairs, int tile) {
+    TileGeo g;
+    g.pair = pair_of_tile(pairs, n_pairs, tile);
+    const sssgs_pair& P = pairs[g.pair];
     const int lt = tile - P.tile_offset;
-    x0 = (lt % P.tiles_x) * TILE;
-    y0 = (lt / P.tiles_x) * TILE;
+    g.x0 = (lt % P.tiles_x) * TILE;
+    g.y0 = (lt / P.tiles_x) * TILE;
+    g.W = P.W;
+    g.H = P.H;
+    g.pix0 = P.pixel_offset;
+    g.first = lt == 0;
+    return g;
 }
 
-// Pass A. coef[pix * 9 + 3 c + (0, 1, 2)] = (dS/dmu_x, dS/dE[x^2], dS/dE[xy])
-// of channel c for the mean SSIM of the pair; d_loss[pair] += loss terms.
+__device__ __forceinline__ float2 f2(float w) { return make_float2(w, w); }
+
+// 4-byte asynchronous copy global -> shared; zero-fills when !ok (src is then
+// not read).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Pass A staging: the tile and its halo, all three channels, as (x, y) pairs
+// xy[(c E + r) ES + col]; one warp per staged row reads the row's 3E
+// interleaved floats (coalesced), zero outside the image.
+template <int TILE>
+__device__ __forceinline__ void stage_xy(float2* xy, const TileGeo& g, const float* __restrict__ img,
+                                         const float* __restrict__ target) {
+    using T = SsimTile<TILE>;
+    constexpr int E = T::E, ES = T::ES;
+    constexpr int PER = (3 * E + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < E; r += T::NW) {
+        const int gy = g.y0 - R + r;
+        const bool rok = gy >= 0 && gy < g.H;
+        const int64_t base = 3 * (g.pix0 + (int64_t)gy * g.W + (g.x0 - R));
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int f = lane + 32 * u;
+            if (f < 3 * E) {
+                const int col = f / 3, ch = f - 3 * col, gx = g.x0 - R + col;
+                const bool ok = rok && gx >= 0 && gx < g.W;
+                float2* d = xy + (ch * E + r) * ES + col;
+                cp_async4(&d->x, ok ? img + base + f : img, ok);
+                cp_async4(&d->y, ok ? target + base + f : target, ok);
+            }
+        }
+    }
+}
+
+// Pass A, one block per tile: all staging copies are issued at once
+// (cp.async, no registers held), then the block waits for them. Row pass: every item slides the 11-tap window
+// over KH adjacent outputs of one staged row, forming (W*x, W*y),
+// (W*x^2, W*y^2) with paired FP32 FMAs and W*xy. Column pass: KV adjacent
+// outputs of one column, then per pixel and channel the SSIM, the loss terms
+// and the coefficients
+//   coef plane 3c+0: dS/dmu_x, 3c+1: dS/dE[x^2], 3c+2: dS/dE[xy]
+// (for the mean over the pair), planar over all pixels (n_pix_total apart).
 template <int TILE>
 __global__ void __launch_bounds__(TILE * TILE) k_ssim_moments(const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                                              int n_tiles, int64_t n_pix_total,
                                                               const float* __restrict__ img,
                                                               const float* __restrict__ target, Win win,
                                                               float lambda, float* __restrict__ coef,
                                                               float* __restrict__ d_loss) {
-    constexpr int E = LossTile<TILE>::E;
-    __shared__ float sx[E * E], sy[E * E];
-    __shared__ float sh[5][E * TILE];
-    __shared__ float s_red[TILE * TILE / 32];
-    __shared__ __align__(16) sssgs_pair sP;
-    const int tile = blockIdx.x, tid = threadIdx.x;
-    if (tid < 8) {
-        const int pi = pair_of_tile(pairs, n_pairs, tile);
-        reinterpret_cast<float4*>(&sP)[tid] = reinterpret_cast<const float4*>(pairs + pi)[tid];
-    }
-    __syncthreads();
-    int x0, y0;
-    tile_origin<TILE>(sP, tile, x0, y0);
-    const int ti = tid % TILE, tj = tid / TILE;
-    const int i = x0 + ti, j = y0 + tj;
-    const bool inside = i < sP.W && j < sP.H;
-    const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
-    const float inv_n = 1.f / (3.f * (float)sP.W * (float)sP.H);
-    float part = 0.f;
-    for (int c = 0; c < 3; ++c) {
-        for (int k = tid; k < E * E; k += TILE * TILE) {
-            const int gi = x0 - R + k % E, gj = y0 - R + k / E;
-            float xv = 0.f, yv = 0.f;
-            if (gi >= 0 && gi < sP.W && gj >= 0 && gj < sP.H) {
-                const int64_t q = sP.pixel_offset + (int64_t)gj * sP.W + gi;
-                xv = img[3 * q + c];
-                yv = target[3 * q + c];
-            }
-            sx[k] = xv;
-            sy[k] = yv;
-        }
-        __syncthreads();
-        for (int k = tid; k < E * TILE; k += TILE * TILE) {       // rows: all E staged rows, TILE columns
-            const int r = k / TILE, cc = k % TILE;
-            float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    using T = SsimTile<TILE>;
+    constexpr int E = T::E, ES = T::ES, NT = T::NT, KH = T::KH, KV = T::KV;
+    extern __shared__ __align__(16) float smem[];
+    float2* xy = reinterpret_cast<float2*>(smem);            // [3][E][ES]
+    float2* hm = xy + T::STAGE;                             // [3][E][TILE]  row sums of (x, y)
+    float2* hs = hm + T::HSZ;                               // [3][E][TILE]  row sums of (x^2, y^2)
+    float* hp = reinterpret_cast<float*>(hs + T::HSZ);      // [3][E][TILE]  row sums of xy
+    float* red = hp + T::HSZ;                               // [NW]
+    const int tid = threadIdx.x;
+    float2 w2[2 * R + 1];
 #pragma unroll
-            for (int t = 0; t <= 2 * R; ++t) {
-                const float xv = sx[r * E + cc + t], yv = sy[r * E + cc + t], w = win.w[t];
-                a[0] += w * xv;
-                a[1] += w * yv;
-                a[2] += w * xv * xv;
-                a[3] += w * yv * yv;
-                a[4] += w * xv * yv;
+    for (int t = 0; t <= 2 * R; ++t) w2[t] = f2(win.w[t]);
+    const int tile = blockIdx.x;
+    const TileGeo g = tile_geo<TILE>(pairs, n_pairs, tile);
+    stage_xy<TILE>(xy, g, img, target);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    {
+        const float2* X = xy;
+        for (int k = tid; k < 3 * E * T::GH; k += NT) {
+            const int gi = k % T::GH, rc = k / T::GH;         // rc = channel * E + staged row
+            const float4* src = reinterpret_cast<const float4*>(X + rc * ES + gi * KH);
+            float2 m[KH], sq[KH];
+            float p[KH];
+#pragma unroll
+            for (int o = 0; o < KH; ++o) {
+                m[o] = make_float2(0.f, 0.f);
+                sq[o] = make_float2(0.f, 0.f);
+                p[o] = 0.f;
             }
 #pragma unroll
-            for (int q = 0; q < 5; ++q) sh[q][r * TILE + cc] = a[q];
+            for (int jj = 0; jj < (KH + 2 * R) / 2; ++jj) {
+                const float4 q4 = src[jj];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * jj + h;
+                    const float2 v = h ? make_float2(q4.z, q4.w) : make_float2(q4.x, q4.y);
+                    const float2 v2 = __fmul2_rn(v, v);
+                    const float pr = v.x * v.y;
+#pragma unroll
+                    for (int o = 0; o < KH; ++o) {
+                        const int t = j - o;
+                        if (t >= 0 && t <= 2 * R) {
+                            m[o] = __ffma2_rn(w2[t], v, m[o]);
+                            sq[o] = __ffma2_rn(w2[t], v2, sq[o]);
+                            p[o] = fmaf(w2[t].x, pr, p[o]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < KH; ++o) {
+                const int d = rc * TILE + gi * KH + o;
+                hm[d] = m[o];
+                hs[d] = sq[o];
+                hp[d] = p[o];
+            }
         }
         __syncthreads();
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};                   // columns
+        const float inv_n = 1.f / (3.f * (float)g.W * (float)g.H);
+        float part = 0.f;
+        for (int k = tid; k < 3 * TILE * T::GV; k += NT) {
+            const int col = k % TILE, rest = k / TILE;
+            const int ch = rest % 3, rb = (rest / 3) * KV;
+            float2 m[KV], sq[KV];
+            float p[KV];
 #pragma unroll
-        for (int t = 0; t <= 2 * R; ++t)
+            for (int o = 0; o < KV; ++o) {
+                m[o] = make_float2(0.f, 0.f);
+                sq[o] = make_float2(0.f, 0.f);
+                p[o] = 0.f;
+            }
 #pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] += win.w[t] * sh[q][(tj + t) * TILE + ti];
-        if (inside) {
-            const float mx = m[0], my = m[1];
-            const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-            const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
-            const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
-            const float iB = 1.f / (B1 * B2);
-            const float S = A1 * A2 * iB;
-            const float dA1 = A2 * iB * inv_n, dA2 = A1 * iB * inv_n;
-            const float dB1 = -S / B1 * inv_n, dB2 = -S / B2 * inv_n;
-            const float d_sxx = dB2, d_sxy = 2.f * dA2;
-            const float d_mx = dA1 * 2.f * my + dB1 * 2.f * mx - 2.f * mx * d_sxx - my * d_sxy;
-            float* cf = coef + 9 * pix + 3 * c;
-            cf[0] = d_mx;
-            cf[1] = d_sxx;
-            cf[2] = d_sxy;
-            const float xv = sx[(tj + R) * E + ti + R], yv = sy[(tj + R) * E + ti + R];
-            part += ((1.f - lambda) * fabsf(xv - yv) - lambda * S) * inv_n;
+            for (int j = 0; j < KV + 2 * R; ++j) {
+                const int d = (ch * E + rb + j) * TILE + col;
+                const float2 a = hm[d], b = hs[d];
+                const float c = hp[d];
+#pragma unroll
+                for (int o = 0; o < KV; ++o) {
+                    const int t = j - o;
+                    if (t >= 0 && t <= 2 * R) {
+                        m[o] = __ffma2_rn(w2[t], a, m[o]);
+                        sq[o] = __ffma2_rn(w2[t], b, sq[o]);
+                        p[o] = fmaf(w2[t].x, c, p[o]);
+                    }
+                }
+            }
+            const int i = g.x0 + col;
+#pragma unroll
+            for (int o = 0; o < KV; ++o) {
+                const int j = g.y0 + rb + o;
+                if (i < g.W && j < g.H) {
+                    const float mx = m[o].x, my = m[o].y;
+                    const float sxx = sq[o].x - mx * mx, syy = sq[o].y - my * my, sxy = p[o] - mx * my;
+                    const float A1 = 2.f * mx * my + C1, A2 = 2.f * sxy + C2;
+                    const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+                    const float iB = 1.f / (B1 * B2);
+                    const float S = A1 * A2 * iB;
+                    const float sn = S * iB * inv_n;
+                    const float dA1 = A2 * iB * inv_n, dA2 = A1 * iB * inv_n;
+                    const float d_sxx = -sn * B1, d_sxy = 2.f * dA2;          // dS/dB2 = -S / B2
+                    const float d_mx = 2.f * (dA1 * my - sn * B2 * mx) - 2.f * mx * d_sxx - my * d_sxy;
+                    const int64_t pix = g.pix0 + (int64_t)j * g.W + i;
+                    coef[(3 * ch + 0) * n_pix_total + pix] = d_mx;
+                    coef[(3 * ch + 1) * n_pix_total + pix] = d_sxx;
+                    coef[(3 * ch + 2) * n_pix_total + pix] = d_sxy;
+                    const float2 v = X[(ch * E + rb + o + R) * ES + col + R];
+                    part += ((1.f - lambda) * fabsf(v.x - v.y) - lambda * S) * inv_n;
+                }
+            }
         }
-        __syncthreads();
-    }
-    // block sum of the loss terms; the pair's first tile also adds lambda (the 1 of 1 - SSIM)
+        // block sum of the loss terms; the pair's first tile also adds lambda (the 1 of 1 - SSIM)
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(SSSGS_FULL, part, o);
-    if ((tid & 31) == 0) s_red[tid >> 5] = part;
-    __syncthreads();
-    if (tid == 0) {
-        float s = 0.f;
-        for (int w = 0; w < TILE * TILE / 32; ++w) s += s_red[w];
-        if (tile == sP.tile_offset) s += lambda;
-        atomicAdd(d_loss + pair_of_tile(pairs, n_pairs, tile), s);
+        for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(SSSGS_FULL, part, o);
+        if ((tid & 31) == 0) red[tid >> 5] = part;
+        __syncthreads();
+        if (tid == 0) {
+            float s = 0.f;
+            for (int w = 0; w < T::NW; ++w) s += red[w];
+            if (g.first) s += lambda;
+            atomicAdd(d_loss + g.pair, s);
+        }
     }
 }
 
-// Pass B: dimg = (1 - lambda) sign(x - y) / n - lambda (W*a + 2 x W*b + y W*c).
+// Pass B staging: the coefficient planes of the tile and its halo,
+// sab[(c E + r) ES + col] = (a, b), sc[...] = c; one warp per (channel, row).
+template <int TILE>
+__device__ __forceinline__ void stage_coef(float2* sab, float* sc, const TileGeo& g, int64_t n_pix_total,
+                                           const float* __restrict__ coef) {
+    using T = SsimTile<TILE>;
+    constexpr int E = T::E, ES = T::ES;
+    constexpr int PER = (E + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int rc = threadIdx.x >> 5; rc < 3 * E; rc += T::NW) {
+        const int ch = rc / E, r = rc - ch * E, gy = g.y0 - R + r;
+        const bool rok = gy >= 0 && gy < g.H;
+        const float* cf = coef + 3 * ch * n_pix_total + g.pix0 + (int64_t)gy * g.W + (g.x0 - R);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int col = lane + 32 * u, gx = g.x0 - R + col;
+            if (col < E) {
+                const bool ok = rok && gx >= 0 && gx < g.W;
+                float2* d = sab + rc * ES + col;
+                cp_async4(&d->x, ok ? cf + col : coef, ok);
+                cp_async4(&d->y, ok ? cf + n_pix_total + col : coef, ok);
+                cp_async4(sc + rc * ES + col, ok ? cf + 2 * n_pix_total + col : coef, ok);
+            }
+        }
+    }
+}
+
+// Pass B: dimg = (1 - lambda) sign(x - y) / n - lambda (W*a + 2 x W*b + y W*c)
+// with a, b, c the coefficient planes of pass A (the window is symmetric, so
+// the adjoint of the windowed mean is the same correlation). Same staging,
+// one block per tile, two separable passes with (a, b) paired.
 template <int TILE>
 __global__ void __launch_bounds__(TILE * TILE) k_ssim_grad(const sssgs_pair* __restrict__ pairs, int n_pairs,
+                                                           int n_tiles, int64_t n_pix_total,
                                                            const float* __restrict__ img,
                                                            const float* __restrict__ target, Win win, float lambda,
                                                            const float* __restrict__ coef, float* __restrict__ dimg) {
-    constexpr int E = LossTile<TILE>::E;
-    __shared__ float sc[3][E * E];
-    __shared__ float sh[3][E * TILE];
-    __shared__ __align__(16) sssgs_pair sP;
-    const int tile = blockIdx.x, tid = threadIdx.x;
-    if (tid < 8) {
-        const int pi = pair_of_tile(pairs, n_pairs, tile);
-        reinterpret_cast<float4*>(&sP)[tid] = reinterpret_cast<const float4*>(pairs + pi)[tid];
-    }
+    using T = SsimTile<TILE>;
+    constexpr int E = T::E, ES = T::ES, NT = T::NT, KH = T::KH, KV = T::KV;
+    extern __shared__ __align__(16) float smem[];
+    float2* sab = reinterpret_cast<float2*>(smem);              // [3][E][ES]  (a, b)
+    float* sc = reinterpret_cast<float*>(sab + T::STAGE);       // [3][E][ES]  c
+    float2* h2 = reinterpret_cast<float2*>(sc + T::STAGE);      // [3][E][TILE]
+    float* h1 = reinterpret_cast<float*>(h2 + T::HSZ);          // [3][E][TILE]
+    const int tid = threadIdx.x;
+    float2 w2[2 * R + 1];
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) w2[t] = f2(win.w[t]);
+    const int tile = blockIdx.x;
+    const TileGeo g = tile_geo<TILE>(pairs, n_pairs, tile);
+    stage_coef<TILE>(sab, sc, g, n_pix_total, coef);
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
-    int x0, y0;
-    tile_origin<TILE>(sP, tile, x0, y0);
-    const int ti = tid % TILE, tj = tid / TILE;
-    const int i = x0 + ti, j = y0 + tj;
-    const bool inside = i < sP.W && j < sP.H;
-    const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
-    const float inv_n = 1.f / (3.f * (float)sP.W * (float)sP.H);
-    for (int c = 0; c < 3; ++c) {
-        for (int k = tid; k < E * E; k += TILE * TILE) {
-            const int gi = x0 - R + k % E, gj = y0 - R + k / E;
-            float a = 0.f, b = 0.f, d = 0.f;
-            if (gi >= 0 && gi < sP.W && gj >= 0 && gj < sP.H) {
-                const float* cf = coef + 9 * (sP.pixel_offset + (int64_t)gj * sP.W + gi) + 3 * c;
-                a = cf[0];
-                b = cf[1];
-                d = cf[2];
+    {
+        const float2* SAB = sab;
+        const float* SC = sc;
+        for (int k = tid; k < 3 * E * T::GH; k += NT) {
+            const int gi = k % T::GH, rc = k / T::GH;
+            const float4* s4 = reinterpret_cast<const float4*>(SAB + rc * ES + gi * KH);
+            const float2* c2 = reinterpret_cast<const float2*>(SC + rc * ES + gi * KH);
+            float2 u[KH];
+            float v[KH];
+#pragma unroll
+            for (int o = 0; o < KH; ++o) {
+                u[o] = make_float2(0.f, 0.f);
+                v[o] = 0.f;
             }
-            sc[0][k] = a;
-            sc[1][k] = b;
-            sc[2][k] = d;
+#pragma unroll
+            for (int jj = 0; jj < (KH + 2 * R) / 2; ++jj) {
+                const float4 q4 = s4[jj];
+                const float2 cc = c2[jj];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * jj + h;
+                    const float2 ab = h ? make_float2(q4.z, q4.w) : make_float2(q4.x, q4.y);
+                    const float c = h ? cc.y : cc.x;
+#pragma unroll
+                    for (int o = 0; o < KH; ++o) {
+                        const int t = j - o;
+                        if (t >= 0 && t <= 2 * R) {
+                            u[o] = __ffma2_rn(w2[t], ab, u[o]);
+                            v[o] = fmaf(w2[t].x, c, v[o]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < KH; ++o) {
+                h2[rc * TILE + gi * KH + o] = u[o];
+                h1[rc * TILE + gi * KH + o] = v[o];
+            }
         }
         __syncthreads();
-        for (int k = tid; k < E * TILE; k += TILE * TILE) {
-            const int r = k / TILE, cc = k % TILE;
-            float s[3] = {0.f, 0.f, 0.f};
+        const float inv_n = 1.f / (3.f * (float)g.W * (float)g.H);
+        for (int k = tid; k < 3 * TILE * T::GV; k += NT) {
+            const int col = k % TILE, rest = k / TILE;
+            const int ch = rest % 3, rb = (rest / 3) * KV;
+            const int i = g.x0 + col;
+            float2 u[KV], xyv[KV];
+            float v[KV];
 #pragma unroll
-            for (int t = 0; t <= 2 * R; ++t)
+            for (int o = 0; o < KV; ++o) {             // image values first: their latency hides under the taps
+                u[o] = make_float2(0.f, 0.f);
+                v[o] = 0.f;
+                const int j = g.y0 + rb + o;
+                xyv[o] = make_float2(0.f, 0.f);
+                if (i < g.W && j < g.H) {
+                    const int64_t q = 3 * (g.pix0 + (int64_t)j * g.W + i) + ch;
+                    xyv[o] = make_float2(img[q], target[q]);
+                }
+            }
 #pragma unroll
-                for (int q = 0; q < 3; ++q) s[q] += win.w[t] * sc[q][r * E + cc + t];
+            for (int j = 0; j < KV + 2 * R; ++j) {
+                const int d = (ch * E + rb + j) * TILE + col;
+                const float2 ab = h2[d];
+                const float c = h1[d];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) sh[q][r * TILE + cc] = s[q];
+                for (int o = 0; o < KV; ++o) {
+                    const int t = j - o;
+                    if (t >= 0 && t <= 2 * R) {
+                        u[o] = __ffma2_rn(w2[t], ab, u[o]);
+                        v[o] = fmaf(w2[t].x, c, v[o]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < KV; ++o) {
+                const int j = g.y0 + rb + o;
+                if (i < g.W && j < g.H) {
+                    const int64_t q = 3 * (g.pix0 + (int64_t)j * g.W + i) + ch;
+                    const float xv = xyv[o].x, yv = xyv[o].y;
+                    const float d = xv - yv;
+                    const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                    dimg[q] = (1.f - lambda) * sg * inv_n - lambda * (u[o].x + 2.f * xv * u[o].y + yv * v[o]);
+                }
+            }
         }
-        __syncthreads();
-        if (inside) {
-            float s[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int t = 0; t <= 2 * R; ++t)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) s[q] += win.w[t] * sh[q][(tj + t) * TILE + ti];
-            const float xv = img[3 * pix + c], yv = target[3 * pix + c];
-            const float d = xv - yv;
-            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            dimg[3 * pix + c] = (1.f - lambda) * sg * inv_n - lambda * (s[0] + 2.f * xv * s[1] + yv * s[2]);
-        }
-        __syncthreads();
     }
 }
 
@@ -245,11 +434,14 @@ Win gaussian_window() {
 }
 
 template <int TILE>
-int launch_image_loss(const sssgs_pair* d, int n, int tiles, const float* img, const float* target, float lambda,
-                      float* dimg, float* d_loss, float* coef, cudaStream_t st) {
+int launch_image_loss(const sssgs_pair* d, int n, int tiles, int64_t n_pix, const float* img, const float* target,
+                      float lambda, float* dimg, float* d_loss, float* coef, cudaStream_t st) {
+    using T = SsimTile<TILE>;
     const Win w = gaussian_window();
-    k_ssim_moments<TILE><<<tiles, TILE * TILE, 0, st>>>(d, n, img, target, w, lambda, coef, d_loss);
-    k_ssim_grad<TILE><<<tiles, TILE * TILE, 0, st>>>(d, n, img, target, w, lambda, coef, dimg);
+    cudaFuncSetAttribute(k_ssim_moments<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_A);
+    cudaFuncSetAttribute(k_ssim_grad<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_B);
+    k_ssim_moments<TILE><<<tiles, T::NT, T::SMEM_A, st>>>(d, n, tiles, n_pix, img, target, w, lambda, coef, d_loss);
+    k_ssim_grad<TILE><<<tiles, T::NT, T::SMEM_B, st>>>(d, n, tiles, n_pix, img, target, w, lambda, coef, dimg);
     sssgs::note_launches(2);
     return launch_status();
 }
@@ -277,9 +469,9 @@ extern "C" int sssgs_image_loss(const sssgs_cfg* cfg, const sssgs_pair* h_pairs,
     float* coef = (float*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
     cudaStream_t st = (cudaStream_t)stream;
     switch (cfg->tile) {
-        case 8: return launch_image_loss<8>(d_pairs, n_pairs, tiles, img, target, lambda_dssim, dimg, d_loss, coef, st);
-        case 16: return launch_image_loss<16>(d_pairs, n_pairs, tiles, img, target, lambda_dssim, dimg, d_loss, coef, st);
-        case 32: return launch_image_loss<32>(d_pairs, n_pairs, tiles, img, target, lambda_dssim, dimg, d_loss, coef, st);
+        case 8: return launch_image_loss<8>(d_pairs, n_pairs, tiles, n_pix, img, target, lambda_dssim, dimg, d_loss, coef, st);
+        case 16: return launch_image_loss<16>(d_pairs, n_pairs, tiles, n_pix, img, target, lambda_dssim, dimg, d_loss, coef, st);
+        case 32: return launch_image_loss<32>(d_pairs, n_pairs, tiles, n_pix, img, target, lambda_dssim, dimg, d_loss, coef, st);
         default: return SSSGS_ERR_INVALID_ARG;
     }
 }

@@ -470,12 +470,7 @@ int64_t floats_per_row(const sssgs_mlp* m) {
     return f;
 }
 
-int num_sms() {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
-}
+int num_sms() { return device_sm_count(); }
 }  // namespace
 
 int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,

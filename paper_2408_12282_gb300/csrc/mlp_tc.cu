@@ -808,12 +808,7 @@ MlpDev to_dev_tc(const sssgs_mlp* m) {
     return d;
 }
 
-int sm_count() {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
-}
+int sm_count() { return device_sm_count(); }
 }  // namespace
 
 int sssgs_mlp_fwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,

@@ -371,12 +371,7 @@ MlpDev paper_dev(const sssgs_mlp* m) {
     return d;
 }
 
-int num_sms_paper() {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
-}
+int num_sms_paper() { return device_sm_count(); }
 
 // Backward workspace: the active-row list, its flags, per-block counts and
 // offsets, and the row count.

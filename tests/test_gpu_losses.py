@@ -40,7 +40,7 @@ def _pairs(sizes, tile):
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_image_loss_matches_oracle(tile):
-    sizes = [(45, 37), (64, 64), (23, 70)]
+    sizes = [(45, 37), (64, 64), (23, 70), (1, 1), (3, 50)]
     cfg, table = _pairs(sizes, tile)
     rng = np.random.default_rng(tile)
     P = table.n_pixels
