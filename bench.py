@@ -178,6 +178,9 @@ def _config(args):
         "c1": "1,024 Gaussians in a shell, 1 pair at 128x128, MLP 9-32x2-4",
         "c5": "8 blob scenes of 50K-1M Gaussians x 8 view/light pairs each, resolutions drawn from "
               "{400,800,1200,1600}^2, PE6 MLP 64-128x4-4",
+        "c6": "300K Gaussians on the c3 blob, light-stage batch: 8 views (Fibonacci cameras r=3 hemisphere) x "
+              "8 lights each of the 112-light stage (7 rings x 16, r=4 upper hemisphere), 800x800, PE6 MLP "
+              "64-128x4-4; geometry shared by the lights of a view",
     }
     cfg = {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
            "loss": ("App. E: 0.8 L1 + 0.2 D-SSIM vs target rendered from perturbed parameters "
@@ -186,6 +189,10 @@ def _config(args):
            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
     if args.pairs is not None:
         cfg["pairs_override"] = args.pairs
+    if getattr(args, "views", None) is not None:
+        cfg["views_override"] = args.views
+    if getattr(args, "lights", None) is not None:
+        cfg["lights_override"] = args.lights
     if args.net is not None:
         cfg["network"] = ("the paper's network (App. E): 42 inputs padded to 48, Leaky-ReLU trunk 64-32-32, "
                           "incident head 32-1, SSS head 3, FP32 CUDA cores")
@@ -230,23 +237,31 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per 300K / 800x800 pair of the fused render kernels,
 # from one ncu capture of an 8-pair launch of the same scene
 # (profiles/k_composite_*_warp_300k_800_8pairs.md), divided by 8. Valid only
-# for the kernel source they were taken on (its sha256) and for workloads made
-# of such pairs; otherwise traffic is null.
+# for the kernel sources they were taken on (sha256 of raster.cu followed by
+# raster_common.cuh) and for workloads made of such pairs; otherwise null.
+TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("raster.cu", "c8048417a3babf99b2513a7d4cdf6b34c9e2c344b35addebb0bd29a23b470ba1", 107.50e6),
-    "render_fwd": ("raster.cu", "c8048417a3babf99b2513a7d4cdf6b34c9e2c344b35addebb0bd29a23b470ba1", 70.51e6),
+    "render_bwd": ("46d47d740881c8c047dabb606a8eee7eaf0ed14f94386a922a7c031dafd7807c", 107.65e6),
+    "render_fwd": ("46d47d740881c8c047dabb606a8eee7eaf0ed14f94386a922a7c031dafd7807c", 70.45e6),
 }
 
 
-def kernel_traffic(stage, workload, n_pairs):
+def render_source_sha():
     import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2408_12282_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(stage, workload, n_pairs):
     if stage not in KERNEL_TRAFFIC or workload not in ("c3", "c4"):
         return None
-    src, sha, per_pair = KERNEL_TRAFFIC[stage]
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2408_12282_gb300", "csrc", src)
-    with open(path, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != sha:
-            return None
+    sha, per_pair = KERNEL_TRAFFIC[stage]
+    if render_source_sha() != sha:
+        return None
     return per_pair * n_pairs
 
 
@@ -538,6 +553,230 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- many lights per view
+
+def ml_alu_flops(L, contrib_f, evals_f, contrib_b, evals_b, view_pixels):
+    """FP32 operations of the many-light render kernels: per contribution the
+    single-light count plus, per further light, 4 composited channels (fwd: 4
+    FMA; bwd: 4 FMA in the dot product, 4 products and 4 reduction adds), and
+    the shading (and its backward) once per light and view pixel."""
+    fwd = ((FLOP_FWD_CONTRIB + 8 * (L - 1)) * contrib_f + FLOP_EVAL * (evals_f - contrib_f)
+           + FLOP_SHADE_FWD * L * view_pixels)
+    bwd = ((FLOP_BWD_CONTRIB + 16 * (L - 1)) * contrib_b + FLOP_EVAL * (evals_b - contrib_b)
+           + FLOP_SHADE_BWD * L * view_pixels)
+    return {"render_fwd": fwd, "render_bwd": bwd}
+
+
+def run_ours_ml(args):
+    """Light-stage batches (workload c6): n_views views x n_lights lights, one
+    step = forward + backward of every (view, light) pair, the geometry shared
+    by the lights of a view (MultiLightRenderer). Also times the single-light
+    batched path on the same pairs for comparison."""
+    import torch
+    import torch.distributed as dist
+
+    import scenegen as sg
+    from paper_2408_12282_gb300 import binding as B
+    from paper_2408_12282_gb300 import pipeline as PL
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    B.load_library()
+    hbm, bf16_burst, bf16_sus, peak_src = _peaks()
+    wl = sg.make_workload(args.workload, seed_offset=rank, net=args.net, n_views=args.views, n_lights=args.lights)
+    precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
+    L = wl.n_lights
+    r = PL.multilight_renderer_for_workload(wl, precision=precision)
+    n_inst = r.fit_capacity()
+    n_pairs = len(wl.pairs)
+    wl_t = sg.Workload(wl.name, [sg.perturbed(s, 4242 + 97 * rank) for s in wl.scenes], wl.pairs, wl.mlp, wl.tile,
+                       None, n_lights=L)
+    rt = PL.multilight_renderer_for_workload(wl_t, precision=precision)
+    rt.fit_capacity()
+    rt.forward()
+    target = rt.img.clone()
+    del rt
+    torch.cuda.empty_cache()
+    l1_scale = 1.0 / (3.0 * r.pairs.n_pixels)
+    grads_flat = [g for g in r.grads.values()] + r.dW + r.db
+    c0 = B.launch_count()
+    graph = r.capture(target=target, l1_scale=l1_scale)
+    graph_launches = (B.launch_count() - c0) // 2
+
+    def step():
+        graph.replay()
+        if world > 1:
+            PL.allreduce_gradients(grads_flat)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    r.check_status()
+    st = torch.cuda.current_stream()
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * n_pairs * 1000.0 / ms_max
+
+    # per-stage timing (separate pass)
+    stages = ("mlp_fwd", "project_fwd", "bin_sort", "render_fwd", "render_bwd", "mlp_bwd", "project_bwd")
+    stage_ms = {k: 0.0 for k in stages}
+    reps = max(2, min(args.steps, 5))
+    r.stats_fwd = torch.zeros(2, dtype=torch.int64, device="cuda")
+    r.stats_bwd = torch.zeros(2, dtype=torch.int64, device="cuda")
+    v, pt = r.views, r.pairs
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(9)]
+        ev[0].record(st)
+        B.mlp_fwd(r._mlp_s, pt.h, pt.d, r._scene_s, r.mlp_out, r.status)
+        ev[1].record(st)
+        B.project_fwd(r.cfg, v.h, v.d, r._scene_s, None, r.rec, r.rect)
+        ev[2].record(st)
+        B.bin_sort(r.cfg, v.h, v.d, r.rec, r.rect, r.capacity, r.vals, r.ranges, r.count, r.status, r.ws_bin)
+        ev[3].record(st)
+        B.render_ml_fwd(r.cfg, v.h, v.d, L, r.lights, r.rec, r.mlp_out, r.vals, r.ranges, r.gbuf, r.last, r.img,
+                        None, r.stats_fwd)
+        ev[4].record(st)
+        r.zero_grads()
+        ev[5].record(st)
+        B.render_ml_bwd(r.cfg, v.h, v.d, L, r.lights, r.rec, r.mlp_out, r.vals, r.ranges, r.gbuf, r.last, r.img,
+                        None, target, l1_scale, r.drec, r.dmlp, r.stats_bwd)
+        ev[6].record(st)
+        B.mlp_bwd_strided(r._mlp_s, pt.h, pt.d, r._scene_s, r.dmlp, 4, r._mlp_g, r.dx_items, r.ws_mlp, r.status)
+        ev[7].record(st)
+        B.project_bwd(r.cfg, v.h, v.d, r._scene_s, r.drec, None, r._grad_s)
+        B.project_bwd(r.cfg, pt.h, pt.d, r._scene_s, None, r.dx_items, r._grad_s)
+        ev[8].record(st)
+        torch.cuda.synchronize()
+        pairs_ev = [(0, 1), (1, 2), (2, 3), (3, 4), (5, 6), (6, 7), (7, 8)]
+        for k, (a, b) in zip(stages, pairs_ev):
+            stage_ms[k] += ev[a].elapsed_time(ev[b]) / reps
+    contrib_f, evals_f = (int(x) // reps for x in r.stats_fwd.tolist())
+    contrib_b, evals_b = (int(x) // reps for x in r.stats_bwd.tolist())
+    n_active = int((r.dmlp != 0).any(dim=1).sum().item())
+    alu = ml_alu_flops(L, contrib_f, evals_f, contrib_b, evals_b, v.n_pixels)
+    dom = max(stages, key=lambda k: stage_ms[k])
+    widths = [int(r._mlp_s.width[i]) for i in range(r._mlp_s.n_layers + 1)]
+    if dom in ("mlp_fwd", "mlp_bwd") and precision == B.BF16:
+        fl = mlp_flops(widths, pt.n_items) if dom == "mlp_fwd" else 2 * mlp_flops(widths, n_active)
+        ach = fl / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
+                "frac": ach / bf16_sus, "traffic": None, "peak_source": peak_src + " (bf16 sustained)"}
+    elif dom in alu:
+        ach = alu[dom] / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom + " (many lights)", "achieved": ach, "peak": ALU_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / ALU_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                "work": {"contributions": contrib_b if dom == "render_bwd" else contrib_f,
+                         "alpha_evaluations": evals_b if dom == "render_bwd" else evals_f, "lights_per_view": L}}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "peak_source": peak_src + " (hbm copy)"}
+
+    # the single-light batched path on the same pairs (each pair on its own)
+    single = None
+    if not args.skip_plain:
+        rs = PL.renderer_for_workload(wl, precision=precision)
+        rs.fit_capacity()
+        gs = rs.capture(target=target, l1_scale=l1_scale)
+        for _ in range(2):
+            gs.replay()
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(st)
+        for _ in range(args.steps):
+            gs.replay()
+        p1.record(st)
+        torch.cuda.synchronize()
+        sms = p0.elapsed_time(p1) / args.steps
+        single = {"renders_per_s": n_pairs * 1000.0 / sms, "ms_per_step": sms,
+                  "what": "the same pairs through the single-light batched path (geometry per pair)",
+                  "speedup_of_many_light": (value / world) / (n_pairs * 1000.0 / sms)}
+        del rs, gs
+        torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.skip_e2e:
+        host_in = {k: t.detach().cpu().pin_memory() for k, t in r.scene.items()}
+        host_tgt = target.cpu().pin_memory()
+        host_out = {k: torch.empty_like(t, device="cpu").pin_memory() for k, t in r.grads.items()}
+        h2d = sum(t.numel() * 4 for t in host_in.values()) + host_tgt.numel() * 4
+        d2h = sum(t.numel() * 4 for t in host_out.values())
+
+        def e2e_step():
+            for k2, t in host_in.items():
+                r.scene[k2].copy_(t, non_blocking=True)
+            target.copy_(host_tgt, non_blocking=True)
+            graph.replay()
+            if world > 1:
+                PL.allreduce_gradients(grads_flat)
+            for k2, t in host_out.items():
+                t.copy_(r.grads[k2], non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(st)
+        for _ in range(args.steps):
+            e2e_step()
+        q1.record(st)
+        torch.cuda.synchronize()
+        ems = q0.elapsed_time(q1) / args.steps
+        e2e = {"value": world * n_pairs * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        try:
+            d = cpu_oracle_sample(args.workload, 16, 1, args.net)
+            cpu = {"value": 1.0 / d["t_full_est"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": (f"one view/light pair of {args.workload}: network fwd+bwd over all Gaussians "
+                              f"({d['t_mlp']:.1f} s) + raster fwd+bwd on every 16th pixel row "
+                              f"({d['t_sample'] - d['t_mlp']:.1f} s) scaled by 16; single thread")}
+        except Exception as ex:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+    if rank == 0:
+        cfg = _config(args)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16+f32" if precision == B.BF16 else "f32", "data": "synthetic",
+                "config": cfg, "roofline": roof, "stage_ms": stage_ms, "instances": n_inst,
+                "views": v.n, "lights_per_view": L, "pairs": n_pairs, "mlp_bwd_rows": n_active,
+                "contributions_per_step": {"forward": contrib_f, "backward": contrib_b},
+                "cuda_graph": True, "single_light_path": single, "e2e": e2e, "gpu_launches": int(graph_launches),
+                "clocks": clocks, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,6 +789,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=None,
                     help="override the number of view/light pairs (smaller cases for profiling)")
     ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--views", type=int, default=None, help="c6: views per batch (default 8)")
+    ap.add_argument("--lights", type=int, default=None, help="c6: lights per view, 1/2/4/8 (default 8)")
     ap.add_argument("--loss", default="l1", choices=["l1", "paper"],
                     help="paper: the training losses of App. E (L1 + D-SSIM image loss, incident constraint)")
     ap.add_argument("--fp32-mlp", action="store_true")
@@ -562,6 +803,10 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c6":
+        if args.loss != "l1":
+            raise SystemExit("c6 (many lights per view) runs the L1 loss")
+        run_ours_ml(args)
     else:
         run_ours(args)
 

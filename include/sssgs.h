@@ -202,8 +202,19 @@ int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_p
                   const sssgs_mlp_grad* grad, float* dx_items,
                   void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream);
 
+/* sssgs_mlp_bwd with the upstream gradient read from dout: item m's four
+ * values dL/d(L_SSS 3, L_in) at dout[m * dout_stride + 0..3] (dout 16-byte
+ * aligned, dout_stride a multiple of 4 and >= 4). sssgs_mlp_bwd is this call
+ * with dout = drec + 16, dout_stride = SSSGS_REC; the many-light path passes
+ * its per-(view, light, item) gradient rows with stride 4. */
+int sssgs_mlp_bwd_strided(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                          int n_pairs, const sssgs_scene* scene, const float* dout, int64_t dout_stride,
+                          const sssgs_mlp_grad* grad, float* dx_items,
+                          void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream);
+
 /* a1 -- EWA projection (Eq. 1, Eq. 2). Per item writes the packed record
- * (rec[n_items*24], features copied from the scene and from mlp_out[n_items*4])
+ * (rec[n_items*24], features copied from the scene and from mlp_out[n_items*4];
+ * mlp_out == NULL leaves fields 16..19 zero, as the many-light path wants)
  * and the inclusive tile rectangle rect[n_items*4] = (tx0, tx1, ty0, ty1) of
  * the ellipse {p <= ln(o / alpha_min)}; tx0 > tx1 marks a culled item. */
 int sssgs_project_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
@@ -289,7 +300,50 @@ int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
                      const float* dimg, const float* target, const float* weight, float l1_scale,
                      float* drec, uint64_t* d_stats, sssgs_stream stream);
 
-/* Training losses (Appendix E "Losses"; NEXT-4 of the build plan).
+/* Many lights per view. A training batch of the paper's light-stage data
+ * holds one camera view under several point lights (Sec. 4.1 "Dataset": fixed
+ * light positions, each view captured under all of them), and a relit view
+ * under an environment map is a sum of such renders weighted by environment
+ * samples (App. C "Image Based Lighting"). The geometry of a view does not
+ * depend on the light: projection, tile binning/sort and every alpha of the
+ * compositing (Eq. 3) are computed once per view; the network output
+ * (L_SSS, L_in; Eq. 6), its composited channels and the shading (Eq. 4,
+ * Eq. 7) are per light. Results equal rendering each (view, light) pair on its
+ * own.
+ *
+ * Views: h_views/d_views[n_views] planned with sssgs_plan (their light field
+ * is unused); rec, vals, ranges from sssgs_project_fwd (mlp_out NULL) and
+ * sssgs_bin_sort on the views. n_lights: 1, 2, 4 or 8 lights per view, with
+ * positions lights[(v * n_lights + l) * 3] (device). mlp_out: the network
+ * output of the (view, light) pair table, pair v * n_lights + l being view v's
+ * camera and scene with light l, as sssgs_mlp_fwd on that table writes it:
+ * row n_lights * item_offset_v + l * g_count_v + k for item k of view v.
+ * G-buffer per view pixel: gbuf[n_view_pixels * (12 + 4 n_lights)] = depth,
+ * n 3, base 3, rough, metal, sss, vis, T, then (L_SSS 3, L_in) per light.
+ * Images: with env_w == NULL one image per (view, light) pair in pair order
+ * (pixel n_lights * pixel_offset_v + l * W_v * H_v + j * W_v + i); with
+ * env_w[n_views * n_lights] (device weights) one image per view (view pixel
+ * layout) holding sum_l env_w[v * n_lights + l] * image of light l.
+ * d_stats as for sssgs_render_fwd. */
+int sssgs_render_ml_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const sssgs_pair* d_views, int n_views,
+                        int n_lights, const float* lights, const float* rec, const float* mlp_out,
+                        const uint32_t* vals, const uint32_t* ranges, float* gbuf, uint32_t* last, float* img,
+                        const float* env_w, uint64_t* d_stats, sssgs_stream stream);
+
+/* Backward of sssgs_render_ml_fwd (per-light images, env_w NULL). Upstream
+ * gradient per (view, light) image in pair pixel order: dimg, or (dimg ==
+ * NULL) the L1 loss l1_scale * sum |img - target|. Accumulates the per-view
+ * gradient records drec[n_view_items * 24] (geometry and the light-independent
+ * features; fields 16..19 untouched) and dmlp[rows * 4] = dL/d(L_SSS 3, L_in)
+ * per (view, light, item) row in mlp_out's layout, for
+ * sssgs_mlp_bwd_strided(dout = dmlp, dout_stride = 4) on the pair table. */
+int sssgs_render_ml_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const sssgs_pair* d_views, int n_views,
+                        int n_lights, const float* lights, const float* rec, const float* mlp_out,
+                        const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
+                        const float* img, const float* dimg, const float* target, float l1_scale, float* drec,
+                        float* dmlp, uint64_t* d_stats, sssgs_stream stream);
+
+/* Training losses (Appendix E "Losses").
  * Image loss per pair p: L_img = (1 - lambda_dssim) L1 + lambda_dssim (1 - SSIM)
  * over the pair's pixels and channels (L1: mean |img - target|; SSIM: Wang et
  * al. 2004, 11 x 11 Gaussian window with sigma 1.5, zero padding, C1 = 0.01^2,
@@ -315,7 +369,8 @@ int sssgs_incident_loss(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, in
  * pairs that render it: the gradient records drec (geometry via Eq. 2 and the
  * covariance parameterisation, features directly) and, if dx_items != NULL,
  * the network-input gradients from sssgs_mlp_bwd (dx_items[n_items*SSSGS_DX]).
- * Accumulates into grad. */
+ * Either may be NULL (the many-light path sums its view records and its
+ * (view, light) network-input gradients in two calls). Accumulates into grad. */
 int sssgs_project_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                       int n_pairs, const sssgs_scene* scene, const float* drec,
                       const float* dx_items, const sssgs_scene_grad* grad, sssgs_stream stream);

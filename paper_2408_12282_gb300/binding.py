@@ -79,6 +79,9 @@ _SIGS = {
     "sssgs_mlp_workspace_bytes": ([ctypes.POINTER(MLP), c_i64], ctypes.c_size_t),
     "sssgs_mlp_bwd": ([ctypes.POINTER(MLP), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp,
                        ctypes.POINTER(MLPGrad), c_vp, c_vp, ctypes.c_size_t, c_vp, c_vp], ctypes.c_int),
+    "sssgs_mlp_bwd_strided": ([ctypes.POINTER(MLP), ctypes.POINTER(Pair), c_vp, ctypes.c_int,
+                               ctypes.POINTER(Scene), c_vp, c_i64, ctypes.POINTER(MLPGrad), c_vp, c_vp,
+                               ctypes.c_size_t, c_vp, c_vp], ctypes.c_int),
     "sssgs_project_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
                            c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_bin_workspace_bytes": ([c_i64, c_i64, c_i32], ctypes.c_size_t),
@@ -100,6 +103,11 @@ _SIGS = {
                           c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_project_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
                            c_vp, c_vp, ctypes.POINTER(SceneGrad), c_vp], ctypes.c_int),
+    "sssgs_render_ml_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.c_int, c_vp,
+                             c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_render_ml_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.c_int, c_vp,
+                             c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp, c_vp],
+                            ctypes.c_int),
     "sssgs_image_loss_workspace_bytes": ([c_i64], ctypes.c_size_t),
     "sssgs_image_loss": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp,
                           c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
@@ -133,10 +141,17 @@ def load_library(build_if_missing: bool = True):
 
 
 def _p(t):
+    """Device (or host) address of a tensor argument. Every buffer of the C ABI
+    is float32, int32/uint32, uint8 or int64 and dense: a float64 or strided
+    tensor would be read with the wrong layout, so it is refused here."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
+    if t.dtype == torch.float64 or t.dtype == torch.float16 or t.dtype == torch.bfloat16:
+        raise TypeError(f"sssgs buffers are float32; got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("sssgs buffers must be contiguous")
     return t.data_ptr()
 
 
@@ -292,6 +307,33 @@ def render_bwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, dim
                                            _p(ranges), _p(gbuf), _p(last), _p(img), _p(dimg), _p(target),
                                            _p(weight), float(l1_scale), _p(drec), _p(stats), _stream(stream)),
            "sssgs_render_bwd")
+
+
+def mlp_bwd_strided(mlp: MLP, pairs, d_pairs, scene: Scene, dout, dout_stride: int, grad: MLPGrad, dx_items,
+                    workspace, d_status=None, stream=None):
+    _check(load_library().sssgs_mlp_bwd_strided(ctypes.byref(mlp), pairs, _p(d_pairs), len(pairs),
+                                                ctypes.byref(scene), _p(dout), int(dout_stride), ctypes.byref(grad),
+                                                _p(dx_items), _p(workspace),
+                                                workspace.numel() * workspace.element_size()
+                                                if workspace is not None else 0, _p(d_status), _stream(stream)),
+           "sssgs_mlp_bwd_strided")
+
+
+def render_ml_fwd(cfg: Cfg, views, d_views, n_lights: int, lights, rec, mlp_out, vals, ranges, gbuf, last, img,
+                  env_w=None, stats=None, stream=None):
+    _check(load_library().sssgs_render_ml_fwd(ctypes.byref(cfg), views, _p(d_views), len(views), int(n_lights),
+                                              _p(lights), _p(rec), _p(mlp_out), _p(vals), _p(ranges), _p(gbuf),
+                                              _p(last), _p(img), _p(env_w), _p(stats), _stream(stream)),
+           "sssgs_render_ml_fwd")
+
+
+def render_ml_bwd(cfg: Cfg, views, d_views, n_lights: int, lights, rec, mlp_out, vals, ranges, gbuf, last, img,
+                  dimg, target, l1_scale, drec, dmlp, stats=None, stream=None):
+    _check(load_library().sssgs_render_ml_bwd(ctypes.byref(cfg), views, _p(d_views), len(views), int(n_lights),
+                                              _p(lights), _p(rec), _p(mlp_out), _p(vals), _p(ranges), _p(gbuf),
+                                              _p(last), _p(img), _p(dimg), _p(target), float(l1_scale), _p(drec),
+                                              _p(dmlp), _p(stats), _stream(stream)),
+           "sssgs_render_ml_bwd")
 
 
 def project_bwd(cfg: Cfg, pairs, d_pairs, scene: Scene, drec, dx_items, grad: SceneGrad, stream=None):

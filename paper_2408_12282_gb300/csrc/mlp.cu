@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpDev net, const sssgs
 // Phase A: recompute, back-propagate, store H_l and dZ_{l+1} for the chunk.
 __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sssgs_pair* __restrict__ pairs,
                                                            int n_pairs, int64_t row_begin, int64_t rows,
-                                                           sssgs_scene sc, const float* __restrict__ drec,
-                                                           float* __restrict__ ws, int64_t chunk,
+                                                           sssgs_scene sc, const float* __restrict__ dout,
+                                                           int64_t dstride, float* __restrict__ ws, int64_t chunk,
                                                            float* __restrict__ dx_items) {
     extern __shared__ float smem[];
     float* sH = smem;                                          // [L][BWD_ROWS][LDA]
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
             const float y = sD0[r * MLP_LDA + c];
             float d = 0.f;
             if (r0 + r < rows) {
-                const float up = drec[(int64_t)SSSGS_REC * (row_begin + r0 + r) + 16 + c];
+                const float up = dout[dstride * (row_begin + r0 + r) + c];
                 if (c < 3) {
                     const float s = 1.f / (1.f + expf(-y));
                     d = up * s * (1.f - s);
@@ -480,8 +480,8 @@ size_t paper_tc_workspace_bytes(int64_t n_items);
 int paper_tc_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
                  const sssgs_scene* scene, float* out, int32_t* d_status, cudaStream_t st);
 int paper_tc_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
-                 const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
-                 void* workspace, size_t workspace_bytes, int32_t* d_status, cudaStream_t st);
+                 const sssgs_scene* scene, const float* dout, int64_t dstride, const sssgs_mlp_grad* grad,
+                 float* dx_items, void* workspace, size_t workspace_bytes, int32_t* d_status, cudaStream_t st);
 }  // namespace sssgs
 
 extern "C" int sssgs_mlp_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
@@ -515,22 +515,33 @@ extern "C" size_t sssgs_mlp_workspace_bytes(const sssgs_mlp* mlp, int64_t n_item
 }
 
 int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
-                     const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
-                     void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream);
+                     const sssgs_scene* scene, const float* dout, int64_t dstride, const sssgs_mlp_grad* grad,
+                     float* dx_items, void* workspace, size_t workspace_bytes, int32_t* d_status,
+                     sssgs_stream stream);
 
 extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                              int n_pairs, const sssgs_scene* scene, const float* drec,
                              const sssgs_mlp_grad* grad, float* dx_items, void* workspace,
                              size_t workspace_bytes, int32_t* d_status, sssgs_stream stream) {
-    if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !drec || !grad || !dx_items)
+    if (!drec) return SSSGS_ERR_INVALID_ARG;
+    return sssgs_mlp_bwd_strided(mlp, h_pairs, d_pairs, n_pairs, scene, drec + 16, SSSGS_REC, grad, dx_items,
+                                 workspace, workspace_bytes, d_status, stream);
+}
+
+extern "C" int sssgs_mlp_bwd_strided(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
+                                     int n_pairs, const sssgs_scene* scene, const float* dout, int64_t dstride,
+                                     const sssgs_mlp_grad* grad, float* dx_items, void* workspace,
+                                     size_t workspace_bytes, int32_t* d_status, sssgs_stream stream) {
+    if (!mlp_ok(mlp) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !dout || !grad || !dx_items)
         return SSSGS_ERR_INVALID_ARG;
+    if (dstride < 4 || (dstride & 3) || ((uintptr_t)dout & 15)) return SSSGS_ERR_INVALID_ARG;
     for (int l = 0; l < mlp->n_layers; ++l)
         if (!grad->W[l]) return SSSGS_ERR_INVALID_ARG;
     if (mlp->precision == SSSGS_BF16 && mlp->kind == SSSGS_MLP_PAPER)
-        return sssgs::paper_tc_bwd(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
-                                   workspace_bytes, d_status, (cudaStream_t)stream);
+        return sssgs::paper_tc_bwd(mlp, h_pairs, d_pairs, n_pairs, scene, dout, dstride, grad, dx_items,
+                                   workspace, workspace_bytes, d_status, (cudaStream_t)stream);
     if (mlp->precision == SSSGS_BF16)
-        return sssgs_mlp_bwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, drec, grad, dx_items, workspace,
+        return sssgs_mlp_bwd_tc(mlp, h_pairs, d_pairs, n_pairs, scene, dout, dstride, grad, dx_items, workspace,
                                 workspace_bytes, d_status, stream);
     int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
     if (n == 0) return SSSGS_OK;
@@ -547,8 +558,8 @@ extern "C" int sssgs_mlp_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, co
         int64_t rows = std::min(chunk, n - r0);
         int64_t tiles = (rows + BWD_ROWS - 1) / BWD_ROWS;
         int grid = (int)std::min<int64_t>(tiles, (int64_t)sms);
-        k_mlp_bwd_a<<<grid, MLP_THREADS, smA, st>>>(net, d_pairs, n_pairs, r0, rows, *scene, drec, ws, chunk,
-                                                    dx_items);
+        k_mlp_bwd_a<<<grid, MLP_THREADS, smA, st>>>(net, d_pairs, n_pairs, r0, rows, *scene, dout, dstride, ws,
+                                                    chunk, dx_items);
         sssgs::note_launches(1);
         int splits = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, (int64_t)(2 * sms / net.L + 1)));
         dim3 gb((unsigned)splits, (unsigned)net.L);

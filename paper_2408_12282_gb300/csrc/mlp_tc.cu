@@ -268,7 +268,7 @@ __global__ void k_mlp_weights_bf16(MlpDev net, TcBwdLayout T, uint8_t* __restric
 
 // ---------------------------------------------------------------- active rows
 //
-// A row whose upstream gradient (drec fields 16..19) is exactly zero adds
+// A row whose upstream gradient (its four dL/d(L_SSS, L_in)) is exactly zero adds
 // exactly zero to every dW, db and to its own input gradient: all dZ of the
 // chain are 0 * finite = 0, and bf16(0) = 0. Gaussians hidden behind the
 // surface in a view never contribute to a pixel, so their rows are zero. The
@@ -277,16 +277,17 @@ __global__ void k_mlp_weights_bf16(MlpDev net, TcBwdLayout T, uint8_t* __restric
 // dx_items = 0 for the rest.
 constexpr int ACT_BLOCK = 1024;
 
-__device__ __forceinline__ bool row_active(const float* __restrict__ drec, int64_t m) {
-    const float* u = drec + (int64_t)SSSGS_REC * m + 16;
-    return (u[0] != 0.f) | (u[1] != 0.f) | (u[2] != 0.f) | (u[3] != 0.f);
+__device__ __forceinline__ bool row_active(const float* __restrict__ dout, int64_t dstride, int64_t m) {
+    const float4 u = *reinterpret_cast<const float4*>(dout + dstride * m);
+    return (u.x != 0.f) | (u.y != 0.f) | (u.z != 0.f) | (u.w != 0.f);
 }
 
-__global__ void __launch_bounds__(ACT_BLOCK) k_active_count(const float* __restrict__ drec, int64_t n,
-                                                            uint32_t* __restrict__ cnt, uint8_t* __restrict__ flag,
+__global__ void __launch_bounds__(ACT_BLOCK) k_active_count(const float* __restrict__ dout, int64_t dstride,
+                                                            int64_t n, uint32_t* __restrict__ cnt,
+                                                            uint8_t* __restrict__ flag,
                                                             float* __restrict__ dx_items) {
     const int64_t m = (int64_t)blockIdx.x * ACT_BLOCK + threadIdx.x;
-    const bool a = m < n && row_active(drec, m);
+    const bool a = m < n && row_active(dout, dstride, m);
     if (m < n) flag[m] = a ? 1 : 0;
     if (m < n && !a) {
 #pragma unroll
@@ -351,10 +352,10 @@ __global__ void __launch_bounds__(ACT_BLOCK) k_active_write(const uint8_t* __res
     if (a) active[off[blockIdx.x] + before + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = (uint32_t)m;
 }
 
-int launch_active_rows(const float* drec, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off, uint32_t* nact,
-                       uint32_t* active, float* dx_items, cudaStream_t st) {
+int launch_active_rows(const float* dout, int64_t dstride, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off,
+                       uint32_t* nact, uint32_t* active, float* dx_items, cudaStream_t st) {
     const int nb = (int)((n + ACT_BLOCK - 1) / ACT_BLOCK);
-    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(drec, n, cnt, flag, dx_items);
+    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(dout, dstride, n, cnt, flag, dx_items);
     k_active_scan<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
     k_active_write<<<nb, ACT_BLOCK, 0, st>>>(flag, n, off, active);
     return 3;
@@ -364,7 +365,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                                                               const uint8_t* __restrict__ gimg,
                                                               const sssgs_pair* __restrict__ pairs, int n_pairs,
                                                               int64_t n_items, sssgs_scene sc,
-                                                              const float* __restrict__ drec, sssgs_mlp_grad gr,
+                                                              const float* __restrict__ dout, int64_t dstride,
+                                                              sssgs_mlp_grad gr,
                                                               float* __restrict__ dx_items,
                                                               const uint32_t* __restrict__ active,
                                                               const uint32_t* __restrict__ n_active,
@@ -483,9 +485,11 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             r.m = mr;
             r.pidx = pair_lookup(s_off, pairs, n_pairs, mr);
             r.q = load_pe6_params(sc, pairs[r.pidx].g_begin + (mr - pairs[r.pidx].item_offset));
-            const float* u = drec + (int64_t)SSSGS_REC * mr + 16;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) r.up[c] = u[c];
+            const float4 u = *reinterpret_cast<const float4*>(dout + dstride * mr);
+            r.up[0] = u.x;
+            r.up[1] = u.y;
+            r.up[2] = u.z;
+            r.up[3] = u.w;
         }
         return r;
     };
@@ -858,8 +862,9 @@ size_t sssgs_mlp_workspace_bytes_tc(const sssgs_mlp* mlp, int64_t n_items) {
 }
 
 int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
-                     const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
-                     void* workspace, size_t workspace_bytes, int32_t* d_status, sssgs_stream stream) {
+                     const sssgs_scene* scene, const float* dout, int64_t dstride, const sssgs_mlp_grad* grad,
+                     float* dx_items, void* workspace, size_t workspace_bytes, int32_t* d_status,
+                     sssgs_stream stream) {
     if (!tc_supported(mlp)) return SSSGS_ERR_UNSUPPORTED;
     MlpDev net = to_dev_tc(mlp);
     TcBwdLayout T = tc_bwd_layout(net);
@@ -880,12 +885,12 @@ int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     uint32_t* nact = (uint32_t*)(base + W.nact);
     cudaStream_t st = (cudaStream_t)stream;
     k_mlp_weights_bf16<<<dim3(32, net.L), 256, 0, st>>>(net, T, gimg);
-    sssgs::note_launches(1 + launch_active_rows(drec, n, flag, cnt, off, nact, active, dx_items, st));
+    sssgs::note_launches(1 + launch_active_rows(dout, dstride, n, flag, cnt, off, nact, active, dx_items, st));
     cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.total);
     int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)sm_count());
-    k_mlp_bwd_tc<<<grid, 2 * TC_THREADS, T.total, st>>>(net, T, gimg, d_pairs, n_pairs, n, *scene, drec, *grad,
-                                                    dx_items, active, nact, d_status);
+    k_mlp_bwd_tc<<<grid, 2 * TC_THREADS, T.total, st>>>(net, T, gimg, d_pairs, n_pairs, n, *scene, dout, dstride,
+                                                    *grad, dx_items, active, nact, d_status);
     sssgs::note_launches(1);
     return launch_status();
 }

@@ -98,7 +98,7 @@ template <bool BWD>
 __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, const sssgs_pair* __restrict__ pairs,
                                                                  int n_pairs, int64_t n_items, sssgs_scene sc,
                                                                  float* __restrict__ out,
-                                                                 const float* __restrict__ drec,
+                                                                 const float* __restrict__ dout, int64_t dstride,
                                                                  sssgs_mlp_grad gr, float* __restrict__ dx_items,
                                                                  const uint32_t* __restrict__ active,
                                                                  const uint32_t* __restrict__ n_active,
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
                     if (BWD) {      // head gradients: dZ of the incident output (column 0 of 16)
                         float dz[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         if (valid) {
-                            const float* up = drec + (int64_t)SSSGS_REC * m + 16;
+                            const float* up = dout + dstride * m;
                             dz[0] = zi > 0.f ? up[3] : 0.f;
 #pragma unroll
                             for (int c = 0; c < 3; ++c) ls[c] = up[c] * ls[c] * (1.f - ls[c]);   // now dL/d(logit)
@@ -405,15 +405,15 @@ int paper_tc_fwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pa
     const int grid = (int)std::min<int64_t>((tiles + PLANES - 1) / PLANES, (int64_t)num_sms_paper());
     sssgs_mlp_grad none{};
     k_mlp_paper_tc<false><<<grid, PLANES * PT, PSmem::TOTAL, st>>>(paper_dev(mlp), d_pairs, n_pairs, n, *scene, out,
-                                                                    nullptr, none, nullptr, nullptr, nullptr,
+                                                                    nullptr, 0, none, nullptr, nullptr, nullptr,
                                                                     d_status);
     sssgs::note_launches(1);
     return launch_status();
 }
 
 int paper_tc_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
-                 const sssgs_scene* scene, const float* drec, const sssgs_mlp_grad* grad, float* dx_items,
-                 void* workspace, size_t workspace_bytes, int32_t* d_status, cudaStream_t st) {
+                 const sssgs_scene* scene, const float* dout, int64_t dstride, const sssgs_mlp_grad* grad,
+                 float* dx_items, void* workspace, size_t workspace_bytes, int32_t* d_status, cudaStream_t st) {
     const int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
     if (n == 0) return SSSGS_OK;
     if (n >= ((int64_t)1 << 32)) return SSSGS_ERR_INVALID_ARG;
@@ -422,14 +422,14 @@ int paper_tc_bwd(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssgs_pa
     uint8_t* base = (uint8_t*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
     uint32_t* active = (uint32_t*)(base + W.active);
     uint32_t* nact = (uint32_t*)(base + W.nact);
-    int launches = launch_active_rows(drec, n, base + W.flag, (uint32_t*)(base + W.cnt), (uint32_t*)(base + W.off),
-                                      nact, active, dx_items, st);
+    int launches = launch_active_rows(dout, dstride, n, base + W.flag, (uint32_t*)(base + W.cnt),
+                                      (uint32_t*)(base + W.off), nact, active, dx_items, st);
     cudaFuncSetAttribute(k_mlp_paper_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSmem::TOTAL);
     const int64_t tiles = (n + PR - 1) / PR;
     const int grid = (int)std::min<int64_t>((tiles + PLANES - 1) / PLANES, (int64_t)num_sms_paper());
     k_mlp_paper_tc<true><<<grid, PLANES * PT, PSmem::TOTAL, st>>>(paper_dev(mlp), d_pairs, n_pairs, n, *scene,
-                                                                   nullptr, drec, *grad, dx_items, active, nact,
-                                                                   d_status);
+                                                                   nullptr, dout, dstride, *grad, dx_items, active,
+                                                                   nact, d_status);
     sssgs::note_launches(launches + 1);
     return launch_status();
 }

@@ -67,7 +67,8 @@ __device__ __forceinline__ void tmem_zero(uint32_t taddr, int n) {
 // fields 16..19) is not all zero, in item order, into active[] with their
 // count in *nact; dx_items of the other items is set to 0. Scratch: flag[n],
 // cnt/off[ceil(n / 1024)]. Returns the number of launches made.
-int launch_active_rows(const float* drec, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off, uint32_t* nact,
+int launch_active_rows(const float* dout, int64_t dstride, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off,
+                       uint32_t* nact,
                        uint32_t* active, float* dx_items, cudaStream_t st);
 
 }  // namespace sssgs

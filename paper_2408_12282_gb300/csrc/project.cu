@@ -110,13 +110,13 @@ __global__ void __launch_bounds__(256) k_project_fwd(sssgs_cfg cfg, const sssgs_
     rect[m] = r;
     const float* n = sc.normal + 3 * g;
     const float* b = sc.base + 3 * g;
-    const float* mo = mlp_out + 4 * m;
+    const float4 mo = mlp_out ? reinterpret_cast<const float4*>(mlp_out)[m] : make_float4(0.f, 0.f, 0.f, 0.f);
     float4* o = rec + 6 * m;
     o[0] = make_float4(mx, my, ca, cb);
     o[1] = make_float4(cc, G.o, G.t[2], n[0]);
     o[2] = make_float4(n[1], n[2], b[0], b[1]);
     o[3] = make_float4(b[2], sc.rough[g], sc.metal[g], sc.sss[g]);
-    o[4] = make_float4(mo[0], mo[1], mo[2], mo[3]);
+    o[4] = mo;
     // tile / sub-tile culling constants of the render kernels: 1/ca, 1/cc and
     // the padded support level of {p <= ln(o / alpha_min)}
     o[5] = make_float4(sc.vis[g], 1.f / ca, 1.f / cc, L * 1.001f + 0.01f);
@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(128) k_project_bwd(sssgs_cfg cfg, const sssgs_
         const sssgs_pair& P = pairs[p];
         if (g < P.g_begin || g >= (int64_t)P.g_begin + P.g_count) continue;
         int64_t m = P.item_offset + (g - P.g_begin);
-        const float* d = drec + (int64_t)SSSGS_REC * m;
         if (dx_items) {
             const float* x = dx_items + SSSGS_DX * m;
             dmu[0] += x[0]; dmu[1] += x[1]; dmu[2] += x[2];
@@ -143,6 +142,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(sssgs_cfg cfg, const sssgs_
             dq[0] += x[7]; dq[1] += x[8]; dq[2] += x[9]; dq[3] += x[10];
             dls[0] += x[11]; dls[1] += x[12]; dls[2] += x[13];
         }
+        if (!drec) continue;
+        const float* d = drec + (int64_t)SSSGS_REC * m;
         dn[0] += d[7]; dn[1] += d[8]; dn[2] += d[9];
         db[0] += d[10]; db[1] += d[11]; db[2] += d[12];
         dr += d[13]; dm += d[14]; dss += d[15]; dv += d[20];
@@ -248,9 +249,9 @@ static int64_t items_of(const sssgs_pair* h, int n) {
 extern "C" int sssgs_project_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                                  int n_pairs, const sssgs_scene* scene, const float* mlp_out,
                                  float* rec, int32_t* rect, sssgs_stream stream) {
-    if (!cfg_ok(cfg) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !mlp_out || !rec || !rect)
+    if (!cfg_ok(cfg) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !rec || !rect)
         return SSSGS_ERR_INVALID_ARG;
-    if (((uintptr_t)rec & 15) || ((uintptr_t)rect & 15)) return SSSGS_ERR_INVALID_ARG;
+    if (((uintptr_t)rec & 15) || ((uintptr_t)rect & 15) || ((uintptr_t)mlp_out & 15)) return SSSGS_ERR_INVALID_ARG;
     int64_t n = items_of(h_pairs, n_pairs);
     if (n == 0) return SSSGS_OK;
     unsigned blocks = (unsigned)((n + 255) / 256);
@@ -263,7 +264,7 @@ extern "C" int sssgs_project_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs
 extern "C" int sssgs_project_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                                  int n_pairs, const sssgs_scene* scene, const float* drec,
                                  const float* dx_items, const sssgs_scene_grad* grad, sssgs_stream stream) {
-    if (!cfg_ok(cfg) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || !drec || !grad)
+    if (!cfg_ok(cfg) || !h_pairs || !d_pairs || n_pairs <= 0 || !scene || (!drec && !dx_items) || !grad)
         return SSSGS_ERR_INVALID_ARG;
     if (scene->n == 0) return SSSGS_OK;
     unsigned blocks = (unsigned)((scene->n + 127) / 128);

@@ -8,7 +8,7 @@ of C-ABI calls on one CUDA stream. PyTorch only owns the memory.
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 import torch
@@ -290,6 +290,151 @@ def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=No
     table = PairTable(pairs, cfg, offs, counts, device)
     mlp = mlp_to_device(wl.mlp, precision, device)
     return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device)
+
+
+class MultiLightRenderer:
+    """A batch of views, each under the same number of point lights: the
+    light-stage batches of the paper's OLAT data (Sec. 4.1), or a relit view as
+    a weighted sum of OLAT renders (App. C "Image Based Lighting").
+
+    Projection, binning/sort and the compositing alphas run once per view
+    (table `views`); the network runs per (view, light) pair (table `pairs`,
+    view-major), and the render kernels composite the light channels and shade
+    every light of a view in one pass. Images come out per (view, light) pair
+    in pair order, or per view as a weighted sum (forward(env_w=...))."""
+
+    def __init__(self, scene: dict, mlp: MLPParams, views, lights, cfg: B.Cfg, scene_offsets, scene_counts,
+                 capacity: int | None = None, device="cuda"):
+        lights = np.asarray(lights, np.float64)
+        V, L = lights.shape[0], lights.shape[1]
+        if len(views) != V or lights.shape[2] != 3:
+            raise ValueError("lights must be n_views x n_lights x 3")
+        self.scene, self.mlp, self.cfg, self.device, self.n_lights = scene, mlp, cfg, device, L
+        self.views = PairTable(views, cfg, scene_offsets, scene_counts, device)
+        pairs = [replace(v, light=lights[k][l]) for k, v in enumerate(views) for l in range(L)]
+        self.pairs = PairTable(pairs, cfg, scene_offsets, scene_counts, device)
+        self.lights = torch.from_numpy(np.ascontiguousarray(lights.reshape(-1), np.float32)).to(device)
+        nv, npi, Pv, Pp, T = (self.views.n_items, self.pairs.n_items, self.views.n_pixels, self.pairs.n_pixels,
+                              self.views.n_tiles)
+        f32 = dict(device=device, dtype=torch.float32)
+        i32 = dict(device=device, dtype=torch.int32)
+        self.mlp_out = torch.zeros(npi, 4, **f32)
+        self.rec = torch.zeros(nv, B.REC, **f32)
+        self.rect = torch.zeros(nv, 4, **i32)
+        self.ranges = torch.zeros(T, 2, **i32)
+        self.count = torch.zeros(1, device=device, dtype=torch.int64)
+        self.status = torch.zeros(1, **i32)
+        self.gbuf = torch.zeros(Pv, 12 + 4 * L, **f32)
+        self.last = torch.zeros(Pv, **i32)
+        self.img = torch.zeros(Pp, 3, **f32)
+        self.drec = torch.zeros(nv, B.REC, **f32)
+        self.dmlp = torch.zeros(npi, 4, **f32)
+        self.dx_items = torch.zeros(npi, B.DX, **f32)
+        self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
+        self.dW = [torch.zeros_like(w) for w in mlp.W]
+        self.db = [torch.zeros_like(b) for b in mlp.b]
+        self._scene_s = B.scene_struct(scene)
+        self._grad_s = B.scene_grad_struct(self.grads)
+        self._mlp_s = mlp.struct()
+        self._mlp_g = B.mlp_grad_struct(self.dW, self.db)
+        mws = B.mlp_workspace_bytes(self._mlp_s, npi)
+        self.ws_mlp = torch.empty(max(mws, 256), device=device, dtype=torch.uint8)
+        self.stats_fwd = None
+        self.stats_bwd = None
+        self.capacity = 0
+        self.set_capacity(capacity if capacity is not None else max(1024, 16 * nv))
+
+    def set_capacity(self, cap: int):
+        self.capacity = int(cap)
+        self.vals = torch.zeros(max(self.capacity, 1), device=self.device, dtype=torch.int32)
+        wsb = B.bin_workspace_bytes(self.views.n_items, self.capacity, self.views.n_tiles)
+        self.ws_bin = torch.empty(max(wsb, 256), device=self.device, dtype=torch.uint8)
+
+    def fit_capacity(self, slack: float = 1.15):
+        self.forward_front()
+        torch.cuda.synchronize()
+        need = int(self.count.item())
+        if need > self.capacity or self.status.item() != 0:
+            self.set_capacity(int(need * slack) + 1024)
+            self.status.zero_()
+            self.forward_front()
+            torch.cuda.synchronize()
+        return need
+
+    def forward_front(self, stream=None):
+        v, p = self.views, self.pairs
+        B.mlp_fwd(self._mlp_s, p.h, p.d, self._scene_s, self.mlp_out, self.status, stream)
+        B.project_fwd(self.cfg, v.h, v.d, self._scene_s, None, self.rec, self.rect, stream)
+        B.bin_sort(self.cfg, v.h, v.d, self.rec, self.rect, self.capacity, self.vals, self.ranges, self.count,
+                   self.status, self.ws_bin, stream)
+
+    def forward(self, stream=None, env_w=None, out=None):
+        """Per-(view, light) images into self.img; with env_w (device
+        float[n_views * n_lights]) the weighted sum per view into `out`
+        (n_view_pixels x 3)."""
+        self.forward_front(stream)
+        v = self.views
+        img = self.img if env_w is None else out
+        B.render_ml_fwd(self.cfg, v.h, v.d, self.n_lights, self.lights, self.rec, self.mlp_out, self.vals,
+                        self.ranges, self.gbuf, self.last, img, env_w, self.stats_fwd, stream)
+        return img
+
+    def zero_grads(self):
+        self.drec.zero_()
+        self.dmlp.zero_()
+        for g in self.grads.values():
+            g.zero_()
+        for g in self.dW + self.db:
+            g.zero_()
+
+    def backward(self, dimg=None, target=None, l1_scale=1.0, stream=None):
+        """Upstream: dimg per (view, light) image, or the L1 loss against target."""
+        v, p = self.views, self.pairs
+        self.zero_grads()
+        B.render_ml_bwd(self.cfg, v.h, v.d, self.n_lights, self.lights, self.rec, self.mlp_out, self.vals,
+                        self.ranges, self.gbuf, self.last, self.img, dimg, target, l1_scale, self.drec, self.dmlp,
+                        self.stats_bwd, stream)
+        B.mlp_bwd_strided(self._mlp_s, p.h, p.d, self._scene_s, self.dmlp, 4, self._mlp_g, self.dx_items,
+                          self.ws_mlp, self.status, stream)
+        B.project_bwd(self.cfg, v.h, v.d, self._scene_s, self.drec, None, self._grad_s, stream)
+        B.project_bwd(self.cfg, p.h, p.d, self._scene_s, None, self.dx_items, self._grad_s, stream)
+
+    def capture(self, dimg=None, target=None, l1_scale=1.0):
+        """One forward + backward step as a CUDA graph (call fit_capacity() first)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.forward()
+            self.backward(dimg=dimg, target=target, l1_scale=l1_scale)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self.forward()
+            self.backward(dimg=dimg, target=target, l1_scale=l1_scale)
+        torch.cuda.synchronize()
+        return g
+
+    def check_status(self):
+        s = int(self.status.item())
+        if s & B.STATUS_CAPACITY:
+            raise B.SSSGSError(f"instance capacity {self.capacity} exceeded ({int(self.count.item())} needed)")
+        if s & B.STATUS_TIMEOUT:
+            raise B.SSSGSError("a tensor-core kernel stopped on its wait limit; outputs are incomplete")
+
+
+def multilight_renderer_for_workload(wl, precision=None, capacity=None, device="cuda") -> MultiLightRenderer:
+    """Views and lights of a workload whose pairs come in runs of wl.n_lights
+    sharing a camera (scenegen c6)."""
+    L = wl.n_lights
+    if len(wl.pairs) % L:
+        raise ValueError("pair count is not a multiple of n_lights")
+    views = wl.pairs[::L]
+    lights = np.array([[p.light for p in wl.pairs[k:k + L]] for k in range(0, len(wl.pairs), L)])
+    cfg = default_cfg(16)
+    scene, offs, counts = concat_scenes(wl.scenes, device)
+    mlp = mlp_to_device(wl.mlp, precision, device)
+    return MultiLightRenderer(scene, mlp, views, lights, cfg, offs, counts, capacity=capacity, device=device)
 
 
 def autotune_tile(wl, candidates=(16, 8), precision=None, steps=2, device="cuda", capacity_slack=1.15):

@@ -108,6 +108,7 @@ class Workload:
     mlp: MLPSpec
     tile: int = 16
     target_scene: Scene | None = None   # perturbed scene for the L1 target
+    n_lights: int = 1        # lights per view: pairs come in runs of n_lights sharing one camera
 
 
 # --------------------------------------------------------------------------
@@ -312,12 +313,29 @@ def _hemisphere_dir(rng, zmin=0.15):
             return v
 
 
+def light_stage(radius: float = 4.0, rings: int = 7, per_ring: int = 16) -> np.ndarray:
+    """The synthetic light stage of Sec. 4.1: `rings` rings of `per_ring` point
+    lights on the upper hemisphere (elevations evenly spaced strictly between
+    the horizon and the pole, rings offset by half a step in azimuth)."""
+    out = []
+    for r in range(rings):
+        el = (r + 0.5) * (0.5 * math.pi) / rings
+        for k in range(per_ring):
+            az = 2.0 * math.pi * (k + 0.5 * (r % 2)) / per_ring
+            out.append(radius * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)]))
+    return np.array(out)
+
+
 def make_workload(name: str, *, N: int | None = None, res=None,
-                  n_pairs: int | None = None, seed_offset: int = 0, net: str | None = None) -> Workload:
-    """Build configuration `name` ("c1".."c5"); N/res/n_pairs shrink it for tests.
+                  n_pairs: int | None = None, seed_offset: int = 0, net: str | None = None,
+                  n_views: int | None = None, n_lights: int | None = None) -> Workload:
+    """Build configuration `name` ("c1".."c6"); N/res/n_pairs shrink it for tests.
     For c5, `res` may be a tuple of resolutions to draw from. net="paper"
-    replaces the configuration's network by the paper's (App. E)."""
-    wl = _make_workload(name, N=N, res=res, n_pairs=n_pairs, seed_offset=seed_offset)
+    replaces the configuration's network by the paper's (App. E). c6 is a
+    light-stage batch of n_views views (default 8) under n_lights lights each
+    (default 8) of the 112-light stage."""
+    wl = _make_workload(name, N=N, res=res, n_pairs=n_pairs, seed_offset=seed_offset, n_views=n_views,
+                        n_lights=n_lights)
     if net == "paper":   # keeps the configuration's precision (BF16 tensor cores for c3-c5)
         wl.mlp = mlp_spec(int(name[1]) * 1000 + seed_offset + 13, "paper", [], precision=wl.mlp.precision)
     elif net is not None:
@@ -326,7 +344,8 @@ def make_workload(name: str, *, N: int | None = None, res=None,
 
 
 def _make_workload(name: str, *, N: int | None = None, res=None,
-                   n_pairs: int | None = None, seed_offset: int = 0) -> Workload:
+                   n_pairs: int | None = None, seed_offset: int = 0, n_views: int | None = None,
+                   n_lights: int | None = None) -> Workload:
     idx = int(name[1])
     seed = idx * 1000 + seed_offset
     rng = np.random.Generator(np.random.PCG64(seed + 7))
@@ -386,6 +405,20 @@ def _make_workload(name: str, *, N: int | None = None, res=None,
                 pairs.append(_make_pair(cams[k], lights[rc], r, r, scene=s))
         mlp = mlp_spec(seed + 11, "pe6", [128, 128, 128, 128], precision="bf16")
         return Workload(name, scenes, pairs, mlp, 16, None)
+    if name == "c6":
+        n = N or 300_000
+        W = res or 800
+        V = n_views or 8
+        L = n_lights or 8
+        scene = blob_scene(3000 + seed_offset, n)      # the c3 scene
+        cams = fibonacci_sphere(V, 3.0, upper=True)
+        stage = light_stage(4.0)
+        pairs = []
+        for v in range(V):
+            for li in rng.choice(len(stage), size=L, replace=False):
+                pairs.append(_make_pair(cams[v], stage[li], W, W))
+        mlp = mlp_spec(3000 + seed_offset + 11, "pe6", [128, 128, 128, 128], precision="bf16")
+        return Workload(name, [scene], pairs, mlp, 16, None, n_lights=L)
     raise ValueError(f"unknown workload {name!r}")
 
 

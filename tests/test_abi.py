@@ -6,6 +6,7 @@ import re
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2408_12282_gb300 import binding as B
 
@@ -90,3 +91,15 @@ def test_argument_errors_launch_nothing():
     c.tile = 5
     assert lib.sssgs_render_fwd(ctypes.byref(c), h, 16, 1, 16, 16, 16, 16, 16, 16, None, None) == -1
     assert lib.sssgs_bin_sort(ctypes.byref(c), h, 16, 1, 16, 16, -1, 16, 16, 16, 16, 16, 0, None) == -1
+
+
+def test_binding_refuses_float64_and_strided_buffers():
+    """Every buffer of the C ABI is dense float32 / int32 / uint8 / int64: a
+    float64 or strided tensor would be read with the wrong layout, so the
+    binding refuses it before any call."""
+    with pytest.raises(TypeError):
+        B._p(torch.zeros(4, 3, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        B._p(torch.zeros(4, 6)[:, ::2])
+    assert B._p(None) is None
+    assert B._p(torch.zeros(4, 3)) != 0
