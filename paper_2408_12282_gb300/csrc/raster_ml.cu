@@ -52,11 +52,18 @@ __device__ __forceinline__ void ml_features(const float* geo, float vis, const f
     F[14] = vis;
 }
 
+#ifndef SSSGS_ML_BWD_BLOCKS8      // resident one-warp blocks per SM the L = 8 backward is built for
+#define SSSGS_ML_BWD_BLOCKS8 8
+#endif
 template <int L>
 struct MlBlocks {
     static constexpr int FWD = L <= 2 ? 16 : (L == 4 ? 14 : 10);
-    static constexpr int BWD = L <= 2 ? 16 : (L == 4 ? 12 : 8);
+    static constexpr int BWD = L <= 2 ? 16 : (L == 4 ? 12 : SSSGS_ML_BWD_BLOCKS8);
 };
+
+// Record float4s the many-light kernels read: 0..3 and 5 (4 holds L_SSS, L_in,
+// which live in the per-light network output instead).
+__device__ __forceinline__ int ml_rec_q(int q) { return q < 4 ? q : 5; }
 
 template <int L>
 __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
@@ -65,7 +72,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
     const uint2* __restrict__ ranges, float* __restrict__ gbuf, uint32_t* __restrict__ last,
     float* __restrict__ img, const float* __restrict__ env_w, unsigned long long* __restrict__ stats) {
     constexpr int GB = ML_GEO + 4 * L;
-    __shared__ __align__(16) float4 s_rec[2][6][32];
+    __shared__ __align__(16) float4 s_rec[2][5][32];     // record float4s 0..3, 5
     __shared__ __align__(16) float4 s_lf[2][L][32];
     __shared__ __align__(16) sssgs_pair sP;
     __shared__ float s_light[L * 3];
@@ -101,7 +108,8 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
         if (item != ML_NONE) {
             const float4* r = rec + 6 * (int64_t)item;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + q);
+            for (int q = 0; q < 5; ++q)
+                cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + ml_rec_q(q));
 #pragma unroll
             for (int l = 0; l < L; ++l)
                 cp_async16((uint32_t)__cvta_generic_to_shared(&s_lf[buf][l][lane]), mlp_out + ml_row(sP, L, l, item));
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
             cp_async_wait1();
             bool pass = false;
             if (it0 != ML_NONE) {
-                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][5][lane];
+                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][4][lane];
                 pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0, y0 + 3.f);
             }
             uint32_t bits = __ballot_sync(SSSGS_FULL, pass);
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
                 geo[0] += w * g1.z; geo[1] += w * g1.w; geo[2] += w * g2.x; geo[3] += w * g2.y;
                 geo[4] += w * g2.z; geo[5] += w * g2.w; geo[6] += w * g3.x; geo[7] += w * g3.y;
                 geo[8] += w * g3.z; geo[9] += w * g3.w;
-                vis += w * s_rec[buf][5][k].x;
+                vis += w * s_rec[buf][4][k].x;
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
                     const float4 v = s_lf[buf][l][k];
@@ -224,10 +232,11 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
     const float* __restrict__ img, const float* __restrict__ dimg, const float* __restrict__ target,
     float l1_scale, float* __restrict__ drec, float* __restrict__ dmlp, unsigned long long* __restrict__ stats) {
     constexpr int GB = ML_GEO + 4 * L, NG = 17 + 4 * L, RS = 36;
-    __shared__ __align__(16) float4 s_rec[2][6][32];
+    constexpr int NR = NG < 32 ? NG : 32;                 // rows the transpose buffer holds at once
+    __shared__ __align__(16) float4 s_rec[2][5][32];     // record float4s 0..3, 5
     __shared__ __align__(16) float4 s_lf[2][L][32];
     __shared__ uint32_t s_item[2][32];
-    __shared__ __align__(16) float s_red[NG * RS];
+    __shared__ __align__(16) float s_red[NR * RS];
     __shared__ __align__(16) sssgs_pair sP;
     __shared__ float s_light[L * 3];
     const int tile = blockIdx.x / ML_NSUB, sub = blockIdx.x % ML_NSUB;
@@ -310,8 +319,8 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
             if (item != ML_NONE) {
                 const float4* r = rec + 6 * (int64_t)item;
 #pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + q);
+                for (int q = 0; q < 5; ++q)
+                    cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + ml_rec_q(q));
 #pragma unroll
                 for (int l = 0; l < L; ++l)
                     cp_async16((uint32_t)__cvta_generic_to_shared(&s_lf[buf][l][lane]),
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
             cp_async_wait1();
             bool pass = false;
             if (it0 != ML_NONE) {
-                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][5][lane];
+                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][4][lane];
                 pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0, y0 + 3.f);
             }
             s_item[buf][lane] = it0;
@@ -344,10 +353,11 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
                 const AlphaEval e = eval_alpha(g0, g1, px, py, a_min, a_max);
                 const bool act = (pos < lastc) && e.use;
                 if (!__any_sync(SSSGS_FULL, act)) continue;
+                float wk;                              // this lane's compositing weight of the splat
                 {
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k];
                     const float f[10] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w};
-                    const float fv = s_rec[buf][5][k].x;
+                    const float fv = s_rec[buf][4][k].x;
                     float dot = dvis * fv;
 #pragma unroll
                     for (int kk = 0; kk < 10; ++kk) dot = fmaf(dgeo[kk], f[kk], dot);
@@ -381,39 +391,49 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
 #pragma unroll
                     for (int kk = 0; kk < 10; ++kk) col[(6 + kk) * RS] = w * dgeo[kk];
                     col[16 * RS] = w * dvis;
+                    if constexpr (NG <= NR) {          // all rows in one transpose
 #pragma unroll
-                    for (int l = 0; l < L; ++l)
+                        for (int l = 0; l < L; ++l)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) col[(17 + 4 * l + c) * RS] = w * dlf[l][c];
+                            for (int c = 0; c < 4; ++c) col[(17 + 4 * l + c) * RS] = w * dlf[l][c];
+                    }
+                    wk = w;
                 }
                 __syncwarp();
                 const uint32_t item = s_item[buf][k];
+                // sum of the 32 lanes' terms of row r of the transpose buffer
+                auto row_sum = [&](int r) -> float {
+                    const float4* row = reinterpret_cast<const float4*>(s_red + r * RS);
+                    float2 a[16];
 #pragma unroll
-                for (int r0 = 0; r0 < NG; r0 += 32) {
-                    const int r = r0 + lane;
-                    if (r < NG) {   // sum of the 32 lanes' terms of row r
-                        const float4* row = reinterpret_cast<const float4*>(s_red + r * RS);
-                        float2 a[16];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 v = row[q];
-                            a[2 * q] = make_float2(v.x, v.y);
-                            a[2 * q + 1] = make_float2(v.z, v.w);
-                        }
-#pragma unroll
-                        for (int h = 8; h >= 1; h >>= 1)
-#pragma unroll
-                            for (int q = 0; q < h; ++q) a[q] = __fadd2_rn(a[q], a[q + h]);
-                        const float sum = a[0].x + a[0].y;
-                        if (r < 16) {
-                            atomicAdd(drec + (int64_t)SSSGS_REC * item + r, sum);
-                        } else if (r == 16) {
-                            atomicAdd(drec + (int64_t)SSSGS_REC * item + 20, sum);
-                        } else {
-                            const int l = (r - 17) >> 2, c = (r - 17) & 3;
-                            atomicAdd(dmlp + 4 * ml_row(sP, L, l, item) + c, sum);
-                        }
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 v = row[q];
+                        a[2 * q] = make_float2(v.x, v.y);
+                        a[2 * q + 1] = make_float2(v.z, v.w);
                     }
+#pragma unroll
+                    for (int h = 8; h >= 1; h >>= 1)
+#pragma unroll
+                        for (int q = 0; q < h; ++q) a[q] = __fadd2_rn(a[q], a[q + h]);
+                    return a[0].x + a[0].y;
+                };
+                auto light_add = [&](int r, float sum) {   // light row r = 4 l + c
+                    atomicAdd(dmlp + 4 * ml_row(sP, L, r >> 2, item) + (r & 3), sum);
+                };
+                if (lane < 17) {
+                    const float sum = row_sum(lane);
+                    atomicAdd(drec + (int64_t)SSSGS_REC * item + (lane < 16 ? lane : 20), sum);
+                } else if (NG <= NR && lane < NG) {
+                    light_add(lane - 17, row_sum(lane));
+                }
+                if constexpr (NG > NR) {               // light channels in a second transpose
+                    __syncwarp();
+#pragma unroll
+                    for (int l = 0; l < L; ++l)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) s_red[(4 * l + c) * RS + lane] = wk * dlf[l][c];
+                    __syncwarp();
+                    if (lane < 4 * L) light_add(lane, row_sum(lane));
                 }
                 __syncwarp();
             }
