@@ -189,6 +189,9 @@ def _config(args):
            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
     if args.pairs is not None:
         cfg["pairs_override"] = args.pairs
+    if getattr(args, "vis_sh", False):
+        cfg["visibility"] = ("SH term per Gaussian (degree 3, evaluated at each pair's light direction) with the "
+                             "ray-traced visibility loss (0.01 L1 to a BVH-traced target)")
     if getattr(args, "views", None) is not None:
         cfg["views_override"] = args.views
     if getattr(args, "lights", None) is not None:
@@ -292,8 +295,25 @@ def run_ours(args):
 
     wl = sg.make_workload(args.workload, seed_offset=rank, n_pairs=args.pairs, net=args.net)
     precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
-    r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile)
+    vis_sh = sg.vis_sh_coeffs(77 + rank, sum(sc.N for sc in wl.scenes)) if args.vis_sh else None
+    r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile, vis_sh=vis_sh)
     n_inst = r.fit_capacity()
+    trace = None
+    if args.vis_sh:
+        # ray-traced visibility target (BVH build + one ray per item), timed once
+        r.trace_visibility()
+        torch.cuda.synchronize()
+        tb0, tb1, tt1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        tb0.record()
+        B.bvh_build(r.cfg, r._scene_s, r.bvh, r.ws_bvh)
+        tb1.record()
+        B.trace_visibility(r.cfg, r.table.h, r.table.d, r._scene_s, r.bvh, r.vis_traced)
+        tt1.record()
+        torch.cuda.synchronize()
+        tms = tb1.elapsed_time(tt1)
+        trace = {"rays": r.table.n_items, "bvh_build_ms": tb0.elapsed_time(tb1), "trace_ms": tms,
+                 "rays_per_s": r.table.n_items * 1000.0 / tms,
+                 "mean_visibility": float(r.vis_traced.mean().item())}
     table = r.table
     n_pairs = table.n
     # target images from the perturbed scene (untimed set-up)
@@ -368,8 +388,15 @@ def run_ours(args):
     reps = max(2, min(args.steps, 5))
     stats_f = torch.zeros(2, dtype=torch.int64, device="cuda")
     stats_b = torch.zeros(2, dtype=torch.int64, device="cuda")
+    if args.vis_sh:
+        stage_ms["vis_sh"] = 0.0
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+        ev_v = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        if args.vis_sh:
+            ev_v[0].record(st)
+            B.vis_sh_fwd(table.h, table.d, r._scene_s, r.vis_sh, r.vis_item)
+            ev_v[1].record(st)
         ev[0].record(st)
         B.mlp_fwd(r._mlp_s, table.h, table.d, r._scene_s, r.mlp_out, r.status)
         ev[1].record(st)
@@ -402,7 +429,15 @@ def run_ours(args):
         ev[6].record(st)
         B.project_bwd(r.cfg, table.h, table.d, r._scene_s, r.drec, r.dx_items, r._grad_s)
         ev[7].record(st)
+        if args.vis_sh:
+            ev_v[2].record(st)
+            r.loss_vis = r.loss_vis if r.loss_vis is not None else torch.zeros(table.n, device="cuda")
+            B.vis_loss(table.h, table.d, r.vis_item, r.vis_traced, 0.01, r.dvis_item, r.loss_vis)
+            B.vis_sh_bwd(table.h, table.d, r._scene_s, r.vis_sh, r.dvis_item, r.dvis_sh, r.grads["mu"])
+            ev_v[3].record(st)
         torch.cuda.synchronize()
+        if args.vis_sh:
+            stage_ms["vis_sh"] += (ev_v[0].elapsed_time(ev_v[1]) + ev_v[2].elapsed_time(ev_v[3])) / reps
         for i, s in enumerate(STAGES):
             a = e_z if s == "render_bwd" else ev[i]
             b = e_l[2] if (s == "render_bwd" and args.loss == "paper") else ev[i + 1]
@@ -543,7 +578,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "bf16+f32" if precision == B.BF16 else "f32",
                 "data": "synthetic", "config": _config(args),
                 "roofline": roof, "step_hbm_frac_of_algorithmic": step_hbm_frac,
-                "stage_ms": stage_ms, "loss_roofline": loss_roof, "instances": n_inst, "items": n_items, "mlp_bwd_rows": n_active, "pixels": n_pixels,
+                "stage_ms": stage_ms, "loss_roofline": loss_roof, "visibility_trace": trace, "instances": n_inst, "items": n_items, "mlp_bwd_rows": n_active, "pixels": n_pixels,
                 "contributions_per_step": {"forward": contrib_f, "backward": contrib_b},
                 "cuda_graph": graph is not None,
                 "plain_fp32": plain, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
@@ -794,6 +829,9 @@ def main():
     ap.add_argument("--loss", default="l1", choices=["l1", "paper"],
                     help="paper: the training losses of App. E (L1 + D-SSIM image loss, incident constraint)")
     ap.add_argument("--fp32-mlp", action="store_true")
+    ap.add_argument("--vis-sh", action="store_true",
+                    help="SH visibility term per Gaussian (v evaluated at each pair's light) with the ray-traced "
+                         "visibility loss; also times the BVH build and the tracing")
     ap.add_argument("--plain-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

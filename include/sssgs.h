@@ -122,15 +122,23 @@ typedef struct sssgs_plan_info {
 
 /* Per-Gaussian parameters (float32 device arrays, concatenated over scenes):
  * mu N*3, log_s N*3, quat N*4 (w,x,y,z; normalised inside), logit_o N,
- * normal N*3, base N*3, rough N, metal N, sss N, vis N. */
+ * normal N*3, base N*3, rough N, metal N, sss N, vis N.
+ * vis_item (optional, NULL: unused): the visibility per item (pair,
+ * Gaussian) instead of per Gaussian, e.g. the SH visibility term evaluated at
+ * each pair's light direction (sssgs_vis_sh_fwd); when set, the projection and
+ * the network read v from it and vis is not read. */
 typedef struct sssgs_scene {
     const float *mu, *log_s, *quat, *logit_o, *normal, *base, *rough, *metal, *sss, *vis;
     int64_t n;
+    const float* vis_item;
 } sssgs_scene;
 
-/* Gradients of the same shapes (accumulated). Any pointer may be NULL to skip. */
+/* Gradients of the same shapes (accumulated). Any pointer may be NULL to skip.
+ * vis_item: with a per-item visibility, sssgs_project_bwd accumulates dL/dv
+ * per item here (n_items floats) instead of into vis. */
 typedef struct sssgs_scene_grad {
     float *mu, *log_s, *quat, *logit_o, *normal, *base, *rough, *metal, *sss, *vis;
+    float* vis_item;
 } sssgs_scene_grad;
 
 enum { SSSGS_MLP_BASIC = 0, SSSGS_MLP_PE6 = 1, SSSGS_MLP_PAPER = 2 };
@@ -342,6 +350,48 @@ int sssgs_render_ml_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const s
                         const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
                         const float* img, const float* dimg, const float* target, float l1_scale, float* drec,
                         float* dmlp, uint64_t* d_stats, sssgs_stream stream);
+
+/* Ray-traced visibility and the SH visibility term (Sec. 3.2 "Incident
+ * Light": visibility is estimated by tracing rays through the Gaussians with a
+ * BVH and learnt as a per-Gaussian SH visibility term v; App. E "Losses":
+ * lambda_raytrace = 0.01).
+ *
+ * Tracing: the visibility of item m (pair p, Gaussian i) is the transmittance
+ * of the segment from mu_i to p's light through every other Gaussian j:
+ * prod_j (1 - alpha_j), alpha_j = min(alpha_max, o_j exp(-q/2)), q the
+ * minimum of the Mahalanobis distance (x - mu_j)^T Sigma_j^-1 (x - mu_j) over
+ * the ray, counted when that minimum lies inside the segment and alpha_j >=
+ * alpha_min. Stops once the product is below 1e-5.
+ *
+ * sssgs_bvh_build: a linear BVH (Morton order of the means, 30-bit codes) over
+ * the boxes bounding each Gaussian's support {alpha >= alpha_min}. Writes
+ * bvh[sssgs_bvh_floats(n)] (nodes and per-Gaussian tracing records); the
+ * caller allocates it and the workspace (sssgs_bvh_workspace_bytes, 256-byte
+ * aligned). The BVH holds the scene's geometry as it is when built. */
+int64_t sssgs_bvh_floats(int64_t n_gaussians);
+size_t sssgs_bvh_workspace_bytes(int64_t n_gaussians);
+int sssgs_bvh_build(const sssgs_cfg* cfg, const sssgs_scene* scene, float* bvh, void* workspace,
+                    size_t workspace_bytes, sssgs_stream stream);
+/* One ray per item of the pairs: vis_traced[n_items]. */
+int sssgs_trace_visibility(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                           const sssgs_scene* scene, const float* bvh, float* vis_traced, sssgs_stream stream);
+
+/* SH visibility: vis_sh[N*16] real spherical-harmonic coefficients per
+ * Gaussian (degree 3, orthonormal, no Condon-Shortley phase; index l^2 + l + m).
+ * Forward: vis_item[m] = clamp(sum_k c_k Y_k(w), 0, 1), w = unit(light - mu)
+ * of item m's pair. Backward: from dvis_item[n_items] accumulates dvis_sh and
+ * the mean gradient dmu (through w); zero where the clamp is active. */
+int sssgs_vis_sh_fwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const sssgs_scene* scene,
+                     const float* vis_sh, float* vis_item, sssgs_stream stream);
+int sssgs_vis_sh_bwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const sssgs_scene* scene,
+                     const float* vis_sh, const float* dvis_item, float* dvis_sh, float* dmu, sssgs_stream stream);
+
+/* Ray-traced visibility loss per pair p: lambda_raytrace * mean over its items
+ * of |vis_item - vis_traced| (the traced value a constant target). Adds
+ * dL/dvis_item to dvis_item and the loss to d_loss[p]. */
+int sssgs_vis_loss(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const float* vis_item,
+                   const float* vis_traced, float lambda_raytrace, float* dvis_item, float* d_loss,
+                   sssgs_stream stream);
 
 /* Training losses (Appendix E "Losses").
  * Image loss per pair p: L_img = (1 - lambda_dssim) L1 + lambda_dssim (1 - SSIM)

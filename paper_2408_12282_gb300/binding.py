@@ -50,11 +50,11 @@ _SCENE_FIELDS = ("mu", "log_s", "quat", "logit_o", "normal", "base", "rough", "m
 
 
 class Scene(ctypes.Structure):
-    _fields_ = [(k, c_vp) for k in _SCENE_FIELDS] + [("n", c_i64)]
+    _fields_ = [(k, c_vp) for k in _SCENE_FIELDS] + [("n", c_i64), ("vis_item", c_vp)]
 
 
 class SceneGrad(ctypes.Structure):
-    _fields_ = [(k, c_vp) for k in _SCENE_FIELDS]
+    _fields_ = [(k, c_vp) for k in _SCENE_FIELDS] + [("vis_item", c_vp)]
 
 
 class MLP(ctypes.Structure):
@@ -108,6 +108,16 @@ _SIGS = {
     "sssgs_render_ml_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.c_int, c_vp,
                              c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp, c_vp],
                             ctypes.c_int),
+    "sssgs_bvh_floats": ([c_i64], c_i64),
+    "sssgs_bvh_workspace_bytes": ([c_i64], ctypes.c_size_t),
+    "sssgs_bvh_build": ([ctypes.POINTER(Cfg), ctypes.POINTER(Scene), c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
+    "sssgs_trace_visibility": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
+                                c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_vis_sh_fwd": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp, c_vp, c_vp],
+                         ctypes.c_int),
+    "sssgs_vis_sh_bwd": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp, c_vp, c_vp, c_vp,
+                          c_vp], ctypes.c_int),
+    "sssgs_vis_loss": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_image_loss_workspace_bytes": ([c_i64], ctypes.c_size_t),
     "sssgs_image_loss": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp,
                           c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
@@ -193,13 +203,13 @@ def plan(pairs_arr, cfg: Cfg) -> PlanInfo:
     return info
 
 
-def scene_struct(t: dict) -> Scene:
-    s = Scene(*[_p(t[k]) for k in _SCENE_FIELDS], t["mu"].shape[0])
-    return s
+def scene_struct(t: dict, vis_item=None) -> Scene:
+    """vis_item: optional per-item visibility (n_items floats)."""
+    return Scene(*[_p(t[k]) for k in _SCENE_FIELDS], t["mu"].shape[0], _p(vis_item))
 
 
-def scene_grad_struct(t: dict) -> SceneGrad:
-    return SceneGrad(*[_p(t.get(k)) for k in _SCENE_FIELDS])
+def scene_grad_struct(t: dict, vis_item=None) -> SceneGrad:
+    return SceneGrad(*[_p(t.get(k)) for k in _SCENE_FIELDS], _p(vis_item))
 
 
 def mlp_struct(kind: int, precision: int, Ws, bs) -> MLP:
@@ -340,6 +350,42 @@ def project_bwd(cfg: Cfg, pairs, d_pairs, scene: Scene, drec, dx_items, grad: Sc
     _check(load_library().sssgs_project_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
                                             _p(drec), _p(dx_items), ctypes.byref(grad), _stream(stream)),
            "sssgs_project_bwd")
+
+
+def bvh_floats(n: int) -> int:
+    return int(load_library().sssgs_bvh_floats(n))
+
+
+def bvh_workspace_bytes(n: int) -> int:
+    return int(load_library().sssgs_bvh_workspace_bytes(n))
+
+
+def bvh_build(cfg: Cfg, scene: Scene, bvh, workspace, stream=None):
+    _check(load_library().sssgs_bvh_build(ctypes.byref(cfg), ctypes.byref(scene), _p(bvh), _p(workspace),
+                                          workspace.numel() * workspace.element_size(), _stream(stream)),
+           "sssgs_bvh_build")
+
+
+def trace_visibility(cfg: Cfg, pairs, d_pairs, scene: Scene, bvh, vis_traced, stream=None):
+    _check(load_library().sssgs_trace_visibility(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs),
+                                                 ctypes.byref(scene), _p(bvh), _p(vis_traced), _stream(stream)),
+           "sssgs_trace_visibility")
+
+
+def vis_sh_fwd(pairs, d_pairs, scene: Scene, vis_sh, vis_item, stream=None):
+    _check(load_library().sssgs_vis_sh_fwd(pairs, _p(d_pairs), len(pairs), ctypes.byref(scene), _p(vis_sh),
+                                           _p(vis_item), _stream(stream)), "sssgs_vis_sh_fwd")
+
+
+def vis_sh_bwd(pairs, d_pairs, scene: Scene, vis_sh, dvis_item, dvis_sh, dmu, stream=None):
+    _check(load_library().sssgs_vis_sh_bwd(pairs, _p(d_pairs), len(pairs), ctypes.byref(scene), _p(vis_sh),
+                                           _p(dvis_item), _p(dvis_sh), _p(dmu), _stream(stream)), "sssgs_vis_sh_bwd")
+
+
+def vis_loss(pairs, d_pairs, vis_item, vis_traced, lambda_raytrace, dvis_item, d_loss, stream=None):
+    _check(load_library().sssgs_vis_loss(pairs, _p(d_pairs), len(pairs), _p(vis_item), _p(vis_traced),
+                                         float(lambda_raytrace), _p(dvis_item), _p(d_loss), _stream(stream)),
+           "sssgs_vis_loss")
 
 
 def image_loss_workspace_bytes(n_pixels: int) -> int:

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_fwd(MlpDev net, const sssgs
             if (m < n_items) {
                 const int p = pair_of_item(pairs, n_pairs, m);
                 const sssgs_pair& P = pairs[p];
-                build_input(net, P, sc, P.g_begin + (m - P.item_offset), x);
+                build_input(net, P, sc, P.g_begin + (m - P.item_offset), m, x);
             } else {
                 for (int k = 0; k < net.w[0]; ++k) x[k] = 0.f;
             }
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_bwd_a(MlpDev net, const sss
             if (r0 + threadIdx.x < rows) {
                 const int p = pair_of_item(pairs, n_pairs, m);
                 const sssgs_pair& P = pairs[p];
-                build_input(net, P, sc, P.g_begin + (m - P.item_offset), x);
+                build_input(net, P, sc, P.g_begin + (m - P.item_offset), m, x);
             } else {
                 for (int k = 0; k < net.w[0]; ++k) x[k] = 0.f;
             }

@@ -16,8 +16,14 @@ struct MlpDev {
 };
 
 // Network input of item m (row of width w[0]) written to x.
+// Visibility v of item m (Gaussian g): the per-item array when the scene has
+// one (SH visibility at the pair's light direction), else the Gaussian's.
+__device__ __forceinline__ float vis_of(const sssgs_scene& sc, int64_t g, int64_t m) {
+    return sc.vis_item ? __ldg(sc.vis_item + m) : __ldg(sc.vis + g);
+}
+
 __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
-                                            int64_t g, float* x) {
+                                            int64_t g, int64_t m, float* x) {
     const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
     const float3 C = cam_center(P);
     float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
@@ -39,7 +45,7 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
         x[10] = wi.x; x[11] = wi.y; x[12] = wi.z;
         x[13] = wo.x; x[14] = wo.y; x[15] = wo.z;
         x[16] = li;
-        x[17] = sc.vis[g];
+        x[17] = vis_of(sc, g, m);
         const float mm[3] = {m0, m1, m2};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -71,7 +77,7 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
     x[42] = wi.x; x[43] = wi.y; x[44] = wi.z;
     x[45] = sc.normal[3 * g]; x[46] = sc.normal[3 * g + 1]; x[47] = sc.normal[3 * g + 2];
     x[48] = li;
-    x[49] = sc.vis[g];
+    x[49] = vis_of(sc, g, m);
     for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
 }
 
@@ -189,19 +195,20 @@ __device__ __forceinline__ void pe6_direct(const sssgs_pair& P, const float (&mm
 struct Pe6Params {
     float mu[3], n[3], v;
 };
-__device__ __forceinline__ Pe6Params load_pe6_params(const sssgs_scene& sc, int64_t g) {
+__device__ __forceinline__ Pe6Params load_pe6_params(const sssgs_scene& sc, int64_t g, int64_t m) {
     Pe6Params q;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         q.mu[c] = __ldg(sc.mu + 3 * g + c);
         q.n[c] = __ldg(sc.normal + 3 * g + c);
     }
-    q.v = __ldg(sc.vis + g);
+    q.v = vis_of(sc, g, m);
     return q;
 }
 
-__device__ __forceinline__ void build_input_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g, float (&x)[64]) {
-    const Pe6Params q = load_pe6_params(sc, g);
+__device__ __forceinline__ void build_input_pe6(const sssgs_pair& P, const sssgs_scene& sc, int64_t g, int64_t m,
+                                                float (&x)[64]) {
+    const Pe6Params q = load_pe6_params(sc, g, m);
     pe6_fourier<0, 6>(q.mu, x);
     pe6_direct(P, q.mu, q.n, q.v, x + 36);
 }

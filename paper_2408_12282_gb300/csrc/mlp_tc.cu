@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
             if (m < n_items) {
                 const int p = pair_lookup(s_off, pairs, n_pairs, m);
                 const sssgs_pair& P = pairs[p];
-                build_input_pe6(P, sc, P.g_begin + (m - P.item_offset), x);
+                build_input_pe6(P, sc, P.g_begin + (m - P.item_offset), m, x);
             }
 #pragma unroll
             for (int c = 0; c < 64; c += 8) store8_bf16(sA, t, c, 64, x + c);
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             const int64_t mr = active[row];
             r.m = mr;
             r.pidx = pair_lookup(s_off, pairs, n_pairs, mr);
-            r.q = load_pe6_params(sc, pairs[r.pidx].g_begin + (mr - pairs[r.pidx].item_offset));
+            r.q = load_pe6_params(sc, pairs[r.pidx].g_begin + (mr - pairs[r.pidx].item_offset), mr);
             const float4 u = *reinterpret_cast<const float4*>(dout + dstride * mr);
             r.up[0] = u.x;
             r.up[1] = u.y;

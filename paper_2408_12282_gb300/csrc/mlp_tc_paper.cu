@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
             float x[48];
 #pragma unroll
             for (int k = 0; k < 48; ++k) x[k] = 0.f;
-            if (valid) build_input(net, pairs[pidx], sc, pairs[pidx].g_begin + (m - pairs[pidx].item_offset), x);
+            if (valid)
+                build_input(net, pairs[pidx], sc, pairs[pidx].g_begin + (m - pairs[pidx].item_offset), m, x);
 #pragma unroll
             for (int c = 0; c < 48; c += 8) store8_bf16(act[0], t, c, 48, x + c);
         }

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_project_fwd(sssgs_cfg cfg, const sssgs_
     o[4] = mo;
     // tile / sub-tile culling constants of the render kernels: 1/ca, 1/cc and
     // the padded support level of {p <= ln(o / alpha_min)}
-    o[5] = make_float4(sc.vis[g], 1.f / ca, 1.f / cc, L * 1.001f + 0.01f);
+    o[5] = make_float4(sc.vis_item ? sc.vis_item[m] : sc.vis[g], 1.f / ca, 1.f / cc, L * 1.001f + 0.01f);
 }
 
 // One thread per scene Gaussian; sums the gradient of every pair rendering it.
@@ -134,19 +134,24 @@ __global__ void __launch_bounds__(128) k_project_bwd(sssgs_cfg cfg, const sssgs_
         const sssgs_pair& P = pairs[p];
         if (g < P.g_begin || g >= (int64_t)P.g_begin + P.g_count) continue;
         int64_t m = P.item_offset + (g - P.g_begin);
+        float dvm = 0.f;                 // dL/dv of this item (record and network input)
         if (dx_items) {
             const float* x = dx_items + SSSGS_DX * m;
             dmu[0] += x[0]; dmu[1] += x[1]; dmu[2] += x[2];
             dn[0] += x[3]; dn[1] += x[4]; dn[2] += x[5];
-            dv += x[6];
+            dvm += x[6];
             dq[0] += x[7]; dq[1] += x[8]; dq[2] += x[9]; dq[3] += x[10];
             dls[0] += x[11]; dls[1] += x[12]; dls[2] += x[13];
         }
-        if (!drec) continue;
-        const float* d = drec + (int64_t)SSSGS_REC * m;
-        dn[0] += d[7]; dn[1] += d[8]; dn[2] += d[9];
-        db[0] += d[10]; db[1] += d[11]; db[2] += d[12];
-        dr += d[13]; dm += d[14]; dss += d[15]; dv += d[20];
+        const float* d = drec ? drec + (int64_t)SSSGS_REC * m : nullptr;
+        if (d) {
+            dn[0] += d[7]; dn[1] += d[8]; dn[2] += d[9];
+            db[0] += d[10]; db[1] += d[11]; db[2] += d[12];
+            dr += d[13]; dm += d[14]; dss += d[15]; dvm += d[20];
+        }
+        if (gr.vis_item) gr.vis_item[m] += dvm;      // per-item visibility: its gradient stays per item
+        else dv += dvm;
+        if (!d) continue;
         float dmx = d[0], dmy = d[1], dca = d[2], dcb = d[3], dcc = d[4], dop = d[5], dz = d[6];
         if (dmx == 0.f && dmy == 0.f && dca == 0.f && dcb == 0.f && dcc == 0.f && dop == 0.f && dz == 0.f)
             continue;

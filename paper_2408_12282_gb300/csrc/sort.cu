@@ -302,6 +302,24 @@ static int passes(int bits) {
     return (bits + per - 1) / per;
 }
 
+// Stable sort of n (u32 key, u32 value) pairs by the low `bits` key bits, for
+// other parts of the library (the BVH builder's Morton codes). Workspace:
+// radix_sort_u32_workspace(n) bytes, 256-byte aligned. Returns 0 when kA/vA
+// hold the result, 1 when kB/vB do.
+size_t radix_sort_u32_workspace(int64_t n) {
+    const int64_t nb = std::max<int64_t>((n + RS_TILE - 1) / RS_TILE, 1);
+    const int64_t np = (1024 * nb + SC_CHUNK - 1) / SC_CHUNK;
+    return ((4 * (size_t)1024 * (size_t)nb + 255) & ~(size_t)255) + 4 * (size_t)(np + 1);
+}
+
+int radix_sort_u32(uint32_t* kA, uint32_t* vA, uint32_t* kB, uint32_t* vB, int64_t n, int bits, void* ws,
+                   cudaStream_t st) {
+    const int64_t nb = std::max<int64_t>((n + RS_TILE - 1) / RS_TILE, 1);
+    uint32_t* hist = (uint32_t*)ws;
+    uint32_t* part32 = (uint32_t*)((uint8_t*)ws + ((4 * (size_t)1024 * (size_t)nb + 255) & ~(size_t)255));
+    return radix_sort<uint32_t>(kA, vA, kB, vB, nullptr, n, bits, hist, part32, st);
+}
+
 // ---------------------------------------------------------------- binning kernels
 
 __global__ void k_depth_keys(const sssgs_pair* __restrict__ pairs, int n_pairs, int64_t n_items,

@@ -76,9 +76,13 @@ class Renderer:
     """Owns every buffer of a batch and runs the forward/backward call sequence."""
 
     def __init__(self, scene: dict, mlp: MLPParams, table: PairTable, cfg: B.Cfg, capacity: int | None = None,
-                 fused: bool = True, device="cuda"):
+                 fused: bool = True, device="cuda", vis_sh=None):
+        """vis_sh (N x 16 device tensor, optional): the SH visibility term; v of
+        each (pair, Gaussian) is then evaluated at the pair's light direction
+        (sssgs_vis_sh_fwd) instead of read from scene["vis"]."""
         self.scene = scene
         self.mlp = mlp
+        self.vis_sh = vis_sh
         self.table = table
         self.cfg = cfg
         self.fused = fused
@@ -101,8 +105,15 @@ class Renderer:
         self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
         self.dW = [torch.zeros_like(w) for w in mlp.W]
         self.db = [torch.zeros_like(b) for b in mlp.b]
-        self._scene_s = B.scene_struct(scene)
-        self._grad_s = B.scene_grad_struct(self.grads)
+        self.vis_item = self.dvis_item = self.dvis_sh = None
+        self.vis_traced = None
+        self.loss_vis = None
+        if vis_sh is not None:
+            self.vis_item = torch.zeros(n, **f32)
+            self.dvis_item = torch.zeros(n, **f32)
+            self.dvis_sh = torch.zeros_like(vis_sh)
+        self._scene_s = B.scene_struct(scene, self.vis_item)
+        self._grad_s = B.scene_grad_struct(self.grads, self.dvis_item)
         self._mlp_s = mlp.struct()
         self._mlp_g = B.mlp_grad_struct(self.dW, self.db)
         mws = B.mlp_workspace_bytes(self._mlp_s, n)
@@ -135,6 +146,8 @@ class Renderer:
     # ------------------------------------------------------------------ steps
     def forward_front(self, stream=None):
         t = self.table
+        if self.vis_sh is not None:
+            B.vis_sh_fwd(t.h, t.d, self._scene_s, self.vis_sh, self.vis_item, stream)
         B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, self.status, stream)
         B.project_fwd(self.cfg, t.h, t.d, self._scene_s, self.mlp_out, self.rec, self.rect, stream)
         B.bin_sort(self.cfg, t.h, t.d, self.rec, self.rect, self.capacity, self.vals, self.ranges, self.count,
@@ -157,6 +170,22 @@ class Renderer:
             g.zero_()
         for g in self.dW + self.db:
             g.zero_()
+        if self.vis_sh is not None:
+            self.dvis_item.zero_()
+            self.dvis_sh.zero_()
+
+    def trace_visibility(self, stream=None):
+        """Ray-traced visibility of every (pair, Gaussian) toward the pair's
+        light (BVH over the current geometry) into self.vis_traced: the target
+        of the ray-traced visibility loss."""
+        n = self.scene["mu"].shape[0]
+        if getattr(self, "bvh", None) is None:
+            self.bvh = torch.empty(B.bvh_floats(n), device=self.device, dtype=torch.float32)
+            self.ws_bvh = torch.empty(B.bvh_workspace_bytes(n), device=self.device, dtype=torch.uint8)
+            self.vis_traced = torch.zeros(self.table.n_items, device=self.device, dtype=torch.float32)
+        B.bvh_build(self.cfg, self._scene_s, self.bvh, self.ws_bvh, stream)
+        B.trace_visibility(self.cfg, self.table.h, self.table.d, self._scene_s, self.bvh, self.vis_traced, stream)
+        return self.vis_traced
 
     def _loss_buffers(self):
         if getattr(self, "loss", None) is None:
@@ -166,12 +195,15 @@ class Renderer:
             self.ws_loss = torch.empty(B.image_loss_workspace_bytes(P), device=self.device, dtype=torch.uint8)
 
     def backward(self, dimg=None, target=None, weight=None, l1_scale=1.0, stream=None, loss="l1",
-                 lambda_dssim=0.2, lambda_incident=0.02):
+                 lambda_dssim=0.2, lambda_incident=0.02, lambda_raytrace=0.01):
         """Backward of one step. loss="l1": the upstream gradient is dimg, or
         (dimg None) the fused L1 loss against target. loss="paper": the training
         losses of App. E: image loss (1 - lambda_dssim) L1 + lambda_dssim
         (1 - SSIM) against target plus the incident-light constraint; the
-        per-pair loss values land in self.loss."""
+        per-pair loss values land in self.loss. With the SH visibility term
+        and a traced target (trace_visibility), the ray-traced visibility loss
+        (weight lambda_raytrace) is added and its per-pair values land in
+        self.loss_vis."""
         t = self.table
         self.zero_grads()
         if loss == "paper":
@@ -198,6 +230,15 @@ class Renderer:
         B.mlp_bwd(self._mlp_s, t.h, t.d, self._scene_s, self.drec, self._mlp_g, self.dx_items, self.ws_mlp,
                   self.status, stream)
         B.project_bwd(self.cfg, t.h, t.d, self._scene_s, self.drec, self.dx_items, self._grad_s, stream)
+        if self.vis_sh is not None:
+            if self.vis_traced is not None and lambda_raytrace > 0.0:
+                if self.loss_vis is None:
+                    self.loss_vis = torch.zeros(t.n, device=self.device, dtype=torch.float32)
+                self.loss_vis.zero_()
+                B.vis_loss(t.h, t.d, self.vis_item, self.vis_traced, lambda_raytrace, self.dvis_item, self.loss_vis,
+                           stream)
+            B.vis_sh_bwd(t.h, t.d, self._scene_s, self.vis_sh, self.dvis_item, self.dvis_sh, self.grads["mu"],
+                         stream)
 
     def capture(self, dimg=None, target=None, weight=None, l1_scale=1.0, loss="l1"):
         """Capture one forward + backward step as a CUDA graph and return it.
@@ -283,13 +324,17 @@ def mlp_to_device(spec, precision=None, device="cuda") -> MLPParams:
 
 
 def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=None, device="cuda",
-                          pair_slice=None) -> Renderer:
+                          pair_slice=None, vis_sh=None) -> Renderer:
+    """vis_sh: optional N x 16 numpy array of SH visibility coefficients."""
     cfg = default_cfg(tile or wl.tile)
     scene, offs, counts = concat_scenes(wl.scenes, device)
     pairs = wl.pairs if pair_slice is None else wl.pairs[pair_slice]
     table = PairTable(pairs, cfg, offs, counts, device)
     mlp = mlp_to_device(wl.mlp, precision, device)
-    return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device)
+    sh = None
+    if vis_sh is not None:
+        sh = torch.from_numpy(np.ascontiguousarray(vis_sh, np.float32)).to(device)
+    return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device, vis_sh=sh)
 
 
 class MultiLightRenderer:

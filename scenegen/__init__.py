@@ -422,6 +422,15 @@ def _make_workload(name: str, *, N: int | None = None, res=None,
     raise ValueError(f"unknown workload {name!r}")
 
 
+def vis_sh_coeffs(seed: int, N: int) -> np.ndarray:
+    """Seeded coefficients of a degree-3 SH visibility term per Gaussian
+    (N x 16): a constant band giving v in [0.3, 0.9] plus small higher bands."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.normal(0.0, 0.08, (N, 16))
+    c[:, 0] = rng.uniform(0.3, 0.9, N) * 2.0 * math.sqrt(math.pi)   # the constant band's basis value is 1 / (2 sqrt(pi))
+    return f32(c)
+
+
 def random_dimg(seed: int, n_pixels: int) -> np.ndarray:
     """Seeded upstream image gradient dL/d(image), float32 values, P x 3."""
     rng = np.random.Generator(np.random.PCG64(seed))
