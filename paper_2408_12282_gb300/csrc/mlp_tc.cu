@@ -273,8 +273,8 @@ __global__ void k_mlp_weights_bf16(MlpDev net, TcBwdLayout T, uint8_t* __restric
 // chain are 0 * finite = 0, and bf16(0) = 0. Gaussians hidden behind the
 // surface in a view never contribute to a pixel, so their rows are zero. The
 // backward therefore runs on the list of the other rows, in item order
-// (deterministic: count with a flag byte per item, scan, write), and writes
-// dx_items = 0 for the rest.
+// (deterministic: count with a flag byte per item, scan, write); dx_items is
+// cleared first, so the rest keep dx = 0.
 constexpr int ACT_BLOCK = 1024;
 
 __device__ __forceinline__ bool row_active(const float* __restrict__ dout, int64_t dstride, int64_t m) {
@@ -284,15 +284,10 @@ __device__ __forceinline__ bool row_active(const float* __restrict__ dout, int64
 
 __global__ void __launch_bounds__(ACT_BLOCK) k_active_count(const float* __restrict__ dout, int64_t dstride,
                                                             int64_t n, uint32_t* __restrict__ cnt,
-                                                            uint8_t* __restrict__ flag,
-                                                            float* __restrict__ dx_items) {
+                                                            uint8_t* __restrict__ flag) {
     const int64_t m = (int64_t)blockIdx.x * ACT_BLOCK + threadIdx.x;
     const bool a = m < n && row_active(dout, dstride, m);
     if (m < n) flag[m] = a ? 1 : 0;
-    if (m < n && !a) {
-#pragma unroll
-        for (int k = 0; k < SSSGS_DX; ++k) dx_items[SSSGS_DX * m + k] = 0.f;
-    }
     const int c = __syncthreads_count(a);
     if (threadIdx.x == 0) cnt[blockIdx.x] = (uint32_t)c;
 }
@@ -355,7 +350,10 @@ __global__ void __launch_bounds__(ACT_BLOCK) k_active_write(const uint8_t* __res
 int launch_active_rows(const float* dout, int64_t dstride, int64_t n, uint8_t* flag, uint32_t* cnt, uint32_t* off,
                        uint32_t* nact, uint32_t* active, float* dx_items, cudaStream_t st) {
     const int nb = (int)((n + ACT_BLOCK - 1) / ACT_BLOCK);
-    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(dout, dstride, n, cnt, flag, dx_items);
+    // every row's input gradient starts at zero (one contiguous clear); the
+    // backward then overwrites the active rows
+    cudaMemsetAsync(dx_items, 0, (size_t)n * SSSGS_DX * sizeof(float), st);
+    k_active_count<<<nb, ACT_BLOCK, 0, st>>>(dout, dstride, n, cnt, flag);
     k_active_scan<<<1, 1024, 0, st>>>(cnt, nb, off, nact);
     k_active_write<<<nb, ACT_BLOCK, 0, st>>>(flag, n, off, active);
     return 3;
@@ -732,8 +730,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
                     for (int k = 0; k < 7; ++k)
                         dx_items[SSSGS_DX * m + k] = s_dx[k * TC_ROWS + t] + (k < 3 ? dmu_a[k] : 0.f);
-#pragma unroll
-                    for (int k = 7; k < SSSGS_DX; ++k) dx_items[SSSGS_DX * m + k] = 0.f;   // no q, log_s inputs
+                    // columns 7..13 (no q, log_s inputs) stay as cleared
                 }
                 if (tid == 0) {
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
