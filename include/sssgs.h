@@ -393,6 +393,13 @@ int sssgs_vis_loss(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_p
                    const float* vis_traced, float lambda_raytrace, float* dvis_item, float* d_loss,
                    sssgs_stream stream);
 
+/* Diagnostic of the failure-detection path: one thread waits on an mbarrier
+ * that nothing arrives on, for at most limit_cycles SM clock cycles (1 ..
+ * 4e9), then sets SSSGS_STATUS_TIMEOUT in *d_status (device int32) and
+ * returns, as the tensor-core kernels do when a wait runs out. The context
+ * stays usable. */
+int sssgs_selftest_wait_timeout(int32_t* d_status, int64_t limit_cycles, sssgs_stream stream);
+
 /* Training losses (Appendix E "Losses").
  * Image loss per pair p: L_img = (1 - lambda_dssim) L1 + lambda_dssim (1 - SSIM)
  * over the pair's pixels and channels (L1: mean |img - target|; SSIM: Wang et

@@ -118,6 +118,7 @@ _SIGS = {
     "sssgs_vis_sh_bwd": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp, c_vp, c_vp, c_vp,
                           c_vp], ctypes.c_int),
     "sssgs_vis_loss": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_selftest_wait_timeout": ([c_vp, c_i64, c_vp], ctypes.c_int),
     "sssgs_image_loss_workspace_bytes": ([c_i64], ctypes.c_size_t),
     "sssgs_image_loss": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp,
                           c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
@@ -350,6 +351,11 @@ def project_bwd(cfg: Cfg, pairs, d_pairs, scene: Scene, drec, dx_items, grad: Sc
     _check(load_library().sssgs_project_bwd(ctypes.byref(cfg), pairs, _p(d_pairs), len(pairs), ctypes.byref(scene),
                                             _p(drec), _p(dx_items), ctypes.byref(grad), _stream(stream)),
            "sssgs_project_bwd")
+
+
+def selftest_wait_timeout(d_status, limit_cycles: int, stream=None):
+    _check(load_library().sssgs_selftest_wait_timeout(_p(d_status), int(limit_cycles), _stream(stream)),
+           "sssgs_selftest_wait_timeout")
 
 
 def bvh_floats(n: int) -> int:

@@ -49,10 +49,10 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Wait for the mbarrier phase with parity `parity`. The limit is counted in
-// SM clock cycles (cheap to read): about 2 s at the maximum clock. Returns
-// false when it runs out (the caller records a timeout and stops).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the mbarrier phase with parity `parity` for at most `limit` SM
+// clock cycles (cheap to read). Returns false when the limit runs out (the
+// caller records a timeout and stops).
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, long long limit) {
     long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
         uint32_t ok;
@@ -65,8 +65,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "memory");
         if (ok) return true;
         if (it == 0) t0 = clock64();
-        else if ((it & 15) == 0 && clock64() - t0 > 4000000000ll) return false;
+        else if ((it & 15) == 0 && clock64() - t0 > limit) return false;
     }
+}
+
+// The kernels' wait: about 2 s at the maximum clock.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, 4000000000ll);
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
