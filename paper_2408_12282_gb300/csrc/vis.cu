@@ -18,8 +18,9 @@
 // the library's radix sort, one thread per internal node for the hierarchy,
 // and one thread per leaf walking up with an arrival counter per node to
 // fit the boxes (the second child to arrive writes the union). Traversal: one
-// thread per item, a depth-first walk with an explicit stack (the depth of
-// this hierarchy is at most 62: 30 code bits and 32 index bits).
+// thread per item in Morton order of the origins, a depth-first walk with an
+// explicit stack, nearer child first (the depth of this hierarchy is at most
+// 62: 30 code bits and 32 index bits).
 #include <algorithm>
 #include <cmath>
 
@@ -242,17 +243,24 @@ __global__ void k_bvh_init(int* __restrict__ parent, int* __restrict__ flags, in
     if (i < n) flags[i] = 0;
 }
 
-// One ray per item: transmittance of the segment mu_i -> light.
+// One ray per item: transmittance of the segment mu_i -> light. Thread t
+// takes pair t / N and the Gaussian at Morton position t % N (the BVH's leaf
+// order), so a warp traces from neighbouring origins toward one light and
+// walks the hierarchy coherently; threads whose Gaussian belongs to another
+// scene than the pair's return at once. At an internal node both children's
+// boxes are tested and the nearer hit is visited first (the farther one is
+// pushed), so dense occluders near the origin end the ray early.
 __global__ void __launch_bounds__(128) k_trace(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs, int n_pairs,
-                                               int64_t n_items, const float* __restrict__ mu,
-                                               const float4* __restrict__ nodes, const float4* __restrict__ trec,
-                                               int n, float* __restrict__ vis) {
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= n_items) return;
-    const int p = pair_of_item(pairs, n_pairs, m);
+                                               const float* __restrict__ mu, const float4* __restrict__ nodes,
+                                               const float4* __restrict__ trec, int n, float* __restrict__ vis) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_pairs * n) return;
+    const int p = (int)(t / n), k = (int)(t - (int64_t)p * n);
     const sssgs_pair& P = pairs[p];
-    const int gi = (int)(P.g_begin + (m - P.item_offset));
+    const int gi = f2i(nodes[2 * ((n - 1) + k) + 1].z);
     const int g0 = P.g_begin, g1 = P.g_begin + P.g_count;
+    if (gi < g0 || gi >= g1) return;
+    const int64_t m = P.item_offset + (gi - g0);
     const float ox = mu[3 * gi], oy = mu[3 * gi + 1], oz = mu[3 * gi + 2];
     float dx = P.light[0] - ox, dy = P.light[1] - oy, dz = P.light[2] - oz;
     const float tL = sqrtf(dx * dx + dy * dy + dz * dz);
@@ -260,22 +268,26 @@ __global__ void __launch_bounds__(128) k_trace(sssgs_cfg cfg, const sssgs_pair* 
     dx *= il; dy *= il; dz *= il;
     auto inv = [](float v) { return fabsf(v) > 1e-20f ? 1.f / v : copysignf(1e20f, v); };
     const float ix = inv(dx), iy = inv(dy), iz = inv(dz);
-    const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
-    float T = 1.f;
-    int stack[STACK];
-    int sp = 0, node = 0;
-    while (true) {
-        const float4 A = nodes[2 * node], B = nodes[2 * node + 1];
-        float t0 = 0.f, t1 = tL;                               // box: lo = (A.x, A.y, A.z), hi = (A.w, B.x, B.y)
+    // entry distance of the segment into node nd's box, or -1 when it misses
+    auto enter = [&](int nd) -> float {
+        const float4 A = nodes[2 * nd], B = nodes[2 * nd + 1];     // lo = (A.x, A.y, A.z), hi = (A.w, B.x, B.y)
+        float t0 = 0.f, t1 = tL;
         float u0 = (A.x - ox) * ix, u1 = (A.w - ox) * ix;
         t0 = fmaxf(t0, fminf(u0, u1)); t1 = fminf(t1, fmaxf(u0, u1));
         u0 = (A.y - oy) * iy; u1 = (B.x - oy) * iy;
         t0 = fmaxf(t0, fminf(u0, u1)); t1 = fminf(t1, fmaxf(u0, u1));
         u0 = (A.z - oz) * iz; u1 = (B.y - oz) * iz;
         t0 = fmaxf(t0, fminf(u0, u1)); t1 = fminf(t1, fmaxf(u0, u1));
-        const bool hit = t0 <= t1;
-        if (hit && node >= n - 1) {                            // leaf
-            const int j = f2i(B.z);
+        return t0 <= t1 ? t0 : -1.f;
+    };
+    const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
+    float T = 1.f;
+    int stack[STACK];
+    int sp = 0, node = 0;
+    if (enter(0) < 0.f) node = -1;
+    while (node >= 0) {
+        if (node >= n - 1) {                                   // leaf (its box was hit)
+            const int j = f2i(nodes[2 * node + 1].z);
             if (j != gi && j >= g0 && j < g1) {
                 const int li = node - (n - 1);
                 const float4 r0 = trec[4 * li], r1 = trec[4 * li + 1], r2 = trec[4 * li + 2], r3 = trec[4 * li + 3];
@@ -287,21 +299,31 @@ __global__ void __launch_bounds__(128) k_trace(sssgs_cfg cfg, const sssgs_pair* 
                 const float qy = r1.w * dx + r2.x * dy + r2.y * dz;
                 const float qz = r2.z * dx + r2.w * dy + r3.x * dz;
                 const float dd = qx * qx + qy * qy + qz * qz;
-                const float t = -(px * qx + py * qy + pz * qz) / dd;
-                const float cx = px + t * qx, cy = py + t * qy, cz = pz + t * qz;
+                const float tt = -(px * qx + py * qy + pz * qz) / dd;
+                const float cx = px + tt * qx, cy = py + tt * qy, cz = pz + tt * qz;
                 const float alpha = fminf(a_max, r0.w * expf(-0.5f * (cx * cx + cy * cy + cz * cz)));
-                if (t > 0.f && t < tL && alpha >= a_min) {
+                if (tt > 0.f && tt < tL && alpha >= a_min) {
                     T *= 1.f - alpha;
                     if (T < VIS_T_STOP) break;
                 }
             }
-        } else if (hit) {                                      // internal: visit the left child, keep the right
-            if (sp < STACK) stack[sp++] = f2i(B.w);
-            node = f2i(B.z);
+            node = sp > 0 ? stack[--sp] : -1;
             continue;
         }
-        if (sp == 0) break;
-        node = stack[--sp];
+        const float4 B = nodes[2 * node + 1];
+        const int ca = f2i(B.z), cb = f2i(B.w);
+        const float ta = enter(ca), tb = enter(cb);
+        if (ta >= 0.f && tb >= 0.f) {
+            const bool a_first = ta <= tb;
+            if (sp < STACK) stack[sp++] = a_first ? cb : ca;
+            node = a_first ? ca : cb;
+        } else if (ta >= 0.f) {
+            node = ca;
+        } else if (tb >= 0.f) {
+            node = cb;
+        } else {
+            node = sp > 0 ? stack[--sp] : -1;
+        }
     }
     vis[m] = T;
 }
@@ -507,8 +529,9 @@ extern "C" int sssgs_trace_visibility(const sssgs_cfg* cfg, const sssgs_pair* h_
     if (n_items == 0 || n <= 0) return SSSGS_OK;
     const float* nodes = bvh;
     const float* trec = bvh + (int64_t)NODE_F * (2 * n - 1);
-    k_trace<<<(unsigned)((n_items + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
-        *cfg, d_pairs, n_pairs, n_items, scene->mu, reinterpret_cast<const float4*>(nodes),
+    const int64_t threads = (int64_t)n_pairs * n;
+    k_trace<<<(unsigned)((threads + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        *cfg, d_pairs, n_pairs, scene->mu, reinterpret_cast<const float4*>(nodes),
         reinterpret_cast<const float4*>(trec), (int)n, vis_traced);
     sssgs::note_launches(1);
     return launch_status();
