@@ -78,3 +78,56 @@ def test_full_64_pair_batch_graph_replay_sampled():
         assert torch.equal(one.img, r.img[offs[p]:offs[p + 1]])
         del one
         torch.cuda.empty_cache()
+
+
+def test_full_light_stage_batch_graph_replay_sampled():
+    """The 8 views x 8 lights light-stage batch (300K, 800x800) through the
+    many-light kernels, replayed from a captured graph with the fused L1 loss
+    as in bench.py: sampled pixels of two (view, light) pairs against the
+    oracle rendering that pair on its own."""
+    import oracle as O2
+    wl = sg.make_workload("c6")
+    r = PL.multilight_renderer_for_workload(wl, precision=B.BF16)
+    r.fit_capacity()
+    target = torch.zeros(r.pairs.n_pixels, 3, device="cuda")
+    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * r.pairs.n_pixels))
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    r.check_status()
+    img = r.img.double().cpu().numpy()
+    assert np.isfinite(r.grads["mu"].cpu().numpy()).all()
+    rng = np.random.default_rng(6)
+    offs = [0]
+    for p in wl.pairs:
+        offs.append(offs[-1] + p.W * p.H)
+    for p in (3, 58):                  # view 0 light 3, view 7 light 2
+        pair = wl.pairs[p]
+        pix = O2.all_pixels(pair.W, pair.H)
+        sel = rng.choice(len(pix), 1500, replace=False)
+        res = O2.render_pair(wl.scenes[0], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=True)
+        fl = flagged(res["margin"])
+        got = img[offs[p] + sel]
+        e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
+        print(f"\nlight-stage pair {p}: {fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
+        assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
+
+
+def test_full_batch_visibility_trace_sampled():
+    """Ray-traced visibility of the 64-pair 300K batch: sampled items of two
+    pairs against the oracle's brute force over all 300K Gaussians."""
+    import oracle.visibility as V
+    wl = sg.make_workload("c4")
+    sc = wl.scenes[0]
+    r = PL.renderer_for_workload(wl, precision=B.BF16, vis_sh=sg.vis_sh_coeffs(1, sc.N))
+    v = r.trace_visibility()
+    torch.cuda.synchronize()
+    got = v.double().cpu().numpy()
+    rng = np.random.default_rng(8)
+    for p in (5, 50):
+        items = rng.choice(sc.N, 60, replace=False)
+        ref, margin = V.trace_visibility(sc, wl.pairs[p].light, items=items)
+        ok = (margin > 2e-5) | (ref < 1e-4)
+        e = np.abs(got[p * sc.N + items] - ref)[ok]
+        print(f"\ntrace pair {p}: {int((~ok).sum())} excluded, max |gpu - oracle| {e.max():.2e}")
+        assert (~ok).sum() <= 3 and e.max() <= 1e-4
