@@ -328,8 +328,43 @@ def all_pixels(W, H):
     return np.stack([ii.ravel(), jj.ravel()], axis=1).astype(np.int32)
 
 
+def gaussian_colors(normal, base, rough, metal, sss, Ls, Lin, mu, cam_center, light, grad_out=None):
+    """Per-Gaussian shading (the paper's "w/o Deferred" ablation, App. "Ablation"):
+    each Gaussian's colour from its own attributes at its own mean x = mu,
+    with the BRDF of Eq. 4 (GGX D, Schlick F, separable Smith V) and the blend
+    of Eq. 7:  c = sss L_SSS + (1 - sss) (f_s + f_d) L_in max(n . w_i, 0),
+    w_o = unit(camera - x), w_i = unit(light - x), n normalised. Plain PyTorch
+    FP64; with grad_out (N x 3) also returns the gradients (autograd) of
+    sum(grad_out * c) w.r.t. (normal, base, rough, metal, sss, Ls, Lin, mu)."""
+    import torch
+    t = lambda a: torch.tensor(np.asarray(a, np.float64), dtype=torch.float64, requires_grad=grad_out is not None)
+    n, b, r, m, s, ls, li, x = (t(normal), t(base), t(rough), t(metal), t(sss), t(Ls), t(Lin), t(mu))
+    C = torch.tensor(np.asarray(cam_center, np.float64), dtype=torch.float64)
+    Lp = torch.tensor(np.asarray(light, np.float64), dtype=torch.float64)
+    unit = lambda v, eps=0.0: v / torch.clamp(torch.linalg.norm(v, dim=1, keepdim=True), min=eps)
+    wo, wi = unit(C[None, :] - x), unit(Lp[None, :] - x)
+    nh = unit(n, 1e-12)
+    h = unit(wo + wi, 1e-12)
+    dot = lambda a, c: (a * c).sum(dim=1)
+    no, ni = torch.clamp(dot(nh, wo), min=0), torch.clamp(dot(nh, wi), min=0)
+    nhc, vh = torch.clamp(dot(nh, h), min=0), torch.clamp(dot(wo, h), min=0)
+    a2 = (r * r) ** 2
+    den = nhc * nhc * (a2 - 1) + 1
+    D = a2 / (math.pi * den * den)
+    V = 1.0 / ((no + torch.sqrt(a2 + (1 - a2) * no * no)) * (ni + torch.sqrt(a2 + (1 - a2) * ni * ni)))
+    F0 = 0.04 * (1 - m[:, None]) + b * m[:, None]
+    Fr = F0 + (1 - F0) * ((1 - vh) ** 5)[:, None]
+    fs = D[:, None] * Fr * V[:, None]
+    fd = (1 - m[:, None]) * b / math.pi
+    c = s[:, None] * ls + (1 - s[:, None]) * (fs + fd) * (li * ni)[:, None]
+    if grad_out is None:
+        return c.detach().numpy()
+    (c * torch.tensor(np.asarray(grad_out, np.float64), dtype=torch.float64)).sum().backward()
+    return c.detach().numpy(), tuple(v.grad.numpy() for v in (n, b, r, m, s, ls, li, x))
+
+
 def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=None,
-                bf16=False, mlp_out=None, dlin_extra=None, dvis_extra=None):
+                bf16=False, mlp_out=None, dlin_extra=None, dvis_extra=None, per_gaussian_shading=False):
     """Forward (and, if dimg is given, backward) of one view/light pair.
 
     pixels: (P x 2) int array of (i, j) to evaluate; default all, row-major.
@@ -339,7 +374,9 @@ def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=No
     and of the MLP weights.
     dlin_extra, dvis_extra (N): gradients of further loss terms on the
     predicted incident light L_in and the visibility v of each Gaussian (the
-    incident-light constraint of App. E), added before the network backward."""
+    incident-light constraint of App. E), added before the network backward.
+    per_gaussian_shading: shade each Gaussian (gaussian_colors) and composite
+    the colours instead of the deferred per-pixel shading."""
     L = lib()
     N = scene.N
     C = pair.center
@@ -352,6 +389,11 @@ def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=No
     feat = np.concatenate([proj[:, 6:7], scene.normal, scene.base, scene.rough[:, None],
                            scene.metal[:, None], scene.sss[:, None], Ls, Lin[:, None],
                            scene.vis[:, None]], axis=1)
+    if per_gaussian_shading:
+        colors = gaussian_colors(scene.normal, scene.base, scene.rough, scene.metal, scene.sss, Ls, Lin,
+                                 scene.mu, C, pair.light)
+        feat = np.concatenate([colors, np.zeros((N, 12))], axis=1)
+        mode = mode | 2
     if pixels is None:
         pixels = all_pixels(pair.W, pair.H)
     P = pixels.shape[0]
@@ -376,6 +418,13 @@ def render_pair(scene, pair, spec, cfg=DEFAULT_CFG, mode=1, pixels=None, dimg=No
     if dimg is None:
         return out
     g = {k: np.zeros_like(v) for k, v in scene.arrays().items()}
+    if per_gaussian_shading:          # the composited colours' gradient through each Gaussian's shading
+        _, gs = gaussian_colors(scene.normal, scene.base, scene.rough, scene.metal, scene.sss, Ls, Lin,
+                                scene.mu, C, pair.light, grad_out=dfeat[:, 0:3])
+        dfeat = np.zeros_like(dfeat)  # feature layout of the deferred path (depth unused here)
+        dfeat[:, 1:4], dfeat[:, 4:7], dfeat[:, 7], dfeat[:, 8], dfeat[:, 9] = gs[0], gs[1], gs[2], gs[3], gs[4]
+        dfeat[:, 10:13], dfeat[:, 13] = gs[5], gs[6]
+        g["mu"] += gs[7]
     L.orc_project_bwd(N, _d(scene.mu)[1], _d(scene.log_s)[1], _d(scene.quat)[1],
                       _d(scene.logit_o)[1], keep[4][1], keep[0][1], keep[1][1],
                       dgeom.ctypes.data_as(_dp), np.ascontiguousarray(dfeat[:, 0]).ctypes.data_as(_dp),

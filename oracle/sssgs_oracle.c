@@ -327,9 +327,12 @@ static int cmp_depth(const void* a, const void* b) {
 }
 
 /*
- * Render one view/light pair. mode 0: brute force (every valid Gaussian is
- * tested at every pixel, in depth order). mode 1: tiled (each pixel walks the
- * depth-ordered list of Gaussians whose pixel rectangle touches its tile).
+ * Render one view/light pair. mode bit 0 clear: brute force (every valid
+ * Gaussian is tested at every pixel, in depth order); set: tiled (each pixel
+ * walks the depth-ordered list of Gaussians whose pixel rectangle touches its
+ * tile). mode bit 1 set: per-Gaussian shading (the paper's "w/o Deferred"
+ * ablation): feat[0..2] hold each Gaussian's own shaded colour and the image
+ * is their composite (black background), img = F[0..2], dF = (dimg, 0, ...).
  * pix[npix*2] lists the pixels (i, j) to evaluate. Outputs per listed pixel:
  * gbuf[16], img[3], ncontrib, margin[3] (relative distance of the nearest
  * alpha decision and transmittance-stop decision to its threshold, and the
@@ -343,6 +346,7 @@ int orc_render(int N, const double* proj, const int* rect, const uint32_t* dkey,
                double* gbuf, double* img, int* ncontrib, double* margin,
                const double* dimg, double* dgeom, double* dfeat) {
     int tile = (int)cfg[0];
+    const int tiled = mode & 1, per_gaussian = mode & 2;
     double a_min = cfg[4], a_max = cfg[5], T_min = cfg[6], A_eps = cfg[7];
     int W = (int)cam[16], H = (int)cam[17];
     int tiles_x = (W + tile - 1) / tile, tiles_y = (H + tile - 1) / tile;
@@ -351,7 +355,7 @@ int orc_render(int N, const double* proj, const int* rect, const uint32_t* dkey,
     int nv = 0;
     for (int g = 0; g < N; ++g)
         if (rect[4 * g] <= rect[4 * g + 1]) order[nv++] = g;
-        else if (mode == 0 && proj[16 * (size_t)g + 7] > 0 && proj[16 * (size_t)g + 12] >= cfg[3]) {
+        else if (!tiled && proj[16 * (size_t)g + 7] > 0 && proj[16 * (size_t)g + 12] >= cfg[3]) {
             /* brute force ignores rectangles; an off-screen Gaussian still has
              * no support at any pixel, so keep only ones that survive culling */
             double a = proj[16 * (size_t)g + 13], b = proj[16 * (size_t)g + 14], c = proj[16 * (size_t)g + 15];
@@ -361,7 +365,7 @@ int orc_render(int N, const double* proj, const int* rect, const uint32_t* dkey,
     qsort(order, (size_t)nv, sizeof(int), cmp_depth);
     /* per-tile lists for tiled mode */
     int* tstart = NULL; int* tlist = NULL;
-    if (mode == 1) {
+    if (tiled) {
         int nt = tiles_x * tiles_y;
         tstart = (int*)calloc((size_t)nt + 1, sizeof(int));
         for (int k = 0; k < nv; ++k) {
@@ -385,7 +389,7 @@ int orc_render(int N, const double* proj, const int* rect, const uint32_t* dkey,
         int pi = pix[2 * q], pj = pix[2 * q + 1];
         double px = pi + 0.5, py = pj + 0.5;
         const int* list; int nl;
-        if (mode == 1) {
+        if (tiled) {
             int t = (pj / tile) * tiles_x + pi / tile;
             list = tlist + tstart[t]; nl = tstart[t + 1] - tstart[t];
         } else { list = order; nl = nv; }
@@ -421,8 +425,15 @@ int orc_render(int N, const double* proj, const int* rect, const uint32_t* dkey,
         ncontrib[q] = nc;
         margin[3 * q] = ma; margin[3 * q + 1] = mt; margin[3 * q + 2] = ncl;
         double dF[NF], dT;
-        shade_pixel(F, T, nc > 0, px, py, cam, light, A_eps, img + 3 * (size_t)q,
-                    dimg ? dimg + 3 * (size_t)q : NULL, dF, &dT);
+        if (per_gaussian) {
+            for (int c = 0; c < 3; ++c) img[3 * (size_t)q + c] = F[c];
+            memset(dF, 0, sizeof(dF));
+            dT = 0;
+            if (dimg) for (int c = 0; c < 3; ++c) dF[c] = dimg[3 * (size_t)q + c];
+        } else {
+            shade_pixel(F, T, nc > 0, px, py, cam, light, A_eps, img + 3 * (size_t)q,
+                        dimg ? dimg + 3 * (size_t)q : NULL, dF, &dT);
+        }
         if (!dimg || nc == 0) continue;
         /* dLoss/dalpha_i = sum_k dF_k (T_i f_ik - S_ik / (1 - alpha_i))
          *                  - dT * T_final / (1 - alpha_i),
