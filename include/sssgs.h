@@ -76,7 +76,8 @@ enum {
  * 16-18 L_SSS, 19 L_in, 20 vis), 21 1/ca, 22 1/cc, 23 1.001 ln(o/alpha_min)
  * + 0.01 (culling constants the render kernels read; sssgs_project_fwd
  * writes them). The gradient record has the layout of fields 0..20
- * (d/dmx ... d/dvis); its fields 21..23 stay zero. */
+ * (d/dmx ... d/dvis); its fields 21..23 hold dL/dmu of the per-Gaussian
+ * shading (sssgs_shade_gaussians_bwd) and are zero otherwise. */
 
 /* Render conventions. Defaults (sssgs_cfg_default): tile 16, dilation 0.3 px^2,
  * det_eps 1e-6 px^4, z_near 0.2, alpha_min 1/255, alpha_max 0.99, T_min 1e-4,
@@ -399,6 +400,27 @@ int sssgs_vis_loss(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_p
  * returns, as the tensor-core kernels do when a wait runs out. The context
  * stays usable. */
 int sssgs_selftest_wait_timeout(int32_t* d_status, int64_t limit_cycles, sssgs_stream stream);
+
+/* Per-Gaussian shading: the paper's "w/o Deferred" ablation (appendix
+ * "Ablation"). Each Gaussian is shaded at its own mean with its own attributes
+ * (Eq. 4 BRDF, Eq. 7 blend) and the colours are composited (Eq. 3), black
+ * background. Forward: sssgs_project_fwd -> sssgs_bin_sort (on rec) ->
+ * sssgs_shade_gaussians_fwd (rec -> rec_colors: a copy of the records whose
+ * feature fields carry the colour (6..8) and zeros (9..20)) ->
+ * sssgs_composite_fwd on rec_colors -> sssgs_colors_to_image (img = G-buffer
+ * channels 0..2). Backward: sssgs_colors_to_image_bwd (dimg -> dgbuf) ->
+ * sssgs_composite_bwd on rec_colors -> sssgs_shade_gaussians_bwd (replaces
+ * drec fields 6..8, dL/dcolour, by the gradients of the shaded attributes in
+ * fields 7..19 and of the mean in 21..23) -> sssgs_mlp_bwd ->
+ * sssgs_project_bwd. */
+int sssgs_shade_gaussians_fwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                              const sssgs_scene* scene, const float* rec, float* rec_colors, sssgs_stream stream);
+int sssgs_shade_gaussians_bwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
+                              const sssgs_scene* scene, const float* rec, float* drec, sssgs_stream stream);
+int sssgs_colors_to_image(const sssgs_pair* h_pairs, int n_pairs, const float* gbuf, float* img,
+                          sssgs_stream stream);
+int sssgs_colors_to_image_bwd(const sssgs_pair* h_pairs, int n_pairs, const float* dimg, float* dgbuf,
+                              sssgs_stream stream);
 
 /* Training losses (Appendix E "Losses").
  * Image loss per pair p: L_img = (1 - lambda_dssim) L1 + lambda_dssim (1 - SSIM)

@@ -119,6 +119,12 @@ _SIGS = {
                           c_vp], ctypes.c_int),
     "sssgs_vis_loss": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_selftest_wait_timeout": ([c_vp, c_i64, c_vp], ctypes.c_int),
+    "sssgs_shade_gaussians_fwd": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp, c_vp,
+                                   c_vp], ctypes.c_int),
+    "sssgs_shade_gaussians_bwd": ([ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene), c_vp, c_vp,
+                                   c_vp], ctypes.c_int),
+    "sssgs_colors_to_image": ([ctypes.POINTER(Pair), ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_colors_to_image_bwd": ([ctypes.POINTER(Pair), ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_image_loss_workspace_bytes": ([c_i64], ctypes.c_size_t),
     "sssgs_image_loss": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_f32, c_vp,
                           c_vp, c_vp, ctypes.c_size_t, c_vp], ctypes.c_int),
@@ -356,6 +362,26 @@ def project_bwd(cfg: Cfg, pairs, d_pairs, scene: Scene, drec, dx_items, grad: Sc
 def selftest_wait_timeout(d_status, limit_cycles: int, stream=None):
     _check(load_library().sssgs_selftest_wait_timeout(_p(d_status), int(limit_cycles), _stream(stream)),
            "sssgs_selftest_wait_timeout")
+
+
+def shade_gaussians_fwd(pairs, d_pairs, scene: Scene, rec, rec_colors, stream=None):
+    _check(load_library().sssgs_shade_gaussians_fwd(pairs, _p(d_pairs), len(pairs), ctypes.byref(scene), _p(rec),
+                                                    _p(rec_colors), _stream(stream)), "sssgs_shade_gaussians_fwd")
+
+
+def shade_gaussians_bwd(pairs, d_pairs, scene: Scene, rec, drec, stream=None):
+    _check(load_library().sssgs_shade_gaussians_bwd(pairs, _p(d_pairs), len(pairs), ctypes.byref(scene), _p(rec),
+                                                    _p(drec), _stream(stream)), "sssgs_shade_gaussians_bwd")
+
+
+def colors_to_image(pairs, gbuf, img, stream=None):
+    _check(load_library().sssgs_colors_to_image(pairs, len(pairs), _p(gbuf), _p(img), _stream(stream)),
+           "sssgs_colors_to_image")
+
+
+def colors_to_image_bwd(pairs, dimg, dgbuf, stream=None):
+    _check(load_library().sssgs_colors_to_image_bwd(pairs, len(pairs), _p(dimg), _p(dgbuf), _stream(stream)),
+           "sssgs_colors_to_image_bwd")
 
 
 def bvh_floats(n: int) -> int:

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(sssgs_cfg cfg, const sssgs_
         if (gr.vis_item) gr.vis_item[m] += dvm;      // per-item visibility: its gradient stays per item
         else dv += dvm;
         if (!d) continue;
+        dmu[0] += d[21]; dmu[1] += d[22]; dmu[2] += d[23];   // per-Gaussian shading at the mean (zero otherwise)
         float dmx = d[0], dmy = d[1], dca = d[2], dcb = d[3], dcc = d[4], dop = d[5], dz = d[6];
         if (dmx == 0.f && dmy == 0.f && dca == 0.f && dcb == 0.f && dcc == 0.f && dop == 0.f && dz == 0.f)
             continue;

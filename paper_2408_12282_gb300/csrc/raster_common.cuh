@@ -8,38 +8,17 @@ namespace sssgs {
 
 // ---------------------------------------------------------------- shading
 
-// Deferred shading of one pixel (Eq. 4 BRDF, Eq. 7 blend) under the point
-// light at Lp. F: composited features, T: final transmittance, (u, v): pixel
-// centre, P: the camera. With BWD it also back-propagates g3 = dLoss/d(out)
-// to dF (15) and dT.
+// Shading of one surface point (Eq. 4 BRDF: GGX D, Schlick F, separable
+// Smith V; Eq. 7 blend): Lc = sss L_SSS + (1 - sss) (f_s + f_d) L_in
+// max(n . w_i, 0) at the point x seen from the camera centre C under the point
+// light Lp, with the (unnormalised) normal nbar. With BWD, back-propagates
+// gL = dLoss/dLc into dg (feature layout of the G-buffer: 1..3 n, 4..6 base,
+// 7 rough, 8 metal, 9 sss, 10..12 L_SSS, 13 L_in; other entries untouched)
+// and dx = dLoss/dx.
 template <bool BWD>
-__device__ __forceinline__ void shade_px_at(const float* F, float T, float u, float v, const sssgs_pair& P,
-                                            float3 Lp, float A_eps, float* out, const float* g3, float* dF,
-                                            float* dT) {
-    out[0] = out[1] = out[2] = 0.f;
-    if (BWD) {
-#pragma unroll
-        for (int k = 0; k < SSSGS_NF; ++k) dF[k] = 0.f;
-        *dT = 0.f;
-    }
-    if (!(T < 1.f)) return;                      // no contribution: black, no gradient
-    const float A = 1.f - T;
-    const float Ad = fmaxf(A, A_eps);
-    const float iA = 1.f / Ad;
-    float g[SSSGS_NF];
-#pragma unroll
-    for (int k = 0; k < SSSGS_NF; ++k) g[k] = F[k] * iA;
-    const float dbar = g[0], rb = g[7], mb = g[8], sb = g[9], Li = g[13];
-    const float3 nbar = make_float3(g[1], g[2], g[3]);
-    const float bb[3] = {g[4], g[5], g[6]};
-    const float Ls[3] = {g[10], g[11], g[12]};
-    // back-projected surface point x = R^T (dbar * ray - t)
-    const float3 ray = make_float3((u - P.cx) / P.fx, (v - P.cy) / P.fy, 1.f);
-    const float3 Xc = make_float3(dbar * ray.x - P.t[0], dbar * ray.y - P.t[1], dbar * ray.z - P.t[2]);
-    const float3 x = make_float3(P.R[0] * Xc.x + P.R[3] * Xc.y + P.R[6] * Xc.z,
-                                 P.R[1] * Xc.x + P.R[4] * Xc.y + P.R[7] * Xc.z,
-                                 P.R[2] * Xc.x + P.R[5] * Xc.y + P.R[8] * Xc.z);
-    const float3 C = cam_center(P);
+__device__ __forceinline__ void shade_point(float3 nbar, const float* bb, float rb, float mb, float sb,
+                                            const float* Ls, float Li, float3 x, float3 C, float3 Lp, float* Lc,
+                                            const float* gL, float* dg, float3* dxo) {
     const float3 Vo = C - x;
     const float3 Vi = make_float3(Lp.x - x.x, Lp.y - x.y, Lp.z - x.z);
     const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
@@ -58,7 +37,7 @@ __device__ __forceinline__ void shade_px_at(const float* F, float T, float u, fl
     const float Lo = no + so, Lm = ni + si;
     const float Vis = 1.f / (Lo * Lm);
     const float om = 1.f - vh, om2 = om * om, w5 = om2 * om2 * om;
-    float F0[3], Fr[3], fs[3], fd[3], Lc[3];
+    float F0[3], Fr[3], fs[3], fd[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         F0[c] = 0.04f * (1.f - mb) + bb[c] * mb;
@@ -66,23 +45,18 @@ __device__ __forceinline__ void shade_px_at(const float* F, float T, float u, fl
         fs[c] = D * Fr[c] * Vis;
         fd[c] = (1.f - mb) * bb[c] * (1.f / kPi);
         Lc[c] = sb * Ls[c] + (1.f - sb) * (fs[c] + fd[c]) * Li * ni;
-        out[c] = A * Lc[c];
     }
     if constexpr (BWD) {
-        float dg[SSSGS_NF];
-    #pragma unroll
-        for (int k = 0; k < SSSGS_NF; ++k) dg[k] = 0.f;
-        float dA = 0.f, dni = 0.f, dD = 0.f, dVis = 0.f, dw5 = 0.f;
-    #pragma unroll
+        float dni = 0.f, dD = 0.f, dVis = 0.f, dw5 = 0.f;
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float gL = g3[c] * A;
-            dA += g3[c] * Lc[c];
+            const float g = gL[c];
             const float fsd = fs[c] + fd[c];
-            dg[9] += gL * (Ls[c] - fsd * Li * ni);
-            dg[10 + c] += gL * sb;
-            dg[13] += gL * (1.f - sb) * fsd * ni;
-            dni += gL * (1.f - sb) * fsd * Li;
-            const float cm = gL * (1.f - sb) * Li * ni;
+            dg[9] += g * (Ls[c] - fsd * Li * ni);
+            dg[10 + c] += g * sb;
+            dg[13] += g * (1.f - sb) * fsd * ni;
+            dni += g * (1.f - sb) * fsd * Li;
+            const float cm = g * (1.f - sb) * Li * ni;
             dg[8] -= cm * bb[c] * (1.f / kPi);
             dg[4 + c] += cm * (1.f - mb) * (1.f / kPi);
             dD += cm * Fr[c] * Vis;
@@ -114,15 +88,70 @@ __device__ __forceinline__ void shade_px_at(const float* F, float T, float u, fl
         dwi = dwi + dHv;
         const float3 dVo = (1.f / lo) * (dwo - dot3(wo, dwo) * wo);
         const float3 dVi = (1.f / li) * (dwi - dot3(wi, dwi) * wi);
-        const float3 dx = make_float3(-dVo.x - dVi.x, -dVo.y - dVi.y, -dVo.z - dVi.z);
+        *dxo = make_float3(-dVo.x - dVi.x, -dVo.y - dVi.y, -dVo.z - dVi.z);
         const float3 dnb = (1.f / nn) * (dn - dot3(nh, dn) * nh);
         dg[1] += dnb.x; dg[2] += dnb.y; dg[3] += dnb.z;
+    }
+}
+
+// Deferred shading of one pixel (Eq. 4 BRDF, Eq. 7 blend) under the point
+// light at Lp. F: composited features, T: final transmittance, (u, v): pixel
+// centre, P: the camera. The normalised features shade the surface point
+// back-projected from the pixel at the composited depth; out = A Lc. With BWD
+// it also back-propagates g3 = dLoss/d(out) to dF (15) and dT.
+template <bool BWD>
+__device__ __forceinline__ void shade_px_at(const float* F, float T, float u, float v, const sssgs_pair& P,
+                                            float3 Lp, float A_eps, float* out, const float* g3, float* dF,
+                                            float* dT) {
+    out[0] = out[1] = out[2] = 0.f;
+    if (BWD) {
+#pragma unroll
+        for (int k = 0; k < SSSGS_NF; ++k) dF[k] = 0.f;
+        *dT = 0.f;
+    }
+    if (!(T < 1.f)) return;                      // no contribution: black, no gradient
+    const float A = 1.f - T;
+    const float Ad = fmaxf(A, A_eps);
+    const float iA = 1.f / Ad;
+    float g[SSSGS_NF];
+#pragma unroll
+    for (int k = 0; k < SSSGS_NF; ++k) g[k] = F[k] * iA;
+    const float dbar = g[0], rb = g[7], mb = g[8], sb = g[9], Li = g[13];
+    const float3 nbar = make_float3(g[1], g[2], g[3]);
+    const float bb[3] = {g[4], g[5], g[6]};
+    const float Ls[3] = {g[10], g[11], g[12]};
+    // back-projected surface point x = R^T (dbar * ray - t)
+    const float3 ray = make_float3((u - P.cx) / P.fx, (v - P.cy) / P.fy, 1.f);
+    const float3 Xc = make_float3(dbar * ray.x - P.t[0], dbar * ray.y - P.t[1], dbar * ray.z - P.t[2]);
+    const float3 x = make_float3(P.R[0] * Xc.x + P.R[3] * Xc.y + P.R[6] * Xc.z,
+                                 P.R[1] * Xc.x + P.R[4] * Xc.y + P.R[7] * Xc.z,
+                                 P.R[2] * Xc.x + P.R[5] * Xc.y + P.R[8] * Xc.z);
+    float Lc[3];
+    if constexpr (!BWD) {
+        shade_point<false>(nbar, bb, rb, mb, sb, Ls, Li, x, cam_center(P), Lp, Lc, nullptr, nullptr, nullptr);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c] = A * Lc[c];
+    } else {
+        float gL[3], dg[SSSGS_NF];
+#pragma unroll
+        for (int k = 0; k < SSSGS_NF; ++k) dg[k] = 0.f;
+        // out = A Lc: dLoss/dLc = A g3, dLoss/dA = g3 . Lc
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gL[c] = g3[c] * A;
+        float3 dx;
+        shade_point<true>(nbar, bb, rb, mb, sb, Ls, Li, x, cam_center(P), Lp, Lc, gL, dg, &dx);
+        float dA = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            out[c] = A * Lc[c];
+            dA += g3[c] * Lc[c];
+        }
         const float3 dXc = make_float3(P.R[0] * dx.x + P.R[1] * dx.y + P.R[2] * dx.z,
                                        P.R[3] * dx.x + P.R[4] * dx.y + P.R[5] * dx.z,
                                        P.R[6] * dx.x + P.R[7] * dx.y + P.R[8] * dx.z);
         dg[0] += dot3(dXc, ray);
         float dAd = 0.f;
-    #pragma unroll
+#pragma unroll
         for (int k = 0; k < SSSGS_NF; ++k) {
             dF[k] = dg[k] * iA;
             dAd -= dg[k] * g[k] * iA;

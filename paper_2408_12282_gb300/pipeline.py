@@ -76,10 +76,19 @@ class Renderer:
     """Owns every buffer of a batch and runs the forward/backward call sequence."""
 
     def __init__(self, scene: dict, mlp: MLPParams, table: PairTable, cfg: B.Cfg, capacity: int | None = None,
-                 fused: bool = True, device="cuda", vis_sh=None):
+                 fused: bool = True, device="cuda", vis_sh=None, shading: str = "deferred"):
         """vis_sh (N x 16 device tensor, optional): the SH visibility term; v of
         each (pair, Gaussian) is then evaluated at the pair's light direction
-        (sssgs_vis_sh_fwd) instead of read from scene["vis"]."""
+        (sssgs_vis_sh_fwd) instead of read from scene["vis"].
+        shading: "deferred" (Eq. 4 per pixel on the composited G-buffer, the
+        paper's method) or "gaussian" (each Gaussian shaded at its mean and the
+        colours composited: the paper's "w/o Deferred" ablation; unfused
+        kernels, upstream gradient dimg or loss="paper")."""
+        if shading not in ("deferred", "gaussian"):
+            raise ValueError(f"unknown shading {shading!r}")
+        self.shading = shading
+        if shading == "gaussian":
+            fused = False
         self.scene = scene
         self.mlp = mlp
         self.vis_sh = vis_sh
@@ -100,6 +109,7 @@ class Renderer:
         self.last = torch.zeros(P, **i32)
         self.img = torch.zeros(P, 3, **f32)
         self.dgbuf = None if fused else torch.zeros(P, B.GBUF, **f32)
+        self.rec_colors = torch.zeros(n, B.REC, **f32) if shading == "gaussian" else None
         self.drec = torch.zeros(n, B.REC, **f32)
         self.dx_items = torch.zeros(n, B.DX, **f32)
         self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
@@ -156,7 +166,12 @@ class Renderer:
     def forward(self, stream=None):
         self.forward_front(stream)
         t = self.table
-        if self.fused:
+        if self.shading == "gaussian":
+            B.shade_gaussians_fwd(t.h, t.d, self._scene_s, self.rec, self.rec_colors, stream)
+            B.composite_fwd(self.cfg, t.h, t.d, self.rec_colors, self.vals, self.ranges, self.gbuf, self.last,
+                            stream)
+            B.colors_to_image(t.h, self.gbuf, self.img, stream)
+        elif self.fused:
             B.render_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
                          self.stats_fwd, stream)
         else:
@@ -207,17 +222,26 @@ class Renderer:
         t = self.table
         self.zero_grads()
         if loss == "paper":
-            if target is None or not self.fused:
-                raise ValueError("the paper's losses take a target and the fused path")
+            if target is None:
+                raise ValueError("the paper's losses take a target")
             self._loss_buffers()
             self.loss.zero_()
             B.image_loss(self.cfg, t.h, t.d, self.img, target, lambda_dssim, self.dimg_loss, self.loss,
                          self.ws_loss, stream)
-            B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
-                         self.dimg_loss, None, None, 1.0, self.drec, self.stats_bwd, stream)
+            if self.shading == "gaussian":
+                self._backward_gaussian_shading(self.dimg_loss, stream)
+            elif self.fused:
+                B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
+                             self.dimg_loss, None, None, 1.0, self.drec, self.stats_bwd, stream)
+            else:
+                raise ValueError("the paper's losses run on the fused path")
             B.incident_loss(t.h, t.d, self.rec, lambda_incident, self.drec, self.loss, stream)
         elif loss != "l1":
             raise ValueError(f"unknown loss {loss!r}")
+        elif self.shading == "gaussian":
+            if dimg is None:
+                raise ValueError("per-Gaussian shading takes dimg (or loss='paper')")
+            self._backward_gaussian_shading(dimg, stream)
         elif self.fused:
             B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
                          dimg, target, weight, l1_scale, self.drec, self.stats_bwd, stream)
@@ -239,6 +263,13 @@ class Renderer:
                            stream)
             B.vis_sh_bwd(t.h, t.d, self._scene_s, self.vis_sh, self.dvis_item, self.dvis_sh, self.grads["mu"],
                          stream)
+
+    def _backward_gaussian_shading(self, dimg, stream):
+        t = self.table
+        B.colors_to_image_bwd(t.h, dimg, self.dgbuf, stream)
+        B.composite_bwd(self.cfg, t.h, t.d, self.rec_colors, self.vals, self.ranges, self.gbuf, self.last,
+                        self.dgbuf, self.drec, stream)
+        B.shade_gaussians_bwd(t.h, t.d, self._scene_s, self.rec, self.drec, stream)
 
     def capture(self, dimg=None, target=None, weight=None, l1_scale=1.0, loss="l1"):
         """Capture one forward + backward step as a CUDA graph and return it.
@@ -324,7 +355,7 @@ def mlp_to_device(spec, precision=None, device="cuda") -> MLPParams:
 
 
 def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=None, device="cuda",
-                          pair_slice=None, vis_sh=None) -> Renderer:
+                          pair_slice=None, vis_sh=None, shading="deferred") -> Renderer:
     """vis_sh: optional N x 16 numpy array of SH visibility coefficients."""
     cfg = default_cfg(tile or wl.tile)
     scene, offs, counts = concat_scenes(wl.scenes, device)
@@ -334,7 +365,8 @@ def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=No
     sh = None
     if vis_sh is not None:
         sh = torch.from_numpy(np.ascontiguousarray(vis_sh, np.float32)).to(device)
-    return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device, vis_sh=sh)
+    return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device, vis_sh=sh,
+                    shading=shading)
 
 
 class MultiLightRenderer:
