@@ -189,6 +189,8 @@ def _config(args):
            "l2": "inputs larger than L2 (G-buffer and instance lists >> 129 MB)"}
     if args.pairs is not None:
         cfg["pairs_override"] = args.pairs
+    if getattr(args, "shading", "deferred") == "gaussian":
+        cfg["shading"] = "per Gaussian (the paper's w/o-Deferred ablation), App. E losses"
     if getattr(args, "vis_sh", False):
         cfg["visibility"] = ("SH term per Gaussian (degree 3, evaluated at each pair's light direction) with the "
                              "ray-traced visibility loss (0.01 L1 to a BVH-traced target)")
@@ -244,8 +246,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # raster_common.cuh) and for workloads made of such pairs; otherwise null.
 TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("46d47d740881c8c047dabb606a8eee7eaf0ed14f94386a922a7c031dafd7807c", 107.65e6),
-    "render_fwd": ("46d47d740881c8c047dabb606a8eee7eaf0ed14f94386a922a7c031dafd7807c", 70.45e6),
+    "render_bwd": ("5d56c5a2c34af8132c2dbc4eff46949b4f7e384f5a34f41e2b28c9948bb5a861", 108.68e6),
+    "render_fwd": ("5d56c5a2c34af8132c2dbc4eff46949b4f7e384f5a34f41e2b28c9948bb5a861", 70.47e6),
 }
 
 
@@ -296,7 +298,7 @@ def run_ours(args):
     wl = sg.make_workload(args.workload, seed_offset=rank, n_pairs=args.pairs, net=args.net)
     precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
     vis_sh = sg.vis_sh_coeffs(77 + rank, sum(sc.N for sc in wl.scenes)) if args.vis_sh else None
-    r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile, vis_sh=vis_sh)
+    r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile, vis_sh=vis_sh, shading=args.shading)
     n_inst = r.fit_capacity()
     trace = None
     if args.vis_sh:
@@ -390,7 +392,7 @@ def run_ours(args):
     stats_b = torch.zeros(2, dtype=torch.int64, device="cuda")
     if args.vis_sh:
         stage_ms["vis_sh"] = 0.0
-    for _ in range(reps):
+    for _ in range(reps if args.shading == "deferred" else 0):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
         ev_v = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         if args.vis_sh:
@@ -444,6 +446,20 @@ def run_ours(args):
             stage_ms[s] += a.elapsed_time(b) / reps
         if args.loss == "paper":
             stage_ms["loss"] += (e_l[0].elapsed_time(e_l[1]) + e_l[2].elapsed_time(e_l[3])) / reps
+    if args.shading == "gaussian":      # the ablation path: forward and backward timed as wholes
+        stage_ms = {"forward": 0.0, "backward": 0.0}
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(st)
+            r.forward()
+            e[1].record(st)
+            r.backward(target=target, loss="paper")
+            e[2].record(st)
+            torch.cuda.synchronize()
+            stage_ms["forward"] += e[0].elapsed_time(e[1]) / reps
+            stage_ms["backward"] += e[1].elapsed_time(e[2]) / reps
+        for k in STAGES:
+            stage_ms.setdefault(k, 0.0)
     n_items, n_pixels = table.n_items, table.n_pixels
     # rows the network backward runs on: items with a nonzero upstream gradient
     # (the others add exactly zero and are compacted out)
@@ -457,7 +473,9 @@ def run_ours(args):
     }
     dom = max(STAGES, key=lambda s: stage_ms[s])
     widths = [int(r._mlp_s.width[i]) for i in range(r._mlp_s.n_layers + 1)]
-    if dom in ("mlp_fwd", "mlp_bwd") and precision == B.BF16:
+    if args.shading == "gaussian":      # an ablation configuration: stages are not split
+        roof = None
+    elif dom in ("mlp_fwd", "mlp_bwd") and precision == B.BF16:
         fl = mlp_flops(widths, n_items) if dom == "mlp_fwd" else 2 * mlp_flops(widths, n_active)
         ach = fl / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
@@ -479,7 +497,7 @@ def run_ours(args):
                 "traffic": None, "peak_source": peak_src + " (hbm copy)"}
     total_bytes = sum(algorithmic_bytes(s, n_items, n_pixels, n_inst, n_gauss, n_pairs) for s in STAGES)
     loss_roof = None
-    if args.loss == "paper":
+    if args.loss == "paper" and "loss" in stage_ms:
         # SSIM pass A: img + target in, 9 coefficient floats out; pass B: the
         # coefficients + img + target in, dimg out; incident: L_in, v in and
         # their two gradient slots read-modify-written
@@ -829,6 +847,9 @@ def main():
     ap.add_argument("--loss", default="l1", choices=["l1", "paper"],
                     help="paper: the training losses of App. E (L1 + D-SSIM image loss, incident constraint)")
     ap.add_argument("--fp32-mlp", action="store_true")
+    ap.add_argument("--shading", default="deferred", choices=["deferred", "gaussian"],
+                    help="gaussian: the paper's w/o-Deferred ablation (each Gaussian shaded, colours composited); "
+                         "runs with the App. E losses")
     ap.add_argument("--vis-sh", action="store_true",
                     help="SH visibility term per Gaussian (v evaluated at each pair's light) with the ray-traced "
                          "visibility loss; also times the BVH build and the tracing")
@@ -839,6 +860,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.shading == "gaussian":
+        args.loss = "paper"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "c6":
