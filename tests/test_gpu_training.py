@@ -38,6 +38,6 @@ def test_adam_steps_reduce_the_l1_loss(shading):
         loss.backward()
         opt.step()
         r.check_status()
-        losses.append(float(loss))
+        losses.append(loss.item())
     print(f"\n{shading}: L1 {losses[0]:.5f} -> {losses[-1]:.5f}")
     assert losses[-1] < 0.7 * losses[0]
