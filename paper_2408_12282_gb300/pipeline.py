@@ -381,7 +381,11 @@ class MultiLightRenderer:
     in pair order, or per view as a weighted sum (forward(env_w=...))."""
 
     def __init__(self, scene: dict, mlp: MLPParams, views, lights, cfg: B.Cfg, scene_offsets, scene_counts,
-                 capacity: int | None = None, device="cuda"):
+                 capacity: int | None = None, device="cuda", vis_sh=None):
+        """vis_sh (N x 16 device tensor, optional): the SH visibility term,
+        evaluated per (view, light) pair at the light direction; v enters the
+        network per pair (the composited visibility channel does not enter the
+        shading, so the per-view records keep the per-Gaussian v)."""
         lights = np.asarray(lights, np.float64)
         V, L = lights.shape[0], lights.shape[1]
         if len(views) != V or lights.shape[2] != 3:
@@ -410,8 +414,16 @@ class MultiLightRenderer:
         self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
         self.dW = [torch.zeros_like(w) for w in mlp.W]
         self.db = [torch.zeros_like(b) for b in mlp.b]
-        self._scene_s = B.scene_struct(scene)
+        self.vis_sh = vis_sh
+        self.vis_item = self.dvis_item = self.dvis_sh = self.vis_traced = self.loss_vis = None
+        if vis_sh is not None:
+            self.vis_item = torch.zeros(npi, **f32)
+            self.dvis_item = torch.zeros(npi, **f32)
+            self.dvis_sh = torch.zeros_like(vis_sh)
+        self._scene_s = B.scene_struct(scene)                       # per-view records
         self._grad_s = B.scene_grad_struct(self.grads)
+        self._scene_p = B.scene_struct(scene, self.vis_item)        # (view, light) pairs: network
+        self._grad_p = B.scene_grad_struct(self.grads, self.dvis_item)
         self._mlp_s = mlp.struct()
         self._mlp_g = B.mlp_grad_struct(self.dW, self.db)
         mws = B.mlp_workspace_bytes(self._mlp_s, npi)
@@ -440,7 +452,9 @@ class MultiLightRenderer:
 
     def forward_front(self, stream=None):
         v, p = self.views, self.pairs
-        B.mlp_fwd(self._mlp_s, p.h, p.d, self._scene_s, self.mlp_out, self.status, stream)
+        if self.vis_sh is not None:
+            B.vis_sh_fwd(p.h, p.d, self._scene_p, self.vis_sh, self.vis_item, stream)
+        B.mlp_fwd(self._mlp_s, p.h, p.d, self._scene_p, self.mlp_out, self.status, stream)
         B.project_fwd(self.cfg, v.h, v.d, self._scene_s, None, self.rec, self.rect, stream)
         B.bin_sort(self.cfg, v.h, v.d, self.rec, self.rect, self.capacity, self.vals, self.ranges, self.count,
                    self.status, self.ws_bin, stream)
@@ -463,18 +477,42 @@ class MultiLightRenderer:
             g.zero_()
         for g in self.dW + self.db:
             g.zero_()
+        if self.vis_sh is not None:
+            self.dvis_item.zero_()
+            self.dvis_sh.zero_()
 
-    def backward(self, dimg=None, target=None, l1_scale=1.0, stream=None):
+    def trace_visibility(self, stream=None):
+        """Ray-traced visibility of every (view, light, Gaussian) toward its
+        light into self.vis_traced (the target of the visibility loss)."""
+        n = self.scene["mu"].shape[0]
+        if getattr(self, "bvh", None) is None:
+            self.bvh = torch.empty(B.bvh_floats(n), device=self.device, dtype=torch.float32)
+            self.ws_bvh = torch.empty(B.bvh_workspace_bytes(n), device=self.device, dtype=torch.uint8)
+            self.vis_traced = torch.zeros(self.pairs.n_items, device=self.device, dtype=torch.float32)
+        B.bvh_build(self.cfg, self._scene_s, self.bvh, self.ws_bvh, stream)
+        B.trace_visibility(self.cfg, self.pairs.h, self.pairs.d, self._scene_s, self.bvh, self.vis_traced, stream)
+        return self.vis_traced
+
+    def backward(self, dimg=None, target=None, l1_scale=1.0, stream=None, lambda_raytrace=0.01):
         """Upstream: dimg per (view, light) image, or the L1 loss against target."""
         v, p = self.views, self.pairs
         self.zero_grads()
         B.render_ml_bwd(self.cfg, v.h, v.d, self.n_lights, self.lights, self.rec, self.mlp_out, self.vals,
                         self.ranges, self.gbuf, self.last, self.img, dimg, target, l1_scale, self.drec, self.dmlp,
                         self.stats_bwd, stream)
-        B.mlp_bwd_strided(self._mlp_s, p.h, p.d, self._scene_s, self.dmlp, 4, self._mlp_g, self.dx_items,
+        B.mlp_bwd_strided(self._mlp_s, p.h, p.d, self._scene_p, self.dmlp, 4, self._mlp_g, self.dx_items,
                           self.ws_mlp, self.status, stream)
         B.project_bwd(self.cfg, v.h, v.d, self._scene_s, self.drec, None, self._grad_s, stream)
-        B.project_bwd(self.cfg, p.h, p.d, self._scene_s, None, self.dx_items, self._grad_s, stream)
+        B.project_bwd(self.cfg, p.h, p.d, self._scene_p, None, self.dx_items, self._grad_p, stream)
+        if self.vis_sh is not None:
+            if self.vis_traced is not None and lambda_raytrace > 0.0:
+                if self.loss_vis is None:
+                    self.loss_vis = torch.zeros(p.n, device=self.device, dtype=torch.float32)
+                self.loss_vis.zero_()
+                B.vis_loss(p.h, p.d, self.vis_item, self.vis_traced, lambda_raytrace, self.dvis_item,
+                           self.loss_vis, stream)
+            B.vis_sh_bwd(p.h, p.d, self._scene_p, self.vis_sh, self.dvis_item, self.dvis_sh, self.grads["mu"],
+                         stream)
 
     def capture(self, dimg=None, target=None, l1_scale=1.0):
         """One forward + backward step as a CUDA graph (call fit_capacity() first)."""
@@ -500,7 +538,8 @@ class MultiLightRenderer:
             raise B.SSSGSError("a tensor-core kernel stopped on its wait limit; outputs are incomplete")
 
 
-def multilight_renderer_for_workload(wl, precision=None, capacity=None, device="cuda") -> MultiLightRenderer:
+def multilight_renderer_for_workload(wl, precision=None, capacity=None, device="cuda",
+                                     vis_sh=None) -> MultiLightRenderer:
     """Views and lights of a workload whose pairs come in runs of wl.n_lights
     sharing a camera (scenegen c6)."""
     L = wl.n_lights
@@ -511,7 +550,11 @@ def multilight_renderer_for_workload(wl, precision=None, capacity=None, device="
     cfg = default_cfg(16)
     scene, offs, counts = concat_scenes(wl.scenes, device)
     mlp = mlp_to_device(wl.mlp, precision, device)
-    return MultiLightRenderer(scene, mlp, views, lights, cfg, offs, counts, capacity=capacity, device=device)
+    sh = None
+    if vis_sh is not None:
+        sh = torch.from_numpy(np.ascontiguousarray(vis_sh, np.float32)).to(device)
+    return MultiLightRenderer(scene, mlp, views, lights, cfg, offs, counts, capacity=capacity, device=device,
+                              vis_sh=sh)
 
 
 def autotune_tile(wl, candidates=(16, 8), precision=None, steps=2, device="cuda", capacity_slack=1.15):

@@ -118,3 +118,34 @@ def test_multilight_fused_l1_equals_explicit_dimg():
     b = _run_ml(wl, B.FP32, dimg=(s * np.sign(img - target)).astype(np.float32))
     for k in SCENE_KEYS:
         assert _rel(a.grads[k].cpu().numpy(), b.grads[k].cpu().numpy()) < 1e-6, k
+
+
+def test_multilight_with_sh_visibility_equals_single_light_path():
+    """The SH visibility term per (view, light) pair with the ray-traced
+    visibility loss: the many-light renderer against the single-light path on
+    the same pairs (network outputs equal, gradients to summation order)."""
+    wl = sg.make_workload("c6", N=12000, res=48, n_views=2, n_lights=4, net="paper")
+    sh = sg.vis_sh_coeffs(3, wl.scenes[0].N)
+    P = sum(p.W * p.H for p in wl.pairs)
+    dimg = torch.from_numpy(sg.random_dimg(19, P).astype(np.float32)).cuda()
+    ml = PL.multilight_renderer_for_workload(wl, precision=B.FP32, vis_sh=sh)
+    ml.fit_capacity()
+    vt = ml.trace_visibility().clone()
+    ml.forward()
+    ml.backward(dimg=dimg)
+    r = PL.renderer_for_workload(wl, precision=B.FP32, vis_sh=sh)
+    r.fit_capacity()
+    r.vis_traced = vt
+    r.forward()
+    r.backward(dimg=dimg)
+    torch.cuda.synchronize()
+    ml.check_status()
+    r.check_status()
+    assert torch.equal(ml.vis_item, r.vis_item)
+    assert torch.allclose(ml.mlp_out, r.mlp_out, rtol=0, atol=0)
+    assert (ml.img - r.img).abs().max().item() <= 1e-6
+    assert torch.allclose(ml.loss_vis, r.loss_vis, rtol=1e-6)
+    errs = {k: _rel(ml.grads[k].cpu().numpy(), r.grads[k].cpu().numpy()) for k in SCENE_KEYS if k != "vis"}
+    errs["vis_sh"] = _rel(ml.dvis_sh.cpu().numpy(), r.dvis_sh.cpu().numpy())
+    print("\nmany-light with SH visibility vs single-light rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert all(v < 1e-4 for v in errs.values()), errs
