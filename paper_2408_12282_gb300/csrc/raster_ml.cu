@@ -89,13 +89,15 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
     const uint2 rg = ranges[tile];
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max, T_min = cfg.T_min;
     const float x0 = bx + 0.5f, y0 = by + 0.5f, px = i + 0.5f, py = j + 0.5f;
-    float T = 1.f, geo[10], vis = 0.f, lf[L][4];
+    // Accumulators as component pairs for the paired FP32 FMA (each component
+    // rounds as a scalar fmaf): geometry features (2k, 2k+1), light channels
+    // (0, 1) and (2, 3) of every light.
+    float T = 1.f, vis = 0.f;
+    float2 geo2[5], lf2[L][2];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) geo[k] = 0.f;
+    for (int k = 0; k < 5; ++k) geo2[k] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) lf[l][c] = 0.f;
+    for (int l = 0; l < L; ++l) lf2[l][0] = lf2[l][1] = make_float2(0.f, 0.f);
     uint32_t lastc = 0, stop = inside ? rg.y : rg.x, n_use = 0;
     bool done = !inside;
     const int nb = (int)((rg.y - rg.x + 31) >> 5);
@@ -148,15 +150,19 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
                 }
                 ++n_use;
                 const float w = T * e.alpha;
+                const float2 ww = make_float2(w, w);
                 const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k];
-                geo[0] += w * g1.z; geo[1] += w * g1.w; geo[2] += w * g2.x; geo[3] += w * g2.y;
-                geo[4] += w * g2.z; geo[5] += w * g2.w; geo[6] += w * g3.x; geo[7] += w * g3.y;
-                geo[8] += w * g3.z; geo[9] += w * g3.w;
-                vis += w * s_rec[buf][4][k].x;
+                geo2[0] = __ffma2_rn(ww, make_float2(g1.z, g1.w), geo2[0]);
+                geo2[1] = __ffma2_rn(ww, make_float2(g2.x, g2.y), geo2[1]);
+                geo2[2] = __ffma2_rn(ww, make_float2(g2.z, g2.w), geo2[2]);
+                geo2[3] = __ffma2_rn(ww, make_float2(g3.x, g3.y), geo2[3]);
+                geo2[4] = __ffma2_rn(ww, make_float2(g3.z, g3.w), geo2[4]);
+                vis = __fmaf_rn(w, s_rec[buf][4][k].x, vis);
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
                     const float4 v = s_lf[buf][l][k];
-                    lf[l][0] += w * v.x; lf[l][1] += w * v.y; lf[l][2] += w * v.z; lf[l][3] += w * v.w;
+                    lf2[l][0] = __ffma2_rn(ww, make_float2(v.x, v.y), lf2[l][0]);
+                    lf2[l][1] = __ffma2_rn(ww, make_float2(v.z, v.w), lf2[l][1]);
                 }
                 T = Tn;
                 lastc = base + k + 1;
@@ -181,6 +187,19 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
         }
     }
     if (!inside) return;
+    float geo[10], lf[L][4];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        geo[2 * k] = geo2[k].x;
+        geo[2 * k + 1] = geo2[k].y;
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        lf[l][0] = lf2[l][0].x;
+        lf[l][1] = lf2[l][0].y;
+        lf[l][2] = lf2[l][1].x;
+        lf[l][3] = lf2[l][1].y;
+    }
     const int64_t vpix = sP.pixel_offset + (int64_t)j * sP.W + i;
     float4* go = reinterpret_cast<float4*>(gbuf + (int64_t)GB * vpix);
     go[0] = make_float4(geo[0], geo[1], geo[2], geo[3]);
