@@ -7,6 +7,8 @@
 * The 64-pair 300K batch replayed from a captured CUDA graph with the fused
   L1 loss, as in bench.py: sampled pixels of two pairs against the oracle, and
   those pairs bit-identical to single-pair renders.
+* The same for the light-stage batch, the uneven batch of 50K-1M Gaussian
+  scenes at 400-1600 px, and the ray-traced visibility of the 64-pair batch.
 """
 import numpy as np
 import pytest
@@ -110,6 +112,43 @@ def test_full_light_stage_batch_graph_replay_sampled():
         got = img[offs[p] + sel]
         e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
         print(f"\nlight-stage pair {p}: {fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
+        assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
+
+
+def test_full_uneven_batch_graph_replay_sampled():
+    """The uneven batch (8 scenes of 50K-1M Gaussians, 8 pairs each at
+    400-1600 px) replayed from a captured graph with the fused L1 loss, as in
+    bench.py: sampled pixels of the smallest scene's first image and of the
+    1M-Gaussian scene's largest image against the oracle rendering that pair
+    on its own."""
+    wl = sg.make_workload("c5")
+    r = PL.renderer_for_workload(wl, precision=B.BF16)
+    r.fit_capacity()
+    target = torch.zeros(r.table.n_pixels, 3, device="cuda")
+    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * r.table.n_pixels))
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    r.check_status()
+    img = r.img.double().cpu().numpy()
+    assert all(torch.isfinite(g).all().item() for g in r.grads.values())
+    offs = [0]
+    for p in wl.pairs:
+        offs.append(offs[-1] + p.W * p.H)
+    small = next(p for p, q in enumerate(wl.pairs) if q.scene == 0)
+    big = max((p for p, q in enumerate(wl.pairs) if q.scene == len(wl.scenes) - 1), key=lambda p: wl.pairs[p].W)
+    rng = np.random.default_rng(8)
+    for p in (small, big):
+        pair = wl.pairs[p]
+        pix = O.all_pixels(pair.W, pair.H)
+        sel = rng.choice(len(pix), 1500, replace=False)
+        res = O.render_pair(wl.scenes[pair.scene], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=True)
+        fl = flagged(res["margin"])
+        got = img[offs[p] + sel]
+        e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
+        print(f"\nuneven batch pair {p} (scene {pair.scene}, {wl.scenes[pair.scene].N} Gaussians, {pair.W}x{pair.H}): "
+              f"{fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
+        assert (res["ncontrib"] > 0).mean() > 0.05
         assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
 
 
