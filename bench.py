@@ -565,7 +565,8 @@ def run_ours(args):
                 loss_host.copy_(r.loss, non_blocking=True)
             for k2, v in host_out.items():
                 v.copy_(r.grads[k2], non_blocking=True)
-        e2e_step()
+        for _ in range(args.warmup):       # same warm-up as the device-timed loop
+            e2e_step()
         torch.cuda.synchronize()
         q0 = torch.cuda.Event(enable_timing=True)
         q1 = torch.cuda.Event(enable_timing=True)
@@ -792,7 +793,8 @@ def run_ours_ml(args):
                 PL.allreduce_gradients(grads_flat)
             for k2, t in host_out.items():
                 t.copy_(r.grads[k2], non_blocking=True)
-        e2e_step()
+        for _ in range(args.warmup):       # same warm-up as the device-timed loop
+            e2e_step()
         torch.cuda.synchronize()
         q0 = torch.cuda.Event(enable_timing=True)
         q1 = torch.cuda.Event(enable_timing=True)
