@@ -86,12 +86,17 @@ def test_isotropic_gaussian_on_axis_closed_form():
     assert proj[0, 7] == pytest.approx(math.log(255 * o), rel=1e-6)  # alpha_min is f32(1/255)
 
 
-def test_off_axis_projection_matches_monte_carlo():
-    """Small Gaussian off axis: EWA covariance ~ covariance of projected samples."""
+@pytest.mark.parametrize("mu,scales", [([0.4, 0.2, -0.1], [0.004, 0.002, 0.006]),
+                                       ([0.4, 0.9, 0.6], [0.004, 0.002, 0.02])])
+def test_off_axis_projection_matches_monte_carlo(mu, scales):
+    """Small Gaussian off axis: EWA covariance ~ covariance of projected samples.
+    The second case lies far off axis in both image directions (|t_x / t_z|,
+    |t_y / t_z| ~ 0.15, 0.27) and is elongated, so every entry of the
+    projection Jacobian's depth column shapes the footprint."""
     rng = np.random.default_rng(11)
     pair = sg._make_pair([0.3, -2.5, 1.2], [0, 0, 4], 256, 256)
-    mu = np.array([[0.4, 0.2, -0.1]])
-    ls = np.log([[0.004, 0.002, 0.006]])
+    mu = np.array([mu])
+    ls = np.log([scales])
     q = np.array([[0.8, 0.3, -0.4, 0.2]])
     sc = _scene(mu, ls, q, [1.0])
     proj, _, _ = O.project(sc, pair, O.Cfg(dilation=0.0))
@@ -135,6 +140,60 @@ def test_lone_gaussian_peak_alpha_equals_opacity():
     assert np.allclose(r["img"][0], o * np.array([0.2, 0.4, 0.6]), rtol=1e-13)
 
 
+def test_isotropic_alpha_falloff_closed_form():
+    """Isotropic Gaussian on the optical axis: Sigma' = ((f s / z)^2 + dil) I,
+    so alpha at a pixel centre a distance r from the mean is
+    o exp(-r^2 / (2 var)) (Eq. 3's alpha with the EWA footprint of Eq. 2)."""
+    z, s, f, dil = 3.0, 0.06, 60.0, 0.3
+    pair = _pair_looking_down_z(W=32, H=32, fx=f)
+    sc = _scene([[0, 0, z]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [0.0], sss=[1.0])
+    pix = np.array([[i, j] for i in range(12, 21) for j in range(12, 21)], np.int32)
+    r = O.render_pair(sc, pair, sg.mlp_spec(1, "basic", [8]), O.Cfg(dilation=dil), pixels=pix,
+                      mlp_out=np.zeros((1, 4)))
+    var = (f * s / z) ** 2 + dil
+    r2 = (pix[:, 0] + 0.5 - pair.cx) ** 2 + (pix[:, 1] + 0.5 - pair.cy) ** 2
+    expect = 0.5 * np.exp(-r2 / (2 * var))
+    seen = expect >= np.float32(1 / 255) * (1 + 1e-6)
+    assert seen.sum() >= 20
+    assert np.allclose(1 - r["gbuf"][seen, 15], expect[seen], rtol=1e-12)
+
+
+def test_anisotropic_alpha_follows_the_projected_covariance():
+    """Rotated, anisotropic, off-axis Gaussian on a non-square image: alpha at
+    every pixel equals o exp(-d^T Sigma'^-1 d / 2), with Sigma' the projected
+    covariance (pinned against Monte Carlo above), its inverse taken by
+    numpy, and d the offset from the pinhole projection of the mean."""
+    W, H, f = 48, 40, 60.0
+    pair = sg.Pair(R=np.eye(3), t=np.zeros(3), fx=f, fy=f, cx=W / 2, cy=H / 2, W=W, H=H,
+                   light=np.array([0.0, 0.0, -5.0]))
+    mu = np.array([0.3, -0.2, 3.0])
+    sc = _scene([mu], [[-2.6, -3.4, -3.0]], [[0.8, 0.3, -0.4, 0.2]], [0.0], sss=[1.0])
+    proj, _, _ = O.project(sc, pair)
+    E = np.array([[proj[0, 13], proj[0, 14]], [proj[0, 14], proj[0, 15]]])
+    assert abs(E[0, 1]) > 0.1 * math.sqrt(E[0, 0] * E[1, 1])    # the footprint is tilted
+    m = np.array([f * mu[0] / mu[2] + pair.cx, f * mu[1] / mu[2] + pair.cy])
+    pix = O.all_pixels(W, H)
+    r = O.render_pair(sc, pair, sg.mlp_spec(1, "basic", [8]), pixels=pix, mlp_out=np.zeros((1, 4)))
+    d = m[None, :] - (pix + 0.5)
+    q = np.einsum("ni,ij,nj->n", d, np.linalg.inv(E), d)
+    expect = 0.5 * np.exp(-0.5 * q)
+    seen = expect >= np.float32(1 / 255) * (1 + 1e-6)
+    assert seen.sum() >= 30
+    assert np.allclose(1 - r["gbuf"][seen, 15], expect[seen], rtol=1e-11)
+    assert np.all(r["gbuf"][expect < np.float32(1 / 255) * (1 - 1e-6), 15] == 1.0)
+
+
+def test_opaque_gaussian_alpha_clamps_at_alpha_max():
+    """Mean on a pixel centre, opacity above alpha_max: alpha = 0.99 there."""
+    pair = _pair_looking_down_z(W=32, H=32, fx=80.0)
+    z = 3.0
+    x = (16.5 - pair.cx) * z / pair.fx
+    sc = _scene([[x, x, z]], [[-2.5] * 3], [[1, 0, 0, 0]], [8.0])
+    r = O.render_pair(sc, pair, sg.mlp_spec(1, "basic", [8]), O.Cfg(dilation=0.0),
+                      pixels=np.array([[16, 16]], np.int32), mlp_out=np.zeros((1, 4)))
+    assert 1 - r["gbuf"][0, 15] == pytest.approx(float(np.float32(0.99)), rel=1e-14)   # alpha_max is f32(0.99)
+
+
 # ---------------------------------------------------------------- compositing (Eq. 3)
 
 def test_weights_telescope_to_one_minus_T_everywhere():
@@ -162,6 +221,23 @@ def test_two_coincident_gaussians_closed_form():
     expect = a1 * c1 + (1 - a1) * a2 * c2
     assert np.allclose(r["gbuf"][0, 4:7], expect, rtol=1e-13)
     assert r["gbuf"][0, 15] == pytest.approx((1 - a1) * (1 - a2), rel=1e-13)
+
+
+def test_equal_depth_ties_composite_in_storage_order():
+    """Two Gaussians at the same mean (equal float32 depth keys) composite in
+    storage order: C = a0 c0 + (1 - a0) a1 c1 with Gaussian 0 in front (the
+    stable sort's tie rule); a0 != a1 makes the other order differ."""
+    pair = _pair_looking_down_z(W=16, H=16, fx=40.0)
+    z = 2.0
+    x = (8.5 - pair.cx) / pair.fx * z
+    c0, c1 = np.array([0.9, 0.1, 0.2]), np.array([0.1, 0.8, 0.3])
+    sc = _scene([[x, x, z]] * 2, [[-1.5] * 3] * 2, [[1, 0, 0, 0]] * 2, [0.5, 1.5], base=[c0, c1])
+    r = O.render_pair(sc, pair, sg.mlp_spec(1, "basic", [8]), O.Cfg(dilation=0.0),
+                      pixels=np.array([[8, 8]], np.int32), mlp_out=np.zeros((2, 4)))
+    assert r["dkey"][0] == r["dkey"][1]
+    a0, a1 = 1 / (1 + math.exp(-0.5)), 1 / (1 + math.exp(-1.5))
+    assert np.allclose(r["gbuf"][0, 4:7], a0 * c0 + (1 - a0) * a1 * c1, rtol=1e-13)
+    assert not np.allclose(a0 * c0 + (1 - a0) * a1 * c1, a1 * c1 + (1 - a1) * a0 * c0, rtol=1e-3)
 
 
 def test_brute_force_equals_tiled_bitwise_and_tile_size_independent():
@@ -218,6 +294,24 @@ def test_depth_order_and_stop_rule():
     assert r["ncontrib"][0] == n and 0 < n < 12
     assert r["gbuf"][0, 7] == pytest.approx(acc, rel=1e-13)
     assert r["gbuf"][0, 15] == pytest.approx(T, rel=1e-13)
+
+
+def test_stop_rule_ends_the_walk():
+    """The walk ends at the first Gaussian that would take T below T_min: a
+    faint Gaussian behind it, which alone would keep T above T_min, does not
+    contribute. Opacities 0.98, 0.96 give T = 8e-4; 0.9 would give 8e-5 < 1e-4
+    (stop); 0.05 behind it would give 7.6e-4."""
+    pair = _pair_looking_down_z(W=8, H=8, fx=20.0)
+    x = (4.5 - pair.cx) / pair.fx
+    zs = [2.0, 2.2, 2.4, 2.6]
+    ops = [0.98, 0.96, 0.9, 0.05]
+    sc = _scene([[x * z, x * z, z] for z in zs], [[-1.0] * 3] * 4, [[1, 0, 0, 0]] * 4,
+                [math.log(o / (1 - o)) for o in ops], rough=zs)
+    r = O.render_pair(sc, pair, sg.mlp_spec(1, "basic", [8]), O.Cfg(dilation=0.0),
+                      pixels=np.array([[4, 4]], np.int32), mlp_out=np.zeros((4, 4)))
+    assert r["ncontrib"][0] == 2
+    assert r["gbuf"][0, 15] == pytest.approx(0.02 * 0.04, rel=1e-12)
+    assert r["gbuf"][0, 7] == pytest.approx(0.98 * 2.0 + 0.02 * 0.96 * 2.2, rel=1e-12)
 
 
 # ---------------------------------------------------------------- BRDF (Eq. 4)
