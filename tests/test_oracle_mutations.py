@@ -64,6 +64,8 @@ C_MUTANTS = [
     ("quaternion gradient sign", "- y * G[6] + x * G[7]);", "+ y * G[6] + x * G[7]);", FD),
     ("covariance gradient factor", "dM[i * 3 + j] = 2 * acc;", "dM[i * 3 + j] = acc;", FD),
     ("depth gradient sign", "dt[2] += ddepth[g];", "dt[2] -= ddepth[g];", FD),
+    ("pixel rectangle too small", "double ex = sqrt(2.0 * L * a) * (1.0 + 1e-9);", "double ex = sqrt(L * a) * (1.0 + 1e-9);",
+     [(PP.test_brute_force_equals_tiled_bitwise_and_tile_size_independent, ())]),
     ("mean gradient uses the wrong conic entry", "dg[0] += dp * (P[2] * dx + P[3] * dy);",
      "dg[0] += dp * (P[2] * dx + P[4] * dy);", FD),
     ("per-Gaussian shading upstream sign", "dF[c] = dimg[3 * (size_t)q + c];", "dF[c] = -dimg[3 * (size_t)q + c];",
@@ -105,6 +107,9 @@ PY_MUTANTS = [
      [(PP.test_paper_input_encoding_and_gradients_match_autograd, ())]),
     (O, "_paper_backward", "dzh = rnd((dzi @ W[4]) * _dlrelu(hid))", "dzh = rnd(dzi @ W[4])",
      [(PP.test_paper_mlp_matches_torch_modules_fp64, ()), (PG.test_fd_paper_mlp_inputs_and_weights, ())]),
+    (O, "render_pair", "scene.normal, scene.base, scene.rough[:, None],", "scene.base, scene.normal, scene.rough[:, None],",
+     [(PP.test_two_coincident_gaussians_closed_form, ())]),
+    (O, "render_pair", 'g["metal"] += dfeat[:, 8]', 'g["metal"] += dfeat[:, 7]', FD),
     (O, "gaussian_colors", "F0 = 0.04 * (1 - m[:, None]) + b * m[:, None]", "F0 = 0.04 + b * m[:, None]",
      [(PF.test_colour_equals_deferred_shading_at_the_mean, ())]),
 ]
