@@ -598,3 +598,61 @@ def allreduce_gradients(tensors, group=None):
     import torch.distributed as dist
     for t in tensors:
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+
+
+# ---------------------------------------------------------------------- checkpoint / resume
+
+CHECKPOINT_FORMAT = "sssgs-checkpoint-1"
+
+
+def state_dict(renderer) -> dict:
+    """The trainable state of a Renderer or MultiLightRenderer as CPU tensors:
+    scene parameters, network weights and biases, and the SH visibility
+    coefficients when the renderer has them."""
+    sd = {f"scene.{k}": renderer.scene[k].detach().cpu().clone() for k in SCENE_KEYS}
+    for l, w in enumerate(renderer.mlp.W):
+        sd[f"mlp.W{l}"] = w.detach().cpu().clone()
+    for l, b in enumerate(renderer.mlp.b):
+        sd[f"mlp.b{l}"] = b.detach().cpu().clone()
+    if getattr(renderer, "vis_sh", None) is not None:
+        sd["vis_sh"] = renderer.vis_sh.detach().cpu().clone()
+    return sd
+
+
+def load_state_dict(renderer, sd: dict) -> None:
+    """Copy a state_dict into the renderer's existing buffers, in place, so a
+    captured CUDA graph keeps reading the restored values. Raises ValueError
+    on a missing, unexpected or mis-shaped entry (nothing is copied then)."""
+    targets = {f"scene.{k}": renderer.scene[k] for k in SCENE_KEYS}
+    targets.update({f"mlp.W{l}": w for l, w in enumerate(renderer.mlp.W)})
+    targets.update({f"mlp.b{l}": b for l, b in enumerate(renderer.mlp.b)})
+    if getattr(renderer, "vis_sh", None) is not None:
+        targets["vis_sh"] = renderer.vis_sh
+    missing = sorted(set(targets) - set(sd))
+    unexpected = sorted(set(sd) - set(targets))
+    if missing or unexpected:
+        raise ValueError(f"checkpoint keys differ: missing {missing}, unexpected {unexpected}")
+    for k, t in targets.items():
+        if tuple(sd[k].shape) != tuple(t.shape):
+            raise ValueError(f"checkpoint entry {k}: shape {tuple(sd[k].shape)}, expected {tuple(t.shape)}")
+    with torch.no_grad():
+        for k, t in targets.items():
+            t.copy_(sd[k].to(dtype=t.dtype), non_blocking=False)
+
+
+def save_checkpoint(path, renderer, step: int = 0, extra: dict | None = None) -> None:
+    """Write the renderer's trainable state with the step counter and any
+    caller state (optimizer state_dict, RNG state, ...) under `extra`."""
+    torch.save({"format": CHECKPOINT_FORMAT, "step": int(step), "state": state_dict(renderer),
+                "extra": extra or {}}, path)
+
+
+def load_checkpoint(path, renderer) -> dict:
+    """Restore a checkpoint written by save_checkpoint into `renderer` (in
+    place); returns {"step": ..., "extra": ...}. The file is unpickled: load
+    only checkpoints you wrote."""
+    ck = torch.load(path, map_location="cpu", weights_only=False)
+    if not isinstance(ck, dict) or ck.get("format") != CHECKPOINT_FORMAT:
+        raise ValueError(f"{path}: not a {CHECKPOINT_FORMAT} file")
+    load_state_dict(renderer, ck["state"])
+    return {"step": ck["step"], "extra": ck["extra"]}
