@@ -64,3 +64,49 @@ def test_two_rank_gradient_allreduce_equals_full_batch(tmp_path):
     for k in PL.SCENE_KEYS:
         assert np.allclose(got[k], ref[k], rtol=1e-12, atol=1e-14 * np.abs(ref[k]).max()), k
     assert PL.shard_pairs(5, 0, 2) == [0, 2, 4] and PL.shard_pairs(5, 1, 2) == [1, 3]
+
+
+def _worker_peer_dies(rank, world, port, out_path):
+    import sys
+    import time
+    from datetime import timedelta
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_2408_12282_gb300 import pipeline as PL
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)                      # dies between steps, before the gradient exchange
+    t0 = time.time()
+    try:
+        PL.allreduce_gradients([torch.ones(16)])
+        status = "completed"
+    except Exception as ex:              # the exchange must fail, not hang
+        status = f"error:{type(ex).__name__}"
+    with open(out_path, "w") as fh:
+        fh.write(f"{status} {time.time() - t0:.2f}")
+    os._exit(0)
+
+
+def test_a_dead_peer_fails_the_gradient_exchange_instead_of_hanging(tmp_path):
+    """Failure detection on the host: a rank that exits before the exchange
+    makes the survivor's all-reduce raise within the process group's timeout
+    (10 s) rather than wait forever."""
+    out = str(tmp_path / "status.txt")
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_peer_dies, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    alive = [p.is_alive() for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert not any(alive), "a rank did not finish"
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+    status, secs = open(out).read().split()
+    assert status.startswith("error:"), status
+    assert float(secs) < 60
