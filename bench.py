@@ -158,8 +158,9 @@ def run_reference(args):
             times.append(d["t_full_est"])
     t = sum(times) / len(times)
     value = 1.0 / t
-    sample = (f"one view/light pair of workload {args.workload}: full network fwd+bwd over all Gaussians, "
-              f"raster fwd+bwd on every {stride}th pixel row, raster time scaled by {stride}")
+    sample = (f"one view/light pair of workload {args.workload}: full network fwd+bwd over all Gaussians "
+              f"(numpy, {threads} BLAS threads), raster fwd+bwd on every {stride}th pixel row (C, one thread), "
+              f"raster time scaled by {stride}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
