@@ -103,3 +103,40 @@ def test_binding_refuses_float64_and_strided_buffers():
         B._p(torch.zeros(4, 6)[:, ::2])
     assert B._p(None) is None
     assert B._p(torch.zeros(4, 3)) != 0
+
+
+def test_later_entry_points_reject_bad_arguments():
+    """The many-light, visibility, loss and per-Gaussian shading entry points
+    check their host arguments before any device work: a missing buffer, an
+    unsupported light count or tile edge, a misaligned buffer or a loss
+    weight outside [0, 1] returns an error code (fake aligned addresses
+    stand in for device buffers; nothing is dereferenced or launched)."""
+    lib = B.load_library()
+    c = B.cfg_default()
+    h = (B.Pair * 1)()
+    h[0].W = h[0].H = 16
+    h[0].fx = h[0].fy = 10.0
+    B.plan(h, c)
+    A = 256                      # an aligned fake device address
+    INVALID, UNSUPPORTED = -1, -3
+    ml = lambda cfg, d, L, rec: lib.sssgs_render_ml_fwd(ctypes.byref(cfg), h, d, 1, L, A, rec, A, A, A, A, A, A,
+                                                        None, None, None)
+    assert ml(c, None, 8, A) == INVALID                   # no device pair table
+    assert ml(c, A, 3, A) == INVALID                      # light count not 1, 2, 4, 8
+    assert ml(c, A, 8, A + 4) == INVALID                  # records not 16-byte aligned
+    c8 = B.cfg_default()
+    c8.tile = 8
+    assert ml(c8, A, 8, A) == UNSUPPORTED                 # many-light kernels are 16 x 16 only
+    assert lib.sssgs_render_ml_bwd(ctypes.byref(c), h, A, 1, 8, A, A, A, A, A, A, A, None, None, None, 1.0,
+                                   A, A, None, None) == INVALID   # neither dimg nor (img, target)
+    sc = B.Scene()
+    assert lib.sssgs_bvh_build(ctypes.byref(c), ctypes.byref(sc), A, A, 0, None) == INVALID   # no scene arrays
+    assert lib.sssgs_trace_visibility(ctypes.byref(c), h, A, 1, ctypes.byref(sc), A, A, None) == INVALID
+    assert lib.sssgs_vis_sh_fwd(h, A, 1, ctypes.byref(sc), A, A, None) == INVALID
+    assert lib.sssgs_vis_loss(h, A, 1, A, None, 0.01, A, A, None) == INVALID
+    assert lib.sssgs_image_loss(ctypes.byref(c), h, A, 1, A, A, 1.5, A, A, A, 1 << 20, None) == INVALID
+    assert lib.sssgs_image_loss(ctypes.byref(c), h, A, 1, A, None, 0.2, A, A, A, 1 << 20, None) == INVALID
+    assert lib.sssgs_incident_loss(h, A, 1, None, 0.02, A, A, None) == INVALID
+    assert lib.sssgs_shade_gaussians_fwd(h, A, 1, ctypes.byref(sc), A, A, None) == INVALID
+    assert lib.sssgs_colors_to_image(h, 1, A + 4, A, None) == INVALID   # G-buffer not 16-byte aligned
+    assert lib.sssgs_colors_to_image_bwd(h, 0, A, A, None) == INVALID
