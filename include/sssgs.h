@@ -333,7 +333,11 @@ int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
  * (pixel n_lights * pixel_offset_v + l * W_v * H_v + j * W_v + i); with
  * env_w[n_views * n_lights] (device weights) one image per view (view pixel
  * layout) holding sum_l env_w[v * n_lights + l] * image of light l.
- * d_stats as for sssgs_render_fwd. */
+ * d_stats as for sssgs_render_fwd.
+ * Errors: SSSGS_ERR_INVALID_ARG for a missing buffer, n_lights not 1, 2, 4
+ * or 8, or rec / mlp_out / gbuf not 16-byte (ranges not 8-byte) aligned;
+ * SSSGS_ERR_UNSUPPORTED unless cfg->tile == 16; SSSGS_ERR_CUDA if a launch
+ * fails. */
 int sssgs_render_ml_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const sssgs_pair* d_views, int n_views,
                         int n_lights, const float* lights, const float* rec, const float* mlp_out,
                         const uint32_t* vals, const uint32_t* ranges, float* gbuf, uint32_t* last, float* img,
@@ -345,7 +349,9 @@ int sssgs_render_ml_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const s
  * gradient records drec[n_view_items * 24] (geometry and the light-independent
  * features; fields 16..19 untouched) and dmlp[rows * 4] = dL/d(L_SSS 3, L_in)
  * per (view, light, item) row in mlp_out's layout, for
- * sssgs_mlp_bwd_strided(dout = dmlp, dout_stride = 4) on the pair table. */
+ * sssgs_mlp_bwd_strided(dout = dmlp, dout_stride = 4) on the pair table.
+ * Errors as for sssgs_render_ml_fwd, and SSSGS_ERR_INVALID_ARG without drec,
+ * dmlp, or an upstream (dimg, or img and target). */
 int sssgs_render_ml_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const sssgs_pair* d_views, int n_views,
                         int n_lights, const float* lights, const float* rec, const float* mlp_out,
                         const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
@@ -368,12 +374,18 @@ int sssgs_render_ml_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const s
  * the boxes bounding each Gaussian's support {alpha >= alpha_min}. Writes
  * bvh[sssgs_bvh_floats(n)] (nodes and per-Gaussian tracing records); the
  * caller allocates it and the workspace (sssgs_bvh_workspace_bytes, 256-byte
- * aligned). The BVH holds the scene's geometry as it is when built. */
+ * aligned). The BVH holds the scene's geometry as it is when built.
+ * Errors: SSSGS_ERR_INVALID_ARG for missing scene arrays or bvh, bvh not
+ * 16-byte or workspace not 256-byte aligned; SSSGS_ERR_WORKSPACE for a
+ * missing or short workspace; SSSGS_ERR_TOO_LARGE for n >= 2^30. n == 0 is a
+ * no-op. */
 int64_t sssgs_bvh_floats(int64_t n_gaussians);
 size_t sssgs_bvh_workspace_bytes(int64_t n_gaussians);
 int sssgs_bvh_build(const sssgs_cfg* cfg, const sssgs_scene* scene, float* bvh, void* workspace,
                     size_t workspace_bytes, sssgs_stream stream);
-/* One ray per item of the pairs: vis_traced[n_items]. */
+/* One ray per item of the pairs: vis_traced[n_items] (overwritten), from a
+ * BVH of the same scene. SSSGS_ERR_INVALID_ARG for a missing buffer or a bvh
+ * not 16-byte aligned. */
 int sssgs_trace_visibility(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
                            const sssgs_scene* scene, const float* bvh, float* vis_traced, sssgs_stream stream);
 
@@ -381,7 +393,8 @@ int sssgs_trace_visibility(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, cons
  * Gaussian (degree 3, orthonormal, no Condon-Shortley phase; index l^2 + l + m).
  * Forward: vis_item[m] = clamp(sum_k c_k Y_k(w), 0, 1), w = unit(light - mu)
  * of item m's pair. Backward: from dvis_item[n_items] accumulates dvis_sh and
- * the mean gradient dmu (through w); zero where the clamp is active. */
+ * the mean gradient dmu (through w); zero where the clamp is active.
+ * SSSGS_ERR_INVALID_ARG for a missing buffer. */
 int sssgs_vis_sh_fwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const sssgs_scene* scene,
                      const float* vis_sh, float* vis_item, sssgs_stream stream);
 int sssgs_vis_sh_bwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const sssgs_scene* scene,
@@ -389,7 +402,8 @@ int sssgs_vis_sh_bwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n
 
 /* Ray-traced visibility loss per pair p: lambda_raytrace * mean over its items
  * of |vis_item - vis_traced| (the traced value a constant target). Adds
- * dL/dvis_item to dvis_item and the loss to d_loss[p]. */
+ * dL/dvis_item to dvis_item and the loss to d_loss[p] (caller-zeroed).
+ * SSSGS_ERR_INVALID_ARG for a missing buffer. */
 int sssgs_vis_loss(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs, const float* vis_item,
                    const float* vis_traced, float lambda_raytrace, float* dvis_item, float* d_loss,
                    sssgs_stream stream);
@@ -412,7 +426,8 @@ int sssgs_selftest_wait_timeout(int32_t* d_status, int64_t limit_cycles, sssgs_s
  * sssgs_composite_bwd on rec_colors -> sssgs_shade_gaussians_bwd (replaces
  * drec fields 6..8, dL/dcolour, by the gradients of the shaded attributes in
  * fields 7..19 and of the mean in 21..23) -> sssgs_mlp_bwd ->
- * sssgs_project_bwd. */
+ * sssgs_project_bwd. Errors: SSSGS_ERR_INVALID_ARG for a missing buffer,
+ * rec_colors aliasing rec, or a G-buffer / dgbuf not 16-byte aligned. */
 int sssgs_shade_gaussians_fwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
                               const sssgs_scene* scene, const float* rec, float* rec_colors, sssgs_stream stream);
 int sssgs_shade_gaussians_bwd(const sssgs_pair* h_pairs, const sssgs_pair* d_pairs, int n_pairs,
