@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             }
             __syncwarp();
             mine = wait_mma() && mine;
-            // epilogue, round 1
+            // epilogue after the first dH half
             if (last) {
                 if (wg == 0) {
                     float v[16];

@@ -119,7 +119,7 @@ def test_near_plane_and_opacity_culling():
     assert list(valid) == [False, False, True]    # behind z_near; o < 1/255; ok
 
 
-# ---------------------------------------------------------------- alpha (L170)
+# ---------------------------------------------------------------- alpha (Eq. 3)
 
 def test_lone_gaussian_peak_alpha_equals_opacity():
     """Mean on a pixel centre, no dilation: alpha = o there (Eq. 3 with one term)."""
