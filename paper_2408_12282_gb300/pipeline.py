@@ -463,11 +463,14 @@ class MultiLightRenderer:
         """Per-(view, light) images into self.img; with env_w (device
         float[n_views * n_lights]) the weighted sum per view into `out`
         (n_view_pixels x 3)."""
+        if env_w is not None and out is None:
+            raise ValueError("forward(env_w=...) writes the weighted image into `out`; pass it")
         self.forward_front(stream)
         v = self.views
         img = self.img if env_w is None else out
         B.render_ml_fwd(self.cfg, v.h, v.d, self.n_lights, self.lights, self.rec, self.mlp_out, self.vals,
                         self.ranges, self.gbuf, self.last, img, env_w, self.stats_fwd, stream)
+        self._pair_images_current = env_w is None
         return img
 
     def zero_grads(self):
@@ -494,7 +497,11 @@ class MultiLightRenderer:
         return self.vis_traced
 
     def backward(self, dimg=None, target=None, l1_scale=1.0, stream=None, lambda_raytrace=0.01):
-        """Upstream: dimg per (view, light) image, or the L1 loss against target."""
+        """Upstream: dimg per (view, light) image, or the L1 loss against target
+        (which reads the per-(view, light) images of the last forward)."""
+        if dimg is None and not getattr(self, "_pair_images_current", False):
+            raise ValueError("the L1 upstream needs the per-(view, light) images: run forward() without "
+                             "env_w before backward(target=...), or pass dimg")
         v, p = self.views, self.pairs
         self.zero_grads()
         B.render_ml_bwd(self.cfg, v.h, v.d, self.n_lights, self.lights, self.rec, self.mlp_out, self.vals,

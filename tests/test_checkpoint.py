@@ -63,3 +63,4 @@ def test_mismatched_checkpoints_are_refused(tmp_path):
     torch.save({"format": "something-else"}, tmp_path / "bad.pt")
     with pytest.raises(ValueError, match="not a"):
         PL.load_checkpoint(tmp_path / "bad.pt", r)
+
