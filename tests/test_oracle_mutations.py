@@ -70,6 +70,13 @@ C_MUTANTS = [
      "dg[0] += dp * (P[2] * dx + P[4] * dy);", FD),
     ("per-Gaussian shading upstream sign", "dF[c] = dimg[3 * (size_t)q + c];", "dF[c] = -dimg[3 * (size_t)q + c];",
      [(PF.test_fd_of_the_per_gaussian_shaded_render, (0,))]),
+    ("Smith derivative sign", "dni += dLi * (1 + (1 - a2) * ni / si);", "dni += dLi * (1 - (1 - a2) * ni / si);", FD),
+    ("SSS blend gradient term dropped", "dg[9] += gL[c] * (Ls[c] - (fs[c] + fd[c]) * Li * ni);",
+     "dg[9] += gL[c] * Ls[c];", FD),
+    ("depth gradient of the deferred position", "dg[0] += dot3(dXc, ray);", "dg[0] -= dot3(dXc, ray);", FD),
+    ("projected-mean gradient without focal length", "dt[0] += dg[0] * fx / tz;", "dt[0] += dg[0] / tz;", FD),
+    ("alpha gradient of the later sum", "da += dF[c] * (Ti * f[c] - S[c] / (1 - a));",
+     "da += dF[c] * (Ti * f[c] - S[c]);", FD),
     ("bin order by item reversed", "return (x->item > y->item) - (x->item < y->item);",
      "return (x->item < y->item) - (x->item > y->item);", [(PP.test_bin_sort_equals_python_stable_sort, ())]),
 ]
@@ -87,6 +94,14 @@ PY_MUTANTS = [
     (OV, "trace_visibility", "q = np.einsum(\"ni,ni->n\", op, op) - od * od / dd",
      "q = np.einsum(\"ni,ni->n\", op, op) + od * od / dd", [(PV.test_trace_peak_response_equals_dense_ray_sampling, ())]),
     (OV, "vis_loss", "lam * np.sign(d) / d.size", "lam * np.sign(d)", [(PV.test_vis_loss_gradient, ())]),
+    (OV, "vis_sh", "np.clip(u, 0.0, 1.0)", "np.clip(u, 0.0, 2.0)",
+     [(PV.test_vis_sh_equals_clamped_expansion_in_scipy_harmonics, ())]),
+    (OV, "rotation", "np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1)",
+     "np.stack([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z + w * y)], -1)",
+     [(PV.test_rotation_scale_reproduce_the_covariance, ())]),
+    (OL, "ssim_map", "(sxx + syy + SSIM_C2)", "(sxx + syy + SSIM_C1)", [(PP.test_ssim_equals_brute_force_window_sums, ())]),
+    (O, "input_grads", "dmu = dX[:, 0:3] + back_unit(wo, lo, dX[:, 3:6]) + back_unit(wi, li, dX[:, 6:9])",
+     "dmu = dX[:, 0:3] + back_unit(wi, li, dX[:, 3:6]) + back_unit(wi, li, dX[:, 6:9])", FD),
     (OL, "gaussian_window", "return w / w.sum()", "return w", [(PP.test_ssim_closed_forms, ())]),
     (OL, "ssim_map", "sxy = window_mean(x * y) - mx * my", "sxy = window_mean(x * y)",
      [(PP.test_ssim_equals_brute_force_window_sums, ())]),

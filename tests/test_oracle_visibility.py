@@ -59,6 +59,23 @@ def test_sh_gradient_equals_finite_differences():
         np.testing.assert_allclose(g[..., c], fd, atol=1e-7)
 
 
+def test_vis_sh_equals_clamped_expansion_in_scipy_harmonics():
+    """v = clamp(sum_k c_k Y_k(w), 0, 1) with w the unit direction to the
+    light and Y_k from scipy; coefficients large enough that both clamps act."""
+    rng = np.random.default_rng(6)
+    n = 300
+    mu = rng.normal(0, 0.5, (n, 3))
+    light = np.array([0.5, 1.0, 3.0])
+    sh = rng.normal(0, 0.8, (n, 16))
+    v, u = V.vis_sh(sh, mu, light)
+    w = (light[None, :] - mu) / np.linalg.norm(light[None, :] - mu, axis=1, keepdims=True)
+    Y = np.stack([_scipy_real_sh(l, m, w) for l in range(4) for m in range(-l, l + 1)], axis=1)
+    ref = np.einsum("nk,nk->n", sh, Y)
+    np.testing.assert_allclose(u, ref, atol=1e-12)
+    np.testing.assert_allclose(v, np.clip(ref, 0.0, 1.0), atol=1e-12)
+    assert (ref < 0).sum() > 20 and (ref > 1).sum() > 20
+
+
 def test_vis_sh_backward_equals_finite_differences():
     rng = np.random.default_rng(2)
     n = 12
