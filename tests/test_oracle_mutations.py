@@ -15,12 +15,15 @@ import pytest
 import oracle as O
 import oracle.losses as OL
 import oracle.visibility as OV
+import test_oracle_autograd as PA
 import test_oracle_forward_shading as PF
 import test_oracle_grad as PG
 import test_oracle_pins as PP
 import test_oracle_visibility as PV
 
 FD = [(PG.test_fd_scene_parameters_basic_mlp, (0,)), (PG.test_fd_scene_parameters_basic_mlp, (1,))]
+AG = [(PA.test_oracle_gradients_equal_dense_autograd, (0, False)),
+      (PA.test_oracle_gradients_equal_dense_autograd, (3, True))]
 
 # (name, exact source text, replacement, pins that must catch it)
 C_MUTANTS = [
@@ -57,26 +60,26 @@ C_MUTANTS = [
      "Lc[c] = sb * Ls[c] + (1 - sb) * (fs[c] + fd[c]) * Li;", [(PP.test_deferred_position_and_blend_closed_forms, ())]),
     ("coverage not applied", "out[c] = A * Lc[c];", "out[c] = Lc[c];",
      [(PP.test_deferred_position_and_blend_closed_forms, ())]),
-    ("opacity gradient without G", "dg[5] += da * cb[i].G;", "dg[5] += da;", FD),
-    ("final-T gradient sign", "double da = -dT * T / (1 - a);", "double da = dT * T / (1 - a);", FD),
-    ("roughness chain factor", "dg[7] += da2 * 4 * rb * rb * rb;", "dg[7] += da2 * 2 * rb * rb * rb;", FD),
-    ("sigmoid derivative", "d_logit[g] += dg[5] * o * (1 - o);", "d_logit[g] += dg[5] * o;", FD),
-    ("quaternion gradient sign", "- y * G[6] + x * G[7]);", "+ y * G[6] + x * G[7]);", FD),
-    ("covariance gradient factor", "dM[i * 3 + j] = 2 * acc;", "dM[i * 3 + j] = acc;", FD),
-    ("depth gradient sign", "dt[2] += ddepth[g];", "dt[2] -= ddepth[g];", FD),
+    ("opacity gradient without G", "dg[5] += da * cb[i].G;", "dg[5] += da;", AG + FD),
+    ("final-T gradient sign", "double da = -dT * T / (1 - a);", "double da = dT * T / (1 - a);", AG + FD),
+    ("roughness chain factor", "dg[7] += da2 * 4 * rb * rb * rb;", "dg[7] += da2 * 2 * rb * rb * rb;", AG + FD),
+    ("sigmoid derivative", "d_logit[g] += dg[5] * o * (1 - o);", "d_logit[g] += dg[5] * o;", AG + FD),
+    ("quaternion gradient sign", "- y * G[6] + x * G[7]);", "+ y * G[6] + x * G[7]);", AG + FD),
+    ("covariance gradient factor", "dM[i * 3 + j] = 2 * acc;", "dM[i * 3 + j] = acc;", AG + FD),
+    ("depth gradient sign", "dt[2] += ddepth[g];", "dt[2] -= ddepth[g];", AG + FD),
     ("pixel rectangle too small", "double ex = sqrt(2.0 * L * a) * (1.0 + 1e-9);", "double ex = sqrt(L * a) * (1.0 + 1e-9);",
      [(PP.test_brute_force_equals_tiled_bitwise_and_tile_size_independent, ())]),
     ("mean gradient uses the wrong conic entry", "dg[0] += dp * (P[2] * dx + P[3] * dy);",
-     "dg[0] += dp * (P[2] * dx + P[4] * dy);", FD),
+     "dg[0] += dp * (P[2] * dx + P[4] * dy);", AG + FD),
     ("per-Gaussian shading upstream sign", "dF[c] = dimg[3 * (size_t)q + c];", "dF[c] = -dimg[3 * (size_t)q + c];",
      [(PF.test_fd_of_the_per_gaussian_shaded_render, (0,))]),
-    ("Smith derivative sign", "dni += dLi * (1 + (1 - a2) * ni / si);", "dni += dLi * (1 - (1 - a2) * ni / si);", FD),
+    ("Smith derivative sign", "dni += dLi * (1 + (1 - a2) * ni / si);", "dni += dLi * (1 - (1 - a2) * ni / si);", AG + FD),
     ("SSS blend gradient term dropped", "dg[9] += gL[c] * (Ls[c] - (fs[c] + fd[c]) * Li * ni);",
-     "dg[9] += gL[c] * Ls[c];", FD),
-    ("depth gradient of the deferred position", "dg[0] += dot3(dXc, ray);", "dg[0] -= dot3(dXc, ray);", FD),
-    ("projected-mean gradient without focal length", "dt[0] += dg[0] * fx / tz;", "dt[0] += dg[0] / tz;", FD),
+     "dg[9] += gL[c] * Ls[c];", AG + FD),
+    ("depth gradient of the deferred position", "dg[0] += dot3(dXc, ray);", "dg[0] -= dot3(dXc, ray);", AG + FD),
+    ("projected-mean gradient without focal length", "dt[0] += dg[0] * fx / tz;", "dt[0] += dg[0] / tz;", AG + FD),
     ("alpha gradient of the later sum", "da += dF[c] * (Ti * f[c] - S[c] / (1 - a));",
-     "da += dF[c] * (Ti * f[c] - S[c]);", FD),
+     "da += dF[c] * (Ti * f[c] - S[c]);", AG + FD),
     ("bin order by item reversed", "return (x->item > y->item) - (x->item < y->item);",
      "return (x->item < y->item) - (x->item > y->item);", [(PP.test_bin_sort_equals_python_stable_sort, ())]),
 ]
