@@ -109,7 +109,11 @@ PY_MUTANTS = [
     (OL, "ssim_map", "sxy = window_mean(x * y) - mx * my", "sxy = window_mean(x * y)",
      [(PP.test_ssim_equals_brute_force_window_sums, ())]),
     (OL, "ssim", "d_sxy = dS_dA2 * 2", "d_sxy = dS_dA2",
-     [(PP.test_image_and_incident_loss_gradients_match_finite_differences, ())]),
+     [(PP.test_ssim_and_image_loss_gradients_equal_conv2d_autograd, ()),
+      (PP.test_image_and_incident_loss_gradients_match_finite_differences, ())]),
+    (OL, "ssim", "g = window_mean(d_mx) + 2 * x * window_mean(d_sxx) + y * window_mean(d_sxy)",
+     "g = window_mean(d_mx) + x * window_mean(d_sxx) + y * window_mean(d_sxy)",
+     [(PP.test_ssim_and_image_loss_gradients_equal_conv2d_autograd, ())]),
     (OL, "image_loss", "- lam * gs", "+ lam * gs", [(PP.test_image_and_incident_loss_gradients_match_finite_differences, ())]),
     (OL, "incident_loss", "return loss, s * (L_in < 1.0), -s", "return loss, s, -s",
      [(PP.test_image_and_incident_loss_gradients_match_finite_differences, ())]),

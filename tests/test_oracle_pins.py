@@ -615,6 +615,33 @@ def test_image_and_incident_loss_gradients_match_finite_differences():
     assert np.allclose(dv, -0.02 / 4 * np.array([-1, 1, 1, -1]))
 
 
+def test_ssim_and_image_loss_gradients_equal_conv2d_autograd():
+    """SSIM with torch's conv2d (11 x 11 Gaussian window, zero padding) in
+    FP64 and autograd: the oracle's SSIM, image loss and their gradients,
+    every entry of a ragged 13 x 17 image."""
+    import torch
+    import torch.nn.functional as Fn
+    rng = np.random.default_rng(21)
+    x, y = rng.uniform(0, 1, (13, 17, 3)), rng.uniform(0, 1, (13, 17, 3))
+    w1 = torch.from_numpy(O.losses.gaussian_window())
+    win = (w1[:, None] * w1[None, :]).expand(3, 1, 11, 11).contiguous()
+    xt = torch.from_numpy(x).permute(2, 0, 1)[None].clone().requires_grad_(True)
+    yt = torch.from_numpy(y).permute(2, 0, 1)[None]
+    wm = lambda a: Fn.conv2d(a, win, padding=5, groups=3)
+    mx, my = wm(xt), wm(yt)
+    sxx, syy, sxy = wm(xt * xt) - mx * mx, wm(yt * yt) - my * my, wm(xt * yt) - mx * my
+    C1, C2 = O.losses.SSIM_C1, O.losses.SSIM_C2
+    S = ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    lam = 0.2
+    loss = (1 - lam) * (xt - yt).abs().mean() + lam * (1 - S.mean())
+    loss.backward()
+    s_val, _ = O.ssim(x, y)
+    l_val, g = O.image_loss(x, y, lam)
+    assert s_val == pytest.approx(float(S.mean().detach()), rel=1e-13)
+    assert l_val == pytest.approx(float(loss.detach()), rel=1e-13)
+    np.testing.assert_allclose(g, xt.grad[0].permute(1, 2, 0).numpy(), rtol=1e-10, atol=1e-14)
+
+
 # ---------------------------------------------------------------- binning / sort
 
 def test_bin_sort_equals_python_stable_sort():
