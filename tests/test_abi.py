@@ -140,3 +140,31 @@ def test_later_entry_points_reject_bad_arguments():
     assert lib.sssgs_shade_gaussians_fwd(h, A, 1, ctypes.byref(sc), A, A, None) == INVALID
     assert lib.sssgs_colors_to_image(h, 1, A + 4, A, None) == INVALID   # G-buffer not 16-byte aligned
     assert lib.sssgs_colors_to_image_bwd(h, 0, A, A, None) == INVALID
+
+
+def _prototypes():
+    """name -> (parameter count, return type) of every prototype in the header."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*(?:\s*\*)?)\s+(sssgs_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        ret, name, params = m.group(1).strip(), m.group(2), m.group(3).strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        out[name] = (n, ret)
+    return out
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every ctypes signature of the binding has the header's parameter count
+    and a return type of the header's kind (int codes, sizes, strings)."""
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    kinds = {"int": ctypes.c_int, "size_t": ctypes.c_size_t, "int64_t": ctypes.c_int64,
+             "uint64_t": ctypes.c_uint64, "void": None}
+    for name, (args, res) in B._SIGS.items():
+        n, ret = protos[name]
+        assert len(args) == n, (name, len(args), n)
+        if ret.replace(" ", "") == "char*":          # const char* (the qualifier is not captured)
+            assert res is ctypes.c_char_p, name
+        else:
+            assert res is kinds[ret], (name, ret, res)
