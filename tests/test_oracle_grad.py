@@ -227,3 +227,72 @@ def test_fd_training_objective_of_app_e():
     hidden = np.setdiff1d(np.arange(sc.N), live)
     if hidden.size:
         assert np.allclose(r["grads"]["vis"][hidden], dv[hidden])
+
+
+def test_fd_config2_size_64_parameters():
+    """The analytic backward at a realistic list depth: the 100K-Gaussian blob
+    at 512x512 with its 9-64-64-64-4 network, 64 random parameters (36 scene
+    parameters of Gaussians that reach the crop, 28 network weights and
+    biases with a nonzero gradient). The loss is sum(dimg * image) over a
+    56 x 48 pixel crop that holds lit surface, shadow and the silhouette
+    (lists of ~60-140 contributions per pixel); only those pixels are
+    rendered, which leaves the crop's values exact. v enters neither the
+    network nor the shading of this configuration, so it is not sampled."""
+    wl = sg.make_workload("c2")
+    sc, pair, spec = wl.scenes[0], wl.pairs[0], wl.mlp
+    pix = O.all_pixels(pair.W, pair.H)
+    crop = pix[(pix[:, 0] >= 112) & (pix[:, 0] < 168) & (pix[:, 1] >= 40) & (pix[:, 1] < 88)].astype(np.int32)
+    dimg = sg.random_dimg(5, crop.shape[0])
+    r = O.render_pair(sc, pair, spec, pixels=crop, dimg=dimg)
+    assert r["ncontrib"].mean() > 50 and r["ncontrib"].max() > 200
+    assert 0.5 < (r["ncontrib"] > 0).mean() < 1.0           # silhouette inside the crop
+
+    def loss():
+        q = O.render_pair(sc, pair, spec, pixels=crop)
+        return float((q["img"] * dimg).sum()), q["ncontrib"].copy(), q["margin"][:, 2].copy()
+
+    _, nc0, cl0 = loss()
+    rng = np.random.default_rng(2)
+    picks = []
+    for name in ["mu", "log_s", "quat", "logit_o", "normal", "base", "rough", "metal", "sss"]:
+        gg = r["grads"][name]
+        live = np.flatnonzero(np.abs(gg.reshape(gg.shape[0], -1)).sum(1) > 0)
+        assert live.size > 100, name
+        arr = getattr(sc, name)
+        for _ in range(4):
+            g = int(rng.choice(live))
+            picks.append((name, (g,) if arr.ndim == 1 else (g, int(rng.integers(arr.shape[1])))))
+    for l in range(len(spec.weights)):
+        for kind, n_pick in (("W", 5), ("b", 2)):
+            ana = (r["dW"] if kind == "W" else r["db"])[l]
+            nz = np.argwhere(ana != 0)
+            for k in rng.choice(len(nz), n_pick, replace=False):
+                picks.append((f"{kind}{l}", tuple(int(x) for x in nz[k])))
+    assert len(picks) == 64
+    used, bad, worst = 0, [], 0.0
+    for name, idx in picks:
+        if name[0] in "Wb" and name[1:].isdigit():
+            l = int(name[1:])
+            arr = (spec.weights if name[0] == "W" else spec.biases)[l]
+            ana = (r["dW"] if name[0] == "W" else r["db"])[l][idx]
+        else:
+            arr = getattr(sc, name)
+            ana = r["grads"][name][idx]
+        x0 = float(arr[idx])
+        h = 1e-6 * max(1.0, abs(x0))
+        arr[idx] = x0 + h
+        lp, ncp, clp = loss()
+        arr[idx] = x0 - h
+        lm, ncm, clm = loss()
+        arr[idx] = x0
+        if not (np.array_equal(ncp, nc0) and np.array_equal(ncm, nc0)
+                and np.array_equal(clp, cl0) and np.array_equal(clm, cl0)):
+            continue                    # a decision flipped inside +-h: a jump, not a derivative
+        used += 1
+        fd = (lp - lm) / (2 * h)
+        rel = abs(fd - ana) / max(abs(fd), abs(ana), 1e-3)
+        worst = max(worst, rel)
+        if rel > 2e-5:
+            bad.append((name, idx, fd, ana))
+    assert used >= 56, used
+    assert not bad, bad[:5]
