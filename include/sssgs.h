@@ -254,11 +254,16 @@ int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_
  * loads the library keeps until the process exits.
  * Limits: n_items <= SSSGS_STATIC_MAX_ITEMS and capacity <=
  * SSSGS_STATIC_MAX_INSTANCES; larger problems return SSSGS_ERR_TOO_LARGE
- * before anything is launched.
+ * before anything is launched and leave every output untouched. A missing
+ * buffer, a negative capacity or a pair table with negative counts or no
+ * tiles returns SSSGS_ERR_INVALID_ARG, also before any launch.
  * The first call on a device (with that device current) looks up the
- * scratch address; make it before any stream capture. All calls share the
- * scratch, which keeps the last call's contents (nothing in it needs to start
- * at zero); calls that overlap on the GPU race, so serialise them. */
+ * scratch address and caches it; make it before any stream capture. The
+ * cached address belongs to the device's primary context: after
+ * cudaDeviceReset do not call this entry point again in that process. All
+ * calls share the scratch, which keeps the last call's contents (nothing in
+ * it needs to start at zero); calls that overlap on the GPU race, so
+ * serialise them. */
 #define SSSGS_STATIC_MAX_ITEMS 65536
 #define SSSGS_STATIC_MAX_INSTANCES 524288
 #define SSSGS_STATIC_SCRATCH_BYTES 9437184

@@ -278,6 +278,7 @@ def bin_sort(cfg: Cfg, pairs, d_pairs, rec, rect, capacity: int, vals, ranges, d
 
 STATIC_MAX_ITEMS = 65536
 STATIC_MAX_INSTANCES = 524288
+ERR_INVALID_ARG = -1
 ERR_TOO_LARGE = -5
 
 

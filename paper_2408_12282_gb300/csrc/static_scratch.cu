@@ -11,7 +11,10 @@
 // exits. In host code the array's name only stands for the symbol, not for a
 // device address, so its address is looked up with cudaGetSymbolAddress, once
 // per device, on the first call made while that device is current, and cached.
-// Make that first call before any stream capture begins.
+// Make that first call before any stream capture begins. The cached address
+// belongs to the device's primary context: after cudaDeviceReset the array
+// lives at a new address, so do not call this entry point again in that
+// process after a reset.
 //
 // All calls share the one array and it keeps whatever the last call wrote.
 // Nothing in it has to start at zero: every region is written by the sort
@@ -57,11 +60,14 @@ extern "C" int sssgs_bin_sort_static(const sssgs_cfg* cfg, const sssgs_pair* h_p
                                      sssgs_stream stream) {
     if (!cfg || !h_pairs || !d_pairs || n_pairs <= 0 || !rec || !rect || !vals || !ranges || !d_count)
         return SSSGS_ERR_INVALID_ARG;
-    int64_t n_items = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
-    if (n_items > SSSGS_STATIC_MAX_ITEMS || capacity < 0 || capacity > SSSGS_STATIC_MAX_INSTANCES)
-        return SSSGS_ERR_TOO_LARGE;
-    int32_t n_tiles = h_pairs[n_pairs - 1].tile_offset + h_pairs[n_pairs - 1].tiles_x * h_pairs[n_pairs - 1].tiles_y;
-    if (sssgs_bin_workspace_bytes(n_items, capacity, n_tiles) > kScratchBytes) return SSSGS_ERR_TOO_LARGE;
+    const sssgs_pair& lastp = h_pairs[n_pairs - 1];
+    const int64_t n_items = lastp.item_offset + lastp.g_count;
+    const int64_t n_tiles = (int64_t)lastp.tile_offset + (int64_t)lastp.tiles_x * lastp.tiles_y;
+    // a pair table that sssgs_plan did not fill (negative counts or offsets)
+    if (lastp.item_offset < 0 || lastp.g_count < 0 || n_tiles <= 0 || n_tiles > INT32_MAX || capacity < 0)
+        return SSSGS_ERR_INVALID_ARG;
+    if (n_items > SSSGS_STATIC_MAX_ITEMS || capacity > SSSGS_STATIC_MAX_INSTANCES) return SSSGS_ERR_TOO_LARGE;
+    if (sssgs_bin_workspace_bytes(n_items, capacity, (int32_t)n_tiles) > kScratchBytes) return SSSGS_ERR_TOO_LARGE;
     void* ws = scratch_on_current_device();
     if (!ws) return SSSGS_ERR_CUDA;
     return sssgs_bin_sort(cfg, h_pairs, d_pairs, n_pairs, rec, rect, capacity, vals, ranges, d_count, d_status, ws,
