@@ -79,12 +79,12 @@ enum {
  * (d/dmx ... d/dvis); its fields 21..23 hold dL/dmu of the per-Gaussian
  * shading (sssgs_shade_gaussians_bwd) and are zero otherwise. */
 
-/* Render conventions. Defaults (sssgs_cfg_default): tile 16, dilation 0.3 px^2,
+/* Render conventions. Defaults (sssgs_cfg_default): tile 16, batch 32, dilation 0.3 px^2,
  * det_eps 1e-6 px^4, z_near 0.2, alpha_min 1/255, alpha_max 0.99, T_min 1e-4,
  * A_eps 1e-6. All values are float32. */
 typedef struct sssgs_cfg {
     int32_t tile;        /* tile edge in pixels: 8, 16 or 32 */
-    int32_t reserved;    /* must be 0 */
+    int32_t batch;       /* splats staged per round by the one-warp render kernels: 32 or 64 (0 = 32) */
     float dilation;      /* low-pass dilation added to the 2D covariance diagonal */
     float det_eps;       /* cull if det(Sigma') <= det_eps (guards the conic inverse) */
     float z_near;        /* cull if view depth < z_near */
@@ -313,6 +313,70 @@ int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
                      const float* gbuf, const uint32_t* last, const float* img,
                      const float* dimg, const float* target, const float* weight, float l1_scale,
                      float* drec, uint64_t* d_stats, sssgs_stream stream);
+
+/* Schedule autotuner. The paper renders with the tile rasterizer of 3D
+ * Gaussian splatting (Sec. 4.1 "Implementation Details") and fixes no tile
+ * shape; here the tile edge (cfg.tile: 8, 16, 32) and the per-block splat
+ * batch of the one-warp render kernels (cfg.batch: 32, 64) are chosen per
+ * scene by measurement. For the pairs of one scene, every candidate
+ * (tiles[i], batches[j]) runs the stages whose work depends on the schedule
+ * -- sssgs_project_fwd, sssgs_bin_sort, sssgs_render_fwd and sssgs_render_bwd
+ * with the upstream gradient dimg -- once to warm up and check the instance
+ * count, then `reps` times between two CUDA events on `stream`.
+ * results[i * n_batches + j] receives the candidate's mean milliseconds per
+ * pass (ms, -1 if not run), its instance count and status (0, or
+ * SSSGS_STATUS_CAPACITY when its instances exceed buf->capacity; enlarge the
+ * buffers and call again for it); *best becomes *base with the fastest
+ * candidate's tile and batch.
+ * h_pairs: the scene's pairs with the caller-filled fields (camera, light,
+ * W, H, g_begin, g_count); the layout fields are planned per candidate and
+ * the planned table is copied into buf->d_pairs. mlp_out: the network output
+ * of these pairs (sssgs_mlp_fwd; it does not depend on the schedule).
+ * Buffers (device, the caller's scratch; their contents are overwritten):
+ * sized for the largest candidate -- ranges for max_tiles tiles (the smallest
+ * tile edge), vals for `capacity` instances and the bin/sort workspace for
+ * (n_items, capacity, max_tiles); records, rectangles, G-buffer, last index,
+ * image and gradient records for the pairs' items and pixels.
+ * Blocking: the call synchronises `stream` (it reads the instance counts and
+ * the events), so it runs outside stream capture, at set-up.
+ * Errors: SSSGS_ERR_INVALID_ARG for a missing buffer, reps outside 1..1000, a
+ * batch other than 32 or 64, or a candidate needing more than max_tiles
+ * tiles; SSSGS_ERR_WORKSPACE for a bin/sort workspace too small for a
+ * candidate, or when no candidate fits `capacity`; errors of the stages
+ * above as they return them. */
+typedef struct sssgs_tune_buffers {
+    sssgs_pair* d_pairs;        /* n_pairs entries, 16-byte aligned */
+    float* rec;                 /* n_items * SSSGS_REC */
+    int32_t* rect;              /* n_items * 4 */
+    uint32_t* vals;             /* capacity */
+    int64_t capacity;
+    uint32_t* ranges;           /* max_tiles * 2 */
+    int32_t max_tiles;
+    int32_t pad;
+    int64_t* d_count;
+    int32_t* d_status;
+    void* workspace;            /* bin/sort workspace, 256-byte aligned */
+    size_t workspace_bytes;
+    float* gbuf;                /* n_pixels * SSSGS_GBUF */
+    uint32_t* last;             /* n_pixels */
+    float* img;                 /* n_pixels * 3 */
+    float* drec;                /* n_items * SSSGS_REC (accumulated into; scratch) */
+    const float* dimg;          /* n_pixels * 3 upstream gradient */
+} sssgs_tune_buffers;
+
+typedef struct sssgs_tune_result {
+    int32_t tile, batch;
+    int32_t status;             /* 0 measured, SSSGS_STATUS_CAPACITY not run */
+    int32_t reps;
+    int64_t instances;
+    float ms;                   /* mean milliseconds per pass of the four stages; -1 if not run */
+    float reserved;
+} sssgs_tune_result;
+
+int sssgs_autotune(const sssgs_cfg* base, const sssgs_pair* h_pairs, int n_pairs, const sssgs_scene* scene,
+                   const float* mlp_out, const sssgs_tune_buffers* buf, const int32_t* tiles, int n_tiles,
+                   const int32_t* batches, int n_batches, int reps, sssgs_tune_result* results,
+                   sssgs_cfg* best, sssgs_stream stream);
 
 /* Many lights per view. A training batch of the paper's light-stage data
  * holds one camera view under several point lights (Sec. 4.1 "Dataset": fixed

@@ -27,7 +27,7 @@ class SSSGSError(RuntimeError):
 
 
 class Cfg(ctypes.Structure):
-    _fields_ = [("tile", c_i32), ("reserved", c_i32), ("dilation", c_f32), ("det_eps", c_f32),
+    _fields_ = [("tile", c_i32), ("batch", c_i32), ("dilation", c_f32), ("det_eps", c_f32),
                 ("z_near", c_f32), ("alpha_min", c_f32), ("alpha_max", c_f32), ("T_min", c_f32),
                 ("A_eps", c_f32)]
 
@@ -66,6 +66,21 @@ class MLPGrad(ctypes.Structure):
     _fields_ = [("W", c_vp * MAX_LAYERS), ("b", c_vp * MAX_LAYERS)]
 
 
+class TuneBuffers(ctypes.Structure):
+    _fields_ = [("d_pairs", c_vp), ("rec", c_vp), ("rect", c_vp), ("vals", c_vp), ("capacity", c_i64),
+                ("ranges", c_vp), ("max_tiles", c_i32), ("pad", c_i32), ("d_count", c_vp), ("d_status", c_vp),
+                ("workspace", c_vp), ("workspace_bytes", ctypes.c_size_t), ("gbuf", c_vp), ("last", c_vp),
+                ("img", c_vp), ("drec", c_vp), ("dimg", c_vp)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tile", c_i32), ("batch", c_i32), ("status", c_i32), ("reps", c_i32), ("instances", c_i64),
+                ("ms", c_f32), ("reserved", c_f32)]
+
+
+assert ctypes.sizeof(TuneResult) == 32
+
+
 _LIB = None
 
 _SIGS = {
@@ -101,6 +116,10 @@ _SIGS = {
                           c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "sssgs_render_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp,
                           c_vp, c_vp, c_vp, c_vp, c_vp, c_f32, c_vp, c_vp, c_vp], ctypes.c_int),
+    "sssgs_autotune": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), ctypes.c_int, ctypes.POINTER(Scene), c_vp,
+                        ctypes.POINTER(TuneBuffers), ctypes.POINTER(c_i32), ctypes.c_int, ctypes.POINTER(c_i32),
+                        ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult), ctypes.POINTER(Cfg), c_vp],
+                       ctypes.c_int),
     "sssgs_project_bwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.POINTER(Scene),
                            c_vp, c_vp, ctypes.POINTER(SceneGrad), c_vp], ctypes.c_int),
     "sssgs_render_ml_fwd": ([ctypes.POINTER(Cfg), ctypes.POINTER(Pair), c_vp, ctypes.c_int, ctypes.c_int, c_vp,
@@ -279,6 +298,7 @@ def bin_sort(cfg: Cfg, pairs, d_pairs, rec, rect, capacity: int, vals, ranges, d
 STATIC_MAX_ITEMS = 65536
 STATIC_MAX_INSTANCES = 524288
 ERR_INVALID_ARG = -1
+ERR_WORKSPACE = -4
 ERR_TOO_LARGE = -5
 
 
@@ -325,6 +345,26 @@ def render_bwd(cfg: Cfg, pairs, d_pairs, rec, vals, ranges, gbuf, last, img, dim
                                            _p(ranges), _p(gbuf), _p(last), _p(img), _p(dimg), _p(target),
                                            _p(weight), float(l1_scale), _p(drec), _p(stats), _stream(stream)),
            "sssgs_render_bwd")
+
+
+def autotune(base: Cfg, pairs, scene: Scene, mlp_out, buffers: TuneBuffers, tiles, batches, reps: int,
+             stream=None):
+    """Time every (tile, batch) candidate of the schedule-dependent stages on
+    one scene's pairs (sssgs_autotune). Returns (best Cfg, list of
+    TuneResult); best is None when no candidate's instances fitted the
+    buffers' capacity (each result then holds its instance count). Blocking;
+    call outside stream capture."""
+    tl = (c_i32 * len(tiles))(*[int(t) for t in tiles])
+    bl = (c_i32 * len(batches))(*[int(b) for b in batches])
+    res = (TuneResult * (len(tiles) * len(batches)))()
+    best = Cfg()
+    rc = load_library().sssgs_autotune(ctypes.byref(base), pairs, len(pairs), ctypes.byref(scene), _p(mlp_out),
+                                       ctypes.byref(buffers), tl, len(tiles), bl, len(batches), int(reps), res,
+                                       ctypes.byref(best), _stream(stream))
+    if rc == ERR_WORKSPACE and all(r.status == STATUS_CAPACITY for r in res):
+        return None, list(res)       # no candidate fitted the capacity: results hold the instance counts
+    _check(rc, "sssgs_autotune")
+    return best, list(res)
 
 
 def mlp_bwd_strided(mlp: MLP, pairs, d_pairs, scene: Scene, dout, dout_stride: int, grad: MLPGrad, dx_items,

@@ -30,7 +30,7 @@ extern "C" const char* sssgs_strerror(int code) {
 extern "C" void sssgs_cfg_default(sssgs_cfg* c) {
     if (!c) return;
     c->tile = 16;
-    c->reserved = 0;
+    c->batch = 32;
     c->dilation = 0.3f;
     c->det_eps = 1e-6f;
     c->z_near = 0.2f;

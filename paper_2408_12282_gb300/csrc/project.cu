@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(sssgs_cfg cfg, const sssgs_
 using namespace sssgs;
 
 static bool cfg_ok(const sssgs_cfg* c) {
-    return c && (c->tile == 8 || c->tile == 16 || c->tile == 32) && c->reserved == 0 &&
+    return c && (c->tile == 8 || c->tile == 16 || c->tile == 32) && (c->batch == 0 || c->batch == 32 || c->batch == 64) &&
            c->alpha_min > 0.f && c->alpha_max <= 1.f && c->alpha_min < c->alpha_max && c->T_min > 0.f;
 }
 

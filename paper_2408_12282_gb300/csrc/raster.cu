@@ -20,104 +20,31 @@
 
 namespace sssgs {
 
-// ---------------------------------------------------------------- composite forward
-
-template <int TILE, bool SHADE>
-__global__ void __launch_bounds__(TILE * TILE) k_composite_fwd(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
-                                                               int n_pairs, const float4* __restrict__ rec,
-                                                               const uint32_t* __restrict__ vals,
-                                                               const uint2* __restrict__ ranges,
-                                                               float* __restrict__ gbuf, uint32_t* __restrict__ last,
-                                                               float* __restrict__ img,
-                                                               unsigned long long* __restrict__ stats) {
-    constexpr int B = TILE * TILE;
-    extern __shared__ float4 s_rec[];            // [6][B], then sub-tile masks
-    uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_rec + 6 * B);
-    __shared__ __align__(16) sssgs_pair sP;
-    const int tile = blockIdx.x;
-    const uint32_t wbit = 1u << (threadIdx.x >> 5);
-    load_pair_shared(pairs, n_pairs, tile, &sP);
-    const TilePix px = tile_pixel(sP, tile, TILE);
-    const float fx = px.i + 0.5f, fy = px.j + 0.5f;
-    const uint2 rg = ranges[tile];
-    const float a_min = cfg.alpha_min, a_max = cfg.alpha_max, T_min = cfg.T_min;
-    bool done = !px.inside;
-    float T = 1.f;
-    float F[SSSGS_NF];
-#pragma unroll
-    for (int k = 0; k < SSSGS_NF; ++k) F[k] = 0.f;
-    uint32_t lastc = 0, n_use = 0, stop = done ? rg.x : rg.y;
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += B) {
-        if (__syncthreads_count(done) == B) break;
-        const uint32_t idx = b0 + threadIdx.x;
-        if (idx < rg.y) {
-            const float4* r = rec + 6 * (int64_t)vals[idx];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) s_rec[q * B + threadIdx.x] = __ldg(r + q);
-            s_mask[threadIdx.x] =
-                subtile_mask<TILE>(sP, tile, s_rec[threadIdx.x], s_rec[B + threadIdx.x], s_rec[5 * B + threadIdx.x]);
-        }
-        __syncthreads();
-        const int nb = min(B, (int)(rg.y - b0));
-        if (__any_sync(SSSGS_FULL, !done) && !done) {
-            for (int k = 0; k < nb; ++k) {
-                if (!(s_mask[k] & wbit)) continue;       // splat misses this warp's sub-tile
-                const float4 g0 = s_rec[k], g1 = s_rec[B + k];
-                const AlphaEval e = eval_alpha(g0, g1, fx, fy, a_min, a_max);
-                if (!e.use) continue;
-                const float Tn = T * (1.f - e.alpha);
-                if (Tn < T_min) { done = true; stop = b0 + k + 1; break; }
-                ++n_use;
-                const float w = T * e.alpha;
-                const float4 g2 = s_rec[2 * B + k], g3 = s_rec[3 * B + k], g4 = s_rec[4 * B + k];
-                const float g5 = s_rec[5 * B + k].x;
-                F[0] += w * g1.z;  F[1] += w * g1.w;  F[2] += w * g2.x;  F[3] += w * g2.y;
-                F[4] += w * g2.z;  F[5] += w * g2.w;  F[6] += w * g3.x;  F[7] += w * g3.y;
-                F[8] += w * g3.z;  F[9] += w * g3.w;  F[10] += w * g4.x; F[11] += w * g4.y;
-                F[12] += w * g4.z; F[13] += w * g4.w; F[14] += w * g5;
-                T = Tn;
-                lastc = b0 + k + 1;
-            }
-        }
-    }
-    if (stats) {   // contributions, and list positions each pixel considered
-        unsigned long long u = n_use, v = stop - rg.x;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            u += __shfl_xor_sync(SSSGS_FULL, u, o);
-            v += __shfl_xor_sync(SSSGS_FULL, v, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(stats, u);
-            atomicAdd(stats + 1, v);
-        }
-    }
-    if (!px.inside) return;
-    float4* go = reinterpret_cast<float4*>(gbuf + SSSGS_GBUF * px.pix);
-    go[0] = make_float4(F[0], F[1], F[2], F[3]);
-    go[1] = make_float4(F[4], F[5], F[6], F[7]);
-    go[2] = make_float4(F[8], F[9], F[10], F[11]);
-    go[3] = make_float4(F[12], F[13], F[14], T);
-    last[px.pix] = lastc;
-    if (SHADE) {
-        float o[3];
-        shade_px<false>(F, T, fx, fy, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
-        img[3 * px.pix] = o[0];
-        img[3 * px.pix + 1] = o[1];
-        img[3 * px.pix + 2] = o[2];
-    }
-}
-
 // ---------------------------------------------------------------- composite forward, one warp per sub-tile
 //
-// Used for 16 x 16 tiles. Each block is a single warp that owns an 8 x (4 PX)
-// sub-tile, PX vertically adjacent pixels per lane; there is no block barrier
-// and a warp stops as soon as its own pixels are done. The tile's list is
-// walked front to back in batches of 32 splats with the same cp.async double
-// buffer and ballot of the sub-tile test as the backward below.
+// Each block is a single warp that owns an 8 x 4 sub-tile of a TILE x TILE
+// tile (TILE = 8, 16 or 32: (TILE/8) x (TILE/4) sub-tiles per tile), one
+// pixel per lane; there is no block barrier and a warp stops as soon as its
+// own pixels are done. The tile's list is walked front to back in batches of
+// BATCH splats (32 or 64: one or two per lane) through a cp.async double
+// buffer in shared memory; a ballot of each lane's exact sub-tile test lists
+// the splats the warp visits.
 
+// Sub-tile origin of block `blk` for SW x SH sub-tiles of TILE x TILE tiles.
+template <int TILE, int SW, int SH>
+struct SubTile {
+    static constexpr int PER_ROW = TILE / SW, NSUB = (TILE / SW) * (TILE / SH);
+    int tile, bx, by;
+    __device__ __forceinline__ SubTile(int blk, const sssgs_pair& P) {
+        tile = blk / NSUB;
+        const int sub = blk - tile * NSUB;
+        const int lt = tile - P.tile_offset;
+        bx = (lt % P.tiles_x) * TILE + (sub % PER_ROW) * SW;
+        by = (lt / P.tiles_x) * TILE + (sub / PER_ROW) * SH;
+    }
+};
 
-template <int PX, bool SHADE>
+template <int TILE, int BATCH, bool SHADE>
 __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                              int n_pairs, const float4* __restrict__ rec,
                                                              const uint32_t* __restrict__ vals,
@@ -125,116 +52,115 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
                                                              float* __restrict__ gbuf, uint32_t* __restrict__ last,
                                                              float* __restrict__ img,
                                                              unsigned long long* __restrict__ stats) {
-    constexpr int TILE = 16, SH = 4 * PX, NSUB = 2 * (TILE / SH);
+    constexpr int R = BATCH / 32;                 // records per lane per batch
+    using ST = SubTile<TILE, 8, 4>;
     constexpr uint32_t NONE = 0xFFFFFFFFu;
-    __shared__ __align__(16) float4 s_rec[2][6][32];
+    __shared__ __align__(16) float4 s_rec[2][6][BATCH];
     __shared__ __align__(16) sssgs_pair sP;
-    const int tile = blockIdx.x / NSUB, sub = blockIdx.x % NSUB;
     const int lane = threadIdx.x;
     if (lane < 8) {
-        const int pi = pair_of_tile(pairs, n_pairs, tile);
+        const int pi = pair_of_tile(pairs, n_pairs, (int)(blockIdx.x / ST::NSUB));
         reinterpret_cast<float4*>(&sP)[lane] = reinterpret_cast<const float4*>(pairs + pi)[lane];
     }
     __syncwarp();
-    const int lt = tile - sP.tile_offset;
-    const int bx = (lt % sP.tiles_x) * TILE + (sub & 1) * 8, by = (lt / sP.tiles_x) * TILE + (sub >> 1) * SH;
-    const int i = bx + (lane & 7), j0 = by + (lane >> 3) * PX;
+    const ST st(blockIdx.x, sP);
+    const int tile = st.tile, bx = st.bx, by = st.by;
+    const int i = bx + (lane & 7), j = by + (lane >> 3);
     const uint2 rg = ranges[tile];
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max, T_min = cfg.T_min;
     const float x0 = bx + 0.5f, y0 = by + 0.5f;
-    float T[PX], F[PX][SSSGS_NF];
-    uint32_t lastc[PX], stop[PX];
-    bool done[PX];
+    const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+    float T = 1.f, F[SSSGS_NF];
+    uint32_t lastc = 0;
+    bool done = !(i < sP.W && j < sP.H);
+    uint32_t stop = done ? rg.x : rg.y;
 #pragma unroll
-    for (int q = 0; q < PX; ++q) {
-        T[q] = 1.f;
-        lastc[q] = 0;
-        done[q] = !(i < sP.W && j0 + q < sP.H);
-        stop[q] = done[q] ? rg.x : rg.y;
-#pragma unroll
-        for (int k = 0; k < SSSGS_NF; ++k) F[q][k] = 0.f;
-    }
+    for (int k = 0; k < SSSGS_NF; ++k) F[k] = 0.f;
     uint32_t n_use = 0;
-    const int nb = (int)((rg.y - rg.x + 31) >> 5);
-    auto entry = [&](int t) -> uint32_t {
+    const int nb = (int)((rg.y - rg.x + BATCH - 1) / BATCH);
+    auto entry = [&](int t, int r) -> uint32_t {
         if (t >= nb) return NONE;
-        const uint32_t idx = rg.x + 32u * t + lane;
+        const uint32_t idx = rg.x + (uint32_t)BATCH * t + 32u * r + lane;
         return idx < rg.y ? vals[idx] : NONE;
     };
-    auto fetch = [&](uint32_t item, int buf) {
-        if (item != NONE) {
-            const float4* r = rec + 6 * (int64_t)item;
+    auto fetch = [&](const uint32_t* item, int buf) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + q);
+        for (int r = 0; r < R; ++r) {
+            if (item[r] != NONE) {
+                const float4* src = rec + 6 * (int64_t)item[r];
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][32 * r + lane]), src + q);
+            }
         }
         cp_async_commit();
     };
-    bool all_done = true;
+    if (nb > 0 && !__all_sync(SSSGS_FULL, done)) {
+        uint32_t it0[R], it1[R], it2[R];
 #pragma unroll
-    for (int q = 0; q < PX; ++q) all_done = all_done && done[q];
-    if (nb > 0 && !__all_sync(SSSGS_FULL, all_done)) {
-        uint32_t it0 = entry(0);
+        for (int r = 0; r < R; ++r) it0[r] = entry(0, r);
         fetch(it0, 0);
-        uint32_t it1 = entry(1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) it1[r] = entry(1, r);
         for (int t = 0; t < nb; ++t) {
             const int buf = t & 1;
             fetch(it1, buf ^ 1);
-            const uint32_t it2 = entry(t + 2);
+#pragma unroll
+            for (int r = 0; r < R; ++r) it2[r] = entry(t + 2, r);
             cp_async_wait1();
-            bool pass = false;
-            if (it0 != NONE) {
-                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][5][lane];
-                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
-                                         y0 + (float)(SH - 1));
-            }
-            uint32_t bits = __ballot_sync(SSSGS_FULL, pass);
-            __syncwarp();
-            const uint32_t base = rg.x + 32u * t;
-            // Composite one splat (list slot k, alpha already evaluated) into pixel q.
-            auto apply = [&](int q, int k, const AlphaEval& e, float4 g1) {
-                if (done[q] || !e.use) return;
-                const float Tn = T[q] * (1.f - e.alpha);
-                if (Tn < T_min) {
-                    done[q] = true;
-                    stop[q] = base + k + 1;
-                    return;
-                }
-                ++n_use;
-                const float w = T[q] * e.alpha;
-                const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
-                const float g5 = s_rec[buf][5][k].x;
-                float* f = F[q];
-                f[0] += w * g1.z;  f[1] += w * g1.w;  f[2] += w * g2.x;  f[3] += w * g2.y;
-                f[4] += w * g2.z;  f[5] += w * g2.w;  f[6] += w * g3.x;  f[7] += w * g3.y;
-                f[8] += w * g3.z;  f[9] += w * g3.w;  f[10] += w * g4.x; f[11] += w * g4.y;
-                f[12] += w * g4.z; f[13] += w * g4.w; f[14] += w * g5;
-                T[q] = Tn;
-                lastc[q] = base + k + 1;
-            };
-            while (bits) {
-                const int k = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
+            uint32_t bits[R];
 #pragma unroll
-                for (int q = 0; q < PX; ++q) {
-                    if (done[q]) continue;
-                    apply(q, k, eval_alpha(g0, g1, (float)i + 0.5f, (float)(j0 + q) + 0.5f, a_min, a_max), g1);
+            for (int r = 0; r < R; ++r) {
+                bool pass = false;
+                if (it0[r] != NONE) {
+                    const int s = 32 * r + lane;
+                    const float4 g0 = s_rec[buf][0][s], g1 = s_rec[buf][1][s], g5 = s_rec[buf][5][s];
+                    pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
+                                             y0 + 3.f);
+                }
+                bits[r] = __ballot_sync(SSSGS_FULL, pass);
+            }
+            __syncwarp();
+            const uint32_t base = rg.x + (uint32_t)BATCH * t;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                while (bits[r]) {          // warp-uniform loop; finished lanes idle
+                    const int k = 32 * r + __ffs(bits[r]) - 1;
+                    bits[r] &= bits[r] - 1;
+                    if (done) continue;
+                    const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
+                    const AlphaEval e = eval_alpha(g0, g1, px, py, a_min, a_max);
+                    if (!e.use) continue;
+                    const float Tn = T * (1.f - e.alpha);
+                    if (Tn < T_min) {
+                        done = true;
+                        stop = base + k + 1;
+                        continue;
+                    }
+                    ++n_use;
+                    const float w = T * e.alpha;
+                    const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
+                    const float g5 = s_rec[buf][5][k].x;
+                    F[0] += w * g1.z;  F[1] += w * g1.w;  F[2] += w * g2.x;  F[3] += w * g2.y;
+                    F[4] += w * g2.z;  F[5] += w * g2.w;  F[6] += w * g3.x;  F[7] += w * g3.y;
+                    F[8] += w * g3.z;  F[9] += w * g3.w;  F[10] += w * g4.x; F[11] += w * g4.y;
+                    F[12] += w * g4.z; F[13] += w * g4.w; F[14] += w * g5;
+                    T = Tn;
+                    lastc = base + k + 1;
                 }
             }
-            all_done = true;
-#pragma unroll
-            for (int q = 0; q < PX; ++q) all_done = all_done && done[q];
-            if (__all_sync(SSSGS_FULL, all_done)) break;
+            if (__all_sync(SSSGS_FULL, done)) break;
             __syncwarp();
-            it0 = it1;
-            it1 = it2;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                it0[r] = it1[r];
+                it1[r] = it2[r];
+            }
         }
         cp_async_wait_all();
     }
     if (stats) {   // contributions, and list positions each pixel considered
-        unsigned long long u = n_use, v = 0;
-#pragma unroll
-        for (int q = 0; q < PX; ++q) v += stop[q] - rg.x;
+        unsigned long long u = n_use, v = stop - rg.x;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
             u += __shfl_xor_sync(SSSGS_FULL, u, o);
@@ -245,24 +171,20 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
             atomicAdd(stats + 1, v);
         }
     }
-#pragma unroll
-    for (int q = 0; q < PX; ++q) {
-        const int j = j0 + q;
-        if (!(i < sP.W && j < sP.H)) continue;
-        const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
-        float4* go = reinterpret_cast<float4*>(gbuf + SSSGS_GBUF * pix);
-        go[0] = make_float4(F[q][0], F[q][1], F[q][2], F[q][3]);
-        go[1] = make_float4(F[q][4], F[q][5], F[q][6], F[q][7]);
-        go[2] = make_float4(F[q][8], F[q][9], F[q][10], F[q][11]);
-        go[3] = make_float4(F[q][12], F[q][13], F[q][14], T[q]);
-        last[pix] = lastc[q];
-        if (SHADE) {
-            float o[3];
-            shade_px<false>(F[q], T[q], (float)i + 0.5f, (float)j + 0.5f, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
-            img[3 * pix] = o[0];
-            img[3 * pix + 1] = o[1];
-            img[3 * pix + 2] = o[2];
-        }
+    if (!(i < sP.W && j < sP.H)) return;
+    const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
+    float4* go = reinterpret_cast<float4*>(gbuf + SSSGS_GBUF * pix);
+    go[0] = make_float4(F[0], F[1], F[2], F[3]);
+    go[1] = make_float4(F[4], F[5], F[6], F[7]);
+    go[2] = make_float4(F[8], F[9], F[10], F[11]);
+    go[3] = make_float4(F[12], F[13], F[14], T);
+    last[pix] = lastc;
+    if (SHADE) {
+        float o[3];
+        shade_px<false>(F, T, px, py, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
+        img[3 * pix] = o[0];
+        img[3 * pix + 1] = o[1];
+        img[3 * pix + 2] = o[2];
     }
 }
 
@@ -539,7 +461,8 @@ __device__ __forceinline__ void bwd_pixel_setup(PixBwd& p, bool inside, int64_t 
 
 // 20 resident blocks per SM: 96 registers (a 40-byte spill) and ~21 warps per
 // SM measured faster than 124 registers and 16 warps (29.4 vs 31.7 ms).
-template <int MODE>
+// One block per 8 x 8 sub-tile of a TILE x TILE tile ((TILE/8)^2 per tile).
+template <int TILE, int BATCH, int MODE>
 __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                          int n_pairs, const float4* __restrict__ rec,
                                                          const uint32_t* __restrict__ vals,
@@ -552,21 +475,21 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                                                          const float* __restrict__ weight, float l1_scale,
                                                          float* __restrict__ drec,
                                                          unsigned long long* __restrict__ stats) {
-    constexpr int TILE = 16, NG = 6 + SSSGS_NF, RS = 36;
+    constexpr int NG = 6 + SSSGS_NF, RS = 36, R = BATCH / 32;
+    using ST = SubTile<TILE, 8, 8>;
     constexpr uint32_t NONE = 0xFFFFFFFFu;
-    __shared__ __align__(16) float4 s_rec[2][6][32];
-    __shared__ uint32_t s_item[2][32];
+    __shared__ __align__(16) float4 s_rec[2][6][BATCH];
+    __shared__ uint32_t s_item[2][BATCH];
     __shared__ __align__(16) float s_red[NG * RS];
     __shared__ __align__(16) sssgs_pair sP;
-    const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
     const int lane = threadIdx.x;
     if (lane < 8) {
-        const int pi = pair_of_tile(pairs, n_pairs, tile);
+        const int pi = pair_of_tile(pairs, n_pairs, (int)(blockIdx.x / ST::NSUB));
         reinterpret_cast<float4*>(&sP)[lane] = reinterpret_cast<const float4*>(pairs + pi)[lane];
     }
     __syncwarp();
-    const int lt = tile - sP.tile_offset;
-    const int bx = (lt % sP.tiles_x) * TILE + (sub & 1) * 8, by = (lt / sP.tiles_x) * TILE + (sub >> 1) * 8;
+    const ST st(blockIdx.x, sP);
+    const int tile = st.tile, bx = st.bx, by = st.by;
     const int i = bx + (lane & 7), j0 = by + (lane >> 3) * 2;
     const uint2 rg = ranges[tile];
     PixBwd p[2];
@@ -597,42 +520,61 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
     const float x0 = bx + 0.5f, y0 = by + 0.5f;
     uint32_t n_use = 0;
     if (wmax > rg.x) {
-        const int nb = (int)((wmax - rg.x + 31) >> 5);
-        // Batch t covers list positions [lo(t), wmax - 32 t).
-        auto entry = [&](int t) -> uint32_t {
+        const int nb = (int)((wmax - rg.x + BATCH - 1) / BATCH);
+        // Batch t covers list positions [lo(t), wmax - BATCH t); slot s of a
+        // batch holds position lo(t) + s.
+        auto lo_of = [&](int t) -> int64_t { return max((int64_t)rg.x, (int64_t)wmax - (int64_t)BATCH * (t + 1)); };
+        auto entry = [&](int t, int r) -> uint32_t {
             if (t >= nb) return NONE;
-            const int64_t hi = (int64_t)wmax - 32 * t, lo = max((int64_t)rg.x, hi - 32);
-            const int64_t idx = lo + lane;
+            const int64_t hi = (int64_t)wmax - (int64_t)BATCH * t;
+            const int64_t idx = lo_of(t) + 32 * r + lane;
             return idx < hi ? vals[idx] : NONE;
         };
-        auto fetch = [&](uint32_t item, int buf) {
-            if (item != NONE) {
-                const float4* r = rec + 6 * (int64_t)item;
+        auto fetch = [&](const uint32_t* item, int buf) {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][lane]), r + q);
+            for (int r = 0; r < R; ++r) {
+                if (item[r] != NONE) {
+                    const float4* src = rec + 6 * (int64_t)item[r];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q)
+                        cp_async16((uint32_t)__cvta_generic_to_shared(&s_rec[buf][q][32 * r + lane]), src + q);
+                }
             }
             cp_async_commit();
         };
-        uint32_t it0 = entry(0);
+        uint32_t it0[R], it1[R], it2[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) it0[r] = entry(0, r);
         fetch(it0, 0);
-        uint32_t it1 = entry(1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) it1[r] = entry(1, r);
         for (int t = 0; t < nb; ++t) {
             const int buf = t & 1;
             fetch(it1, buf ^ 1);
-            const uint32_t it2 = entry(t + 2);
+#pragma unroll
+            for (int r = 0; r < R; ++r) it2[r] = entry(t + 2, r);
             cp_async_wait1();
-            bool pass = false;
-            if (it0 != NONE) {
-                const float4 g0 = s_rec[buf][0][lane], g1 = s_rec[buf][1][lane], g5 = s_rec[buf][5][lane];
-                pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0, y0 + 7.f);
+            uint32_t bits[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                bool pass = false;
+                const int sl = 32 * r + lane;
+                if (it0[r] != NONE) {
+                    const float4 g0 = s_rec[buf][0][sl], g1 = s_rec[buf][1][sl], g5 = s_rec[buf][5][sl];
+                    pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
+                                             y0 + 7.f);
+                }
+                s_item[buf][sl] = it0[r];
+                bits[r] = __ballot_sync(SSSGS_FULL, pass);
             }
-            s_item[buf][lane] = it0;
-            uint32_t bits = __ballot_sync(SSSGS_FULL, pass);
             __syncwarp();
-            const uint32_t lo = (uint32_t)max((int64_t)rg.x, (int64_t)wmax - 32 * t - 32);
-            while (bits) {
-                const int k = 31 - __clz(bits);
-                bits ^= 1u << k;
+            const uint32_t lo = (uint32_t)lo_of(t);
+#pragma unroll
+            for (int r = R - 1; r >= 0; --r) {
+            while (bits[r]) {
+                const int kb = 31 - __clz(bits[r]);
+                bits[r] ^= 1u << kb;
+                const int k = 32 * r + kb;
                 const uint32_t pos = lo + k;
                 const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
                 const AlphaEval e0 = eval_alpha(g0, g1, px_x, px_y0, a_min, a_max);
@@ -712,9 +654,13 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                 }
                 __syncwarp();
             }
+            }
             __syncwarp();
-            it0 = it1;
-            it1 = it2;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                it0[r] = it1[r];
+                it1[r] = it2[r];
+            }
         }
     }
     if (stats) {
@@ -733,8 +679,6 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
 }
 
 template <int TILE>
-static size_t fwd_smem() { return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 4; }
-template <int TILE>
 static size_t bwd_smem() {
     return (size_t)6 * TILE * TILE * sizeof(float4) + (size_t)TILE * TILE * 8 +
            (size_t)(TILE * TILE / 32) * (6 + SSSGS_NF) * 36 * 4;
@@ -746,77 +690,82 @@ using namespace sssgs;
 
 namespace {
 bool args_ok(const sssgs_cfg* cfg, const sssgs_pair* h, const sssgs_pair* d, int n) {
-    return cfg && h && d && n > 0 && (cfg->tile == 8 || cfg->tile == 16 || cfg->tile == 32) && cfg->reserved == 0;
+    return cfg && h && d && n > 0 && (cfg->tile == 8 || cfg->tile == 16 || cfg->tile == 32) &&
+           (cfg->batch == 0 || cfg->batch == 32 || cfg->batch == 64);
 }
 int tiles_of(const sssgs_pair* h, int n) { return h[n - 1].tile_offset + h[n - 1].tiles_x * h[n - 1].tiles_y; }
 bool a16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-template <int TILE, bool SHADE>
-int launch_fwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
-               const uint32_t* ranges, float* gbuf, uint32_t* last, float* img, cudaStream_t st,
-               unsigned long long* stats = nullptr) {
-    size_t sm = fwd_smem<TILE>();
-    cudaFuncSetAttribute(k_composite_fwd<TILE, SHADE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_composite_fwd<TILE, SHADE><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
-                                                                 (const uint2*)ranges, gbuf, last, img, stats);
+// One-warp forward: (TILE/8) x (TILE/4) blocks of 32 threads per tile.
+template <int TILE, int BATCH, bool SHADE>
+int launch_fwd_warp_t(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
+                      const uint32_t* vals, const uint32_t* ranges, float* gbuf, uint32_t* last, float* img,
+                      cudaStream_t st, unsigned long long* stats) {
+    constexpr int NSUB = (TILE / 8) * (TILE / 4);
+    k_composite_fwd_warp<TILE, BATCH, SHADE><<<NSUB * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals,
+                                                                       (const uint2*)ranges, gbuf, last, img,
+                                                                       stats);
     sssgs::note_launches(1);
     return launch_status();
 }
 
-// One pixel per lane (8 x 4 sub-tiles): measured faster than two (8 x 8),
-// whose coarser sub-tile test lets more splats through.
 template <bool SHADE>
 int launch_fwd_warp(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
                     const uint32_t* vals, const uint32_t* ranges, float* gbuf, uint32_t* last, float* img,
                     cudaStream_t st, unsigned long long* stats = nullptr) {
-    constexpr int PX = 1, NSUB = 8 / PX;
-    k_composite_fwd_warp<PX, SHADE><<<NSUB * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals,
-                                                                 (const uint2*)ranges, gbuf, last, img, stats);
-    sssgs::note_launches(1);
-    return launch_status();
-}
-
-template <int TILE, int MODE>
-int launch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
-               const uint32_t* ranges, const float* gbuf, const uint32_t* last, const float* dgbuf,
-               const float* img, const float* dimg, const float* target, const float* weight, float l1,
-               float* drec, cudaStream_t st, unsigned long long* stats) {
-    size_t sm = bwd_smem<TILE>();
-    cudaFuncSetAttribute(k_composite_bwd<TILE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_composite_bwd<TILE, MODE><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
-                                                                (const uint2*)ranges, gbuf, last, dgbuf, img, dimg,
-                                                                target, weight, l1, drec, stats);
-    sssgs::note_launches(1);
-    return launch_status();
-}
-
-template <int MODE>
-int launch_bwd_warp(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec, const uint32_t* vals,
-                const uint32_t* ranges, const float* gbuf, const uint32_t* last, const float* img,
-                const float* dimg, const float* target, const float* weight, float l1, float* drec,
-                cudaStream_t st, unsigned long long* stats) {
-    k_composite_bwd_warp<MODE><<<4 * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf,
-                                                     last, img, dimg, target, weight, l1, drec, stats);
-    sssgs::note_launches(1);
-    return launch_status();
-}
-
-template <int MODE>
-int dispatch_bwd(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
-                 const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
-                 const float* dgbuf, const float* img, const float* dimg, const float* target,
-                 const float* weight, float l1, float* drec, cudaStream_t st, unsigned long long* stats = nullptr) {
+    const bool b64 = cfg->batch == 64;
     switch (cfg->tile) {
-        case 8: return launch_bwd<8, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
-                                           target, weight, l1, drec, st, stats);
-        case 16:
-            if (MODE != UPSTREAM_DGBUF)
-                return launch_bwd_warp<MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, dimg, target,
-                                             weight, l1, drec, st, stats);
-            return launch_bwd<16, MODE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, dgbuf, img, dimg,
-                                        target, weight, l1, drec, st, stats);
-        default: return SSSGS_ERR_UNSUPPORTED;   // 32x32 tiles: forward only
+        case 8: return b64 ? launch_fwd_warp_t<8, 64, SHADE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, st, stats)
+                           : launch_fwd_warp_t<8, 32, SHADE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
+        case 16: return b64 ? launch_fwd_warp_t<16, 64, SHADE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, st, stats)
+                            : launch_fwd_warp_t<16, 32, SHADE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
+        default: return b64 ? launch_fwd_warp_t<32, 64, SHADE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, st, stats)
+                            : launch_fwd_warp_t<32, 32, SHADE>(cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
     }
+}
+
+// Block-per-tile backward with a G-buffer gradient upstream (the unfused path).
+template <int TILE>
+int launch_bwd_dgbuf(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
+                     const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
+                     const float* dgbuf, float* drec, cudaStream_t st) {
+    size_t sm = bwd_smem<TILE>();
+    cudaFuncSetAttribute(k_composite_bwd<TILE, UPSTREAM_DGBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_composite_bwd<TILE, UPSTREAM_DGBUF><<<tiles, TILE * TILE, sm, st>>>(*cfg, d, n, (const float4*)rec, vals,
+                                                                         (const uint2*)ranges, gbuf, last, dgbuf,
+                                                                         nullptr, nullptr, nullptr, nullptr, 0.f,
+                                                                         drec, nullptr);
+    sssgs::note_launches(1);
+    return launch_status();
+}
+
+// One-warp backward with the fused upstream (dimg or L1): (TILE/8)^2 blocks per tile.
+template <int TILE, int BATCH, int MODE>
+int launch_bwd_warp_t(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
+                      const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
+                      const float* img, const float* dimg, const float* target, const float* weight, float l1,
+                      float* drec, cudaStream_t st, unsigned long long* stats) {
+    constexpr int NSUB = (TILE / 8) * (TILE / 8);
+    k_composite_bwd_warp<TILE, BATCH, MODE><<<NSUB * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals,
+                                                                      (const uint2*)ranges, gbuf, last, img, dimg,
+                                                                      target, weight, l1, drec, stats);
+    sssgs::note_launches(1);
+    return launch_status();
+}
+
+template <int MODE>
+int launch_bwd_warp(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
+                    const uint32_t* vals, const uint32_t* ranges, const float* gbuf, const uint32_t* last,
+                    const float* img, const float* dimg, const float* target, const float* weight, float l1,
+                    float* drec, cudaStream_t st, unsigned long long* stats) {
+    const bool b64 = cfg->batch == 64;
+#define SSSGS_BWD_ARGS cfg, d, n, tiles, rec, vals, ranges, gbuf, last, img, dimg, target, weight, l1, drec, st, stats
+    switch (cfg->tile) {
+        case 8: return b64 ? launch_bwd_warp_t<8, 64, MODE>(SSSGS_BWD_ARGS) : launch_bwd_warp_t<8, 32, MODE>(SSSGS_BWD_ARGS);
+        case 16: return b64 ? launch_bwd_warp_t<16, 64, MODE>(SSSGS_BWD_ARGS) : launch_bwd_warp_t<16, 32, MODE>(SSSGS_BWD_ARGS);
+        default: return b64 ? launch_bwd_warp_t<32, 64, MODE>(SSSGS_BWD_ARGS) : launch_bwd_warp_t<32, 32, MODE>(SSSGS_BWD_ARGS);
+    }
+#undef SSSGS_BWD_ARGS
 }
 }  // namespace
 
@@ -827,11 +776,7 @@ extern "C" int sssgs_composite_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pai
     if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
     int tiles = tiles_of(h_pairs, n_pairs);
     cudaStream_t st = (cudaStream_t)stream;
-    switch (cfg->tile) {
-        case 8: return launch_fwd<8, false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
-        case 16: return launch_fwd_warp<false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
-        default: return launch_fwd<32, false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
-    }
+    return launch_fwd_warp<false>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, st);
 }
 
 extern "C" int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
@@ -843,11 +788,7 @@ extern "C" int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs,
     if (!a16(rec) || !a16(gbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
     int tiles = tiles_of(h_pairs, n_pairs);
     cudaStream_t st = (cudaStream_t)stream;
-    switch (cfg->tile) {
-        case 8: return launch_fwd<8, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
-        case 16: return launch_fwd_warp<true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
-        default: return launch_fwd<32, true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
-    }
+    return launch_fwd_warp<true>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, st, stats);
 }
 
 extern "C" int sssgs_shade_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
@@ -885,9 +826,13 @@ extern "C" int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pai
     if (!args_ok(cfg, h_pairs, d_pairs, n_pairs) || !rec || !ranges || !gbuf || !last || !dgbuf || !drec)
         return SSSGS_ERR_INVALID_ARG;
     if (!a16(rec) || !a16(gbuf) || !a16(dgbuf) || !a16(d_pairs) || !a16(ranges)) return SSSGS_ERR_INVALID_ARG;
-    return dispatch_bwd<UPSTREAM_DGBUF>(cfg, d_pairs, n_pairs, tiles_of(h_pairs, n_pairs), rec, vals, ranges, gbuf,
-                                        last, dgbuf, nullptr, nullptr, nullptr, nullptr, 0.f, drec,
-                                        (cudaStream_t)stream);
+    const int tiles = tiles_of(h_pairs, n_pairs);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (cfg->tile) {
+        case 8: return launch_bwd_dgbuf<8>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, dgbuf, drec, st);
+        case 16: return launch_bwd_dgbuf<16>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, dgbuf, drec, st);
+        default: return SSSGS_ERR_UNSUPPORTED;   // 32 x 32 tiles: the block-per-tile kernel would need 1024 threads
+    }
 }
 
 extern "C" int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
@@ -902,9 +847,9 @@ extern "C" int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs,
     int tiles = tiles_of(h_pairs, n_pairs);
     cudaStream_t st = (cudaStream_t)stream;
     if (dimg)
-        return dispatch_bwd<UPSTREAM_DIMG>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr,
-                                           nullptr, dimg, nullptr, nullptr, 0.f, drec, st, stats);
+        return launch_bwd_warp<UPSTREAM_DIMG>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr,
+                                              dimg, nullptr, nullptr, 0.f, drec, st, stats);
     if (!img || !target) return SSSGS_ERR_INVALID_ARG;
-    return dispatch_bwd<UPSTREAM_L1>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, nullptr, img,
-                                     nullptr, target, weight, l1_scale, drec, st, stats);
+    return launch_bwd_warp<UPSTREAM_L1>(cfg, d_pairs, n_pairs, tiles, rec, vals, ranges, gbuf, last, img, nullptr,
+                                        target, weight, l1_scale, drec, st, stats);
 }

@@ -48,6 +48,21 @@ class PairTable:
         self.d = torch.from_numpy(raw).to(device)
         self.n = n
 
+    @classmethod
+    def from_structs(cls, h_pairs, cfg: B.Cfg, device="cuda"):
+        """A table of copies of planned or unplanned pair structs (their
+        caller-filled fields), planned with cfg."""
+        t = cls.__new__(cls)
+        n = len(h_pairs)
+        t.h = (B.Pair * n)()
+        for k in range(n):
+            ctypes.memmove(ctypes.byref(t.h[k]), ctypes.byref(h_pairs[k]), ctypes.sizeof(B.Pair))
+        t.info = B.plan(t.h, cfg)
+        raw = np.frombuffer(bytes(t.h), dtype=np.uint8).copy()
+        t.d = torch.from_numpy(raw).to(device)
+        t.n = n
+        return t
+
     @property
     def n_items(self):
         return int(self.info.n_items)
@@ -72,11 +87,88 @@ class MLPParams:
         return B.mlp_struct(self.kind, self.precision, self.W, self.b)
 
 
+class GradientBuffers:
+    """Every trainable-parameter gradient of a renderer in one flat float32
+    buffer: the scene tensors (SCENE_KEYS order), the network's dW and db, and
+    optional extra tensors (the SH visibility coefficients). Each is a
+    contiguous view starting at a multiple of 64 floats (256 B). Zeroing is one
+    fill, and the data-parallel exchange is one all-reduce of `flat`."""
+
+    ALIGN = 64
+
+    def __init__(self, scene_shapes: dict, w_shapes, b_shapes, extra_shapes=None, device="cuda"):
+        specs = [("scene", k, tuple(v)) for k, v in scene_shapes.items()]
+        specs += [("W", l, tuple(s)) for l, s in enumerate(w_shapes)]
+        specs += [("b", l, tuple(s)) for l, s in enumerate(b_shapes)]
+        specs += [("extra", k, tuple(v)) for k, v in (extra_shapes or {}).items()]
+        offs, total = [], 0
+        for _, _, shape in specs:
+            offs.append(total)
+            n = int(np.prod(shape)) if len(shape) else 1
+            total += (n + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        self.flat = torch.zeros(max(total, 1), device=device, dtype=torch.float32)
+        self.scene, self.extra = {}, {}
+        self.dW = [None] * len(w_shapes)
+        self.db = [None] * len(b_shapes)
+        for (kind, key, shape), o in zip(specs, offs):
+            n = int(np.prod(shape)) if len(shape) else 1
+            v = self.flat[o:o + n].view(shape)
+            if kind == "scene":
+                self.scene[key] = v
+            elif kind == "W":
+                self.dW[key] = v
+            elif kind == "b":
+                self.db[key] = v
+            else:
+                self.extra[key] = v
+
+    def zero_(self):
+        self.flat.zero_()
+
+
+class _Group:
+    """A run of consecutive pairs rendered with its own schedule (tile edge and
+    per-block splat batch): its own pair table and tile lists. Its records,
+    network rows, G-buffer, images and gradient records are slices of the
+    renderer's buffers (a pair's items and pixels are contiguous)."""
+
+    def __init__(self, r, p0: int, p1: int, cfg: B.Cfg):
+        h = r.table.h
+        self.cfg = cfg
+        self.p0, self.p1 = p0, p1
+        self.table = PairTable.from_structs(h[p0:p1], cfg, r.device)
+        i0 = int(h[p0].item_offset)
+        px0 = int(h[p0].pixel_offset)
+        self.items = slice(i0, i0 + self.table.n_items)
+        self.pixels = slice(px0, px0 + self.table.n_pixels)
+        self.rec, self.rect, self.mlp_out = r.rec[self.items], r.rect[self.items], r.mlp_out[self.items]
+        self.drec = r.drec[self.items]
+        self.gbuf, self.last, self.img = r.gbuf[self.pixels], r.last[self.pixels], r.img[self.pixels]
+        self.ranges = torch.zeros(self.table.n_tiles, 2, device=r.device, dtype=torch.int32)
+        self.count = torch.zeros(1, device=r.device, dtype=torch.int64)
+        self.stream = torch.cuda.Stream() if str(r.device).startswith("cuda") else None
+        self.device = r.device
+        self.capacity = 0
+
+    def set_capacity(self, cap: int):
+        self.capacity = int(cap)
+        self.vals = torch.zeros(max(self.capacity, 1), device=self.device, dtype=torch.int32)
+        wsb = B.bin_workspace_bytes(self.table.n_items, self.capacity, self.table.n_tiles)
+        self.ws_bin = torch.empty(max(wsb, 256), device=self.device, dtype=torch.uint8)
+
+
 class Renderer:
-    """Owns every buffer of a batch and runs the forward/backward call sequence."""
+    """Owns every buffer of a batch and runs the forward/backward call sequence.
+
+    schedule (optional): [(first pair, end pair, cfg), ...] covering the pairs
+    in order. Each run of pairs is rendered with its own tile edge and
+    per-block batch (cfg.tile, cfg.batch; e.g. one per scene from
+    autotune_schedule): the projection, tile lists and render kernels run per
+    run, each on its own stream inside the step (so one captured graph holds
+    them all); the network and projection backward run once over all pairs."""
 
     def __init__(self, scene: dict, mlp: MLPParams, table: PairTable, cfg: B.Cfg, capacity: int | None = None,
-                 fused: bool = True, device="cuda", vis_sh=None, shading: str = "deferred"):
+                 fused: bool = True, device="cuda", vis_sh=None, shading: str = "deferred", schedule=None):
         """vis_sh (N x 16 device tensor, optional): the SH visibility term; v of
         each (pair, Gaussian) is then evaluated at the pair's light direction
         (sssgs_vis_sh_fwd) instead of read from scene["vis"].
@@ -112,16 +204,19 @@ class Renderer:
         self.rec_colors = torch.zeros(n, B.REC, **f32) if shading == "gaussian" else None
         self.drec = torch.zeros(n, B.REC, **f32)
         self.dx_items = torch.zeros(n, B.DX, **f32)
-        self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
-        self.dW = [torch.zeros_like(w) for w in mlp.W]
-        self.db = [torch.zeros_like(b) for b in mlp.b]
+        self.grad_buffers = GradientBuffers({k: v.shape for k, v in scene.items()}, [w.shape for w in mlp.W],
+                                            [b.shape for b in mlp.b],
+                                            {"vis_sh": vis_sh.shape} if vis_sh is not None else None, device)
+        self.grads = self.grad_buffers.scene
+        self.dW = self.grad_buffers.dW
+        self.db = self.grad_buffers.db
         self.vis_item = self.dvis_item = self.dvis_sh = None
         self.vis_traced = None
         self.loss_vis = None
         if vis_sh is not None:
             self.vis_item = torch.zeros(n, **f32)
             self.dvis_item = torch.zeros(n, **f32)
-            self.dvis_sh = torch.zeros_like(vis_sh)
+            self.dvis_sh = self.grad_buffers.extra["vis_sh"]
         self._scene_s = B.scene_struct(scene, self.vis_item)
         self._grad_s = B.scene_grad_struct(self.grads, self.dvis_item)
         self._mlp_s = mlp.struct()
@@ -131,7 +226,18 @@ class Renderer:
         self.stats_fwd = None        # optional uint64[2] work counters (see sssgs_render_fwd/bwd)
         self.stats_bwd = None
         self.capacity = 0
-        self.set_capacity(capacity if capacity is not None else max(1024, 16 * n))
+        self.groups = None
+        if schedule is not None and len(schedule) > 1:
+            if vis_sh is not None or shading != "deferred" or not fused:
+                raise ValueError("a per-run schedule takes the fused deferred path without the SH visibility term")
+            ends = [(a, b) for a, b, _ in schedule]
+            if ends[0][0] != 0 or ends[-1][1] != table.n or any(x[1] != y[0] for x, y in zip(ends, ends[1:])):
+                raise ValueError("the schedule's runs must cover the pairs in order")
+            self.groups = [_Group(self, a, b, c) for a, b, c in schedule]
+            for g in self.groups:
+                g.set_capacity(capacity if capacity is not None else max(1024, 16 * g.table.n_items))
+        else:
+            self.set_capacity(capacity if capacity is not None else max(1024, 16 * n))
 
     # ------------------------------------------------------------------ setup
     def set_capacity(self, cap: int):
@@ -142,9 +248,20 @@ class Renderer:
         self.ws_bin = torch.empty(max(wsb, 256), device=self.device, dtype=torch.uint8)
 
     def fit_capacity(self, slack: float = 1.15):
-        """Run the front end once and size the instance buffers (syncs)."""
+        """Run the front end once and size the instance buffers (syncs).
+        Returns the number of tile instances."""
         self.forward_front()
         torch.cuda.synchronize()
+        if self.groups is not None:
+            needs = [int(g.count.item()) for g in self.groups]
+            if any(nd > g.capacity for nd, g in zip(needs, self.groups)) or self.status.item() != 0:
+                for nd, g in zip(needs, self.groups):
+                    if nd > g.capacity:
+                        g.set_capacity(int(nd * slack) + 1024)
+                self.status.zero_()
+                self.forward_front()
+                torch.cuda.synchronize()
+            return sum(needs)
         need = int(self.count.item())
         if need > self.capacity or self.status.item() != 0:
             self.set_capacity(int(need * slack) + 1024)
@@ -153,9 +270,79 @@ class Renderer:
             torch.cuda.synchronize()
         return need
 
-    # ------------------------------------------------------------------ steps
-    def forward_front(self, stream=None):
+    # ------------------------------------------------------------------ runs of the schedule
+    def _for_groups(self, fn, stream=None):
+        """fn(group) for every run of the schedule, each on its own stream,
+        forked from and joined back into the current (or given) stream."""
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        for g in self.groups:
+            g.stream.wait_stream(cur)
+        for g in self.groups:
+            with torch.cuda.stream(g.stream):
+                fn(g)
+        for g in self.groups:
+            cur.wait_stream(g.stream)
+
+    def _group_front(self, g):
+        B.project_fwd(g.cfg, g.table.h, g.table.d, self._scene_s, g.mlp_out, g.rec, g.rect)
+        B.bin_sort(g.cfg, g.table.h, g.table.d, g.rec, g.rect, g.capacity, g.vals, g.ranges, g.count,
+                   self.status, g.ws_bin)
+
+    def _group_render_fwd(self, g):
+        B.render_fwd(g.cfg, g.table.h, g.table.d, g.rec, g.vals, g.ranges, g.gbuf, g.last, g.img, self.stats_fwd)
+
+    def _group_render_bwd(self, g, dimg, target, weight, l1_scale):
+        sl = g.pixels
+        B.render_bwd(g.cfg, g.table.h, g.table.d, g.rec, g.vals, g.ranges, g.gbuf, g.last, g.img,
+                     dimg[sl] if dimg is not None else None, target[sl] if target is not None else None,
+                     weight[sl] if weight is not None else None, l1_scale, g.drec, self.stats_bwd)
+
+    def run_stage(self, name, stream=None, dimg=None, target=None, weight=None, l1_scale=1.0):
+        """One stage of the step over every pair (for per-stage timing):
+        mlp_fwd, project_fwd, bin_sort, render_fwd, render_bwd (upstream dimg
+        or the L1 loss against target), mlp_bwd, project_bwd."""
         t = self.table
+        if name == "mlp_fwd":
+            B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, self.status, stream)
+        elif name == "mlp_bwd":
+            B.mlp_bwd(self._mlp_s, t.h, t.d, self._scene_s, self.drec, self._mlp_g, self.dx_items, self.ws_mlp,
+                      self.status, stream)
+        elif name == "project_bwd":
+            B.project_bwd(self.cfg, t.h, t.d, self._scene_s, self.drec, self.dx_items, self._grad_s, stream)
+        elif self.groups is not None:
+            fn = {"project_fwd": lambda g: B.project_fwd(g.cfg, g.table.h, g.table.d, self._scene_s, g.mlp_out,
+                                                         g.rec, g.rect),
+                  "bin_sort": lambda g: B.bin_sort(g.cfg, g.table.h, g.table.d, g.rec, g.rect, g.capacity, g.vals,
+                                                   g.ranges, g.count, self.status, g.ws_bin),
+                  "render_fwd": self._group_render_fwd,
+                  "render_bwd": lambda g: self._group_render_bwd(g, dimg, target, weight, l1_scale)}[name]
+            self._for_groups(fn, stream)
+        elif name == "project_fwd":
+            B.project_fwd(self.cfg, t.h, t.d, self._scene_s, self.mlp_out, self.rec, self.rect, stream)
+        elif name == "bin_sort":
+            B.bin_sort(self.cfg, t.h, t.d, self.rec, self.rect, self.capacity, self.vals, self.ranges, self.count,
+                       self.status, self.ws_bin, stream)
+        elif name == "render_fwd":
+            B.render_fwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
+                         self.stats_fwd, stream)
+        elif name == "render_bwd":
+            B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
+                         dimg, target, weight, l1_scale, self.drec, self.stats_bwd, stream)
+        else:
+            raise ValueError(f"unknown stage {name!r}")
+
+    # ------------------------------------------------------------------ steps
+    def forward_front(self, stream=None, render=False):
+        t = self.table
+        if self.groups is not None:
+            B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, self.status, stream)
+
+            def front(g):
+                self._group_front(g)
+                if render:
+                    self._group_render_fwd(g)
+            self._for_groups(front, stream)
+            return
         if self.vis_sh is not None:
             B.vis_sh_fwd(t.h, t.d, self._scene_s, self.vis_sh, self.vis_item, stream)
         B.mlp_fwd(self._mlp_s, t.h, t.d, self._scene_s, self.mlp_out, self.status, stream)
@@ -164,6 +351,9 @@ class Renderer:
                    self.status, self.ws_bin, stream)
 
     def forward(self, stream=None):
+        if self.groups is not None:
+            self.forward_front(stream, render=True)
+            return self.img
         self.forward_front(stream)
         t = self.table
         if self.shading == "gaussian":
@@ -181,13 +371,14 @@ class Renderer:
 
     def zero_grads(self):
         self.drec.zero_()
-        for g in self.grads.values():
-            g.zero_()
-        for g in self.dW + self.db:
-            g.zero_()
+        self.grad_buffers.zero_()
         if self.vis_sh is not None:
             self.dvis_item.zero_()
-            self.dvis_sh.zero_()
+
+    def exchange_gradients(self, group=None):
+        """Data-parallel exchange: sum every parameter gradient over the
+        process group with one all-reduce of the flat gradient buffer."""
+        exchange_gradients(self.grad_buffers.flat, group)
 
     def trace_visibility(self, stream=None):
         """Ray-traced visibility of every (pair, Gaussian) toward the pair's
@@ -230,6 +421,8 @@ class Renderer:
                          self.ws_loss, stream)
             if self.shading == "gaussian":
                 self._backward_gaussian_shading(self.dimg_loss, stream)
+            elif self.groups is not None:
+                self._for_groups(lambda g: self._group_render_bwd(g, self.dimg_loss, None, None, 1.0), stream)
             elif self.fused:
                 B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
                              self.dimg_loss, None, None, 1.0, self.drec, self.stats_bwd, stream)
@@ -242,6 +435,8 @@ class Renderer:
             if dimg is None:
                 raise ValueError("per-Gaussian shading takes dimg (or loss='paper')")
             self._backward_gaussian_shading(dimg, stream)
+        elif self.groups is not None:
+            self._for_groups(lambda g: self._group_render_bwd(g, dimg, target, weight, l1_scale), stream)
         elif self.fused:
             B.render_bwd(self.cfg, t.h, t.d, self.rec, self.vals, self.ranges, self.gbuf, self.last, self.img,
                          dimg, target, weight, l1_scale, self.drec, self.stats_bwd, stream)
@@ -295,9 +490,19 @@ class Renderer:
     def check_status(self):
         s = int(self.status.item())
         if s & B.STATUS_CAPACITY:
+            if self.groups is not None:
+                need = [(g.capacity, int(g.count.item())) for g in self.groups]
+                raise B.SSSGSError(f"instance capacity exceeded in a run of the schedule (capacity, needed): {need}")
             raise B.SSSGSError(f"instance capacity {self.capacity} exceeded ({int(self.count.item())} needed)")
         if s & B.STATUS_TIMEOUT:
             raise B.SSSGSError("a tensor-core kernel stopped on its wait limit; outputs are incomplete")
+
+    @property
+    def n_instances(self) -> int:
+        """Tile instances of the last binning (syncs)."""
+        if self.groups is not None:
+            return sum(int(g.count.item()) for g in self.groups)
+        return int(self.count.item())
 
 
 class SSSRenderFunction(torch.autograd.Function):
@@ -355,18 +560,37 @@ def mlp_to_device(spec, precision=None, device="cuda") -> MLPParams:
 
 
 def renderer_for_workload(wl, precision=None, fused=True, tile=None, capacity=None, device="cuda",
-                          pair_slice=None, vis_sh=None, shading="deferred") -> Renderer:
-    """vis_sh: optional N x 16 numpy array of SH visibility coefficients."""
+                          pair_slice=None, vis_sh=None, shading="deferred", batch=None,
+                          scene_cfgs=None) -> Renderer:
+    """vis_sh: optional N x 16 numpy array of SH visibility coefficients.
+    tile, batch: the schedule of every pair. scene_cfgs: one B.Cfg per scene
+    (autotune_schedule), each run of consecutive pairs of a scene rendered
+    with its scene's tile edge and batch."""
     cfg = default_cfg(tile or wl.tile)
+    if batch is not None:
+        cfg.batch = int(batch)
     scene, offs, counts = concat_scenes(wl.scenes, device)
     pairs = wl.pairs if pair_slice is None else wl.pairs[pair_slice]
+    schedule = None
+    if scene_cfgs is not None:
+        runs = []
+        for k, p in enumerate(pairs):
+            if runs and runs[-1][2] == p.scene:
+                runs[-1][1] = k + 1
+            else:
+                runs.append([k, k + 1, p.scene])
+        schedule = [(a, b, scene_cfgs[sc]) for a, b, sc in runs]
+        keys = {(c.tile, c.batch) for _, _, c in schedule}
+        if len(keys) == 1:          # one schedule for all: the plain single-run path
+            cfg = schedule[0][2]
+            schedule = None
     table = PairTable(pairs, cfg, offs, counts, device)
     mlp = mlp_to_device(wl.mlp, precision, device)
     sh = None
     if vis_sh is not None:
         sh = torch.from_numpy(np.ascontiguousarray(vis_sh, np.float32)).to(device)
     return Renderer(scene, mlp, table, cfg, capacity=capacity, fused=fused, device=device, vis_sh=sh,
-                    shading=shading)
+                    shading=shading, schedule=schedule)
 
 
 class MultiLightRenderer:
@@ -411,15 +635,18 @@ class MultiLightRenderer:
         self.drec = torch.zeros(nv, B.REC, **f32)
         self.dmlp = torch.zeros(npi, 4, **f32)
         self.dx_items = torch.zeros(npi, B.DX, **f32)
-        self.grads = {k: torch.zeros_like(v) for k, v in scene.items()}
-        self.dW = [torch.zeros_like(w) for w in mlp.W]
-        self.db = [torch.zeros_like(b) for b in mlp.b]
+        self.grad_buffers = GradientBuffers({k: v.shape for k, v in scene.items()}, [w.shape for w in mlp.W],
+                                            [b.shape for b in mlp.b],
+                                            {"vis_sh": vis_sh.shape} if vis_sh is not None else None, device)
+        self.grads = self.grad_buffers.scene
+        self.dW = self.grad_buffers.dW
+        self.db = self.grad_buffers.db
         self.vis_sh = vis_sh
         self.vis_item = self.dvis_item = self.dvis_sh = self.vis_traced = self.loss_vis = None
         if vis_sh is not None:
             self.vis_item = torch.zeros(npi, **f32)
             self.dvis_item = torch.zeros(npi, **f32)
-            self.dvis_sh = torch.zeros_like(vis_sh)
+            self.dvis_sh = self.grad_buffers.extra["vis_sh"]
         self._scene_s = B.scene_struct(scene)                       # per-view records
         self._grad_s = B.scene_grad_struct(self.grads)
         self._scene_p = B.scene_struct(scene, self.vis_item)        # (view, light) pairs: network
@@ -476,13 +703,13 @@ class MultiLightRenderer:
     def zero_grads(self):
         self.drec.zero_()
         self.dmlp.zero_()
-        for g in self.grads.values():
-            g.zero_()
-        for g in self.dW + self.db:
-            g.zero_()
+        self.grad_buffers.zero_()
         if self.vis_sh is not None:
             self.dvis_item.zero_()
-            self.dvis_sh.zero_()
+
+    def exchange_gradients(self, group=None):
+        """One all-reduce of the flat gradient buffer (see Renderer)."""
+        exchange_gradients(self.grad_buffers.flat, group)
 
     def trace_visibility(self, stream=None):
         """Ray-traced visibility of every (view, light, Gaussian) toward its
@@ -564,30 +791,68 @@ def multilight_renderer_for_workload(wl, precision=None, capacity=None, device="
                               vis_sh=sh)
 
 
-def autotune_tile(wl, candidates=(16, 8), precision=None, steps=2, device="cuda", capacity_slack=1.15):
-    """Pick the tile edge for a workload by timing full forward + backward steps
-    of each candidate on the device (CUDA events). Returns (best_tile, {tile: ms})."""
-    timings = {}
-    for tile in candidates:
-        r = renderer_for_workload(wl, precision=precision, tile=tile, device=device)
-        r.fit_capacity(capacity_slack)
-        dimg = torch.full((r.table.n_pixels, 3), 1e-6, device=device)
-        r.forward()
-        r.backward(dimg=dimg)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
-            r.forward()
-            r.backward(dimg=dimg)
-        e1.record()
-        torch.cuda.synchronize()
-        timings[tile] = e0.elapsed_time(e1) / steps
-        del r
+def autotune_schedule(wl, precision=None, tiles=(8, 16, 32), batches=(32, 64), reps=3, device="cuda",
+                      slack: float = 1.1):
+    """Pick the tile edge and per-block splat batch of every scene of a
+    workload by measurement (sssgs_autotune): for each scene, its pairs'
+    schedule-dependent stages (projection, binning + sort, fused render
+    forward and backward) are timed on the device for every candidate.
+    Returns (one B.Cfg per scene, {scene: [TuneResult, ...]}). Blocking."""
+    base = default_cfg(16)
+    r = renderer_for_workload(wl, precision=precision, device=device)
+    r.run_stage("mlp_fwd")
+    torch.cuda.synchronize()
+    h = r.table.h
+    cfgs, table = [], {}
+    for sc in range(len(wl.scenes)):
+        ks = [k for k, p in enumerate(wl.pairs) if p.scene == sc]
+        sub = PairTable.from_structs([h[k] for k in ks], base, device)
+        rows = [r.mlp_out[int(h[k].item_offset):int(h[k].item_offset) + int(h[k].g_count)] for k in ks]
+        mlp_out = torch.cat(rows).contiguous()
+        n, P = sub.n_items, sub.n_pixels
+        max_tiles = PairTable.from_structs(sub.h, default_cfg(min(tiles)), device).n_tiles
+        f32 = dict(device=device, dtype=torch.float32)
+        keep = dict(d_pairs=torch.zeros(sub.n * ctypes.sizeof(B.Pair), device=device, dtype=torch.uint8),
+                    rec=torch.zeros(n, B.REC, **f32), rect=torch.zeros(n, 4, device=device, dtype=torch.int32),
+                    ranges=torch.zeros(max_tiles, 2, device=device, dtype=torch.int32),
+                    count=torch.zeros(1, device=device, dtype=torch.int64),
+                    status=torch.zeros(1, device=device, dtype=torch.int32),
+                    gbuf=torch.zeros(P, B.GBUF, **f32), last=torch.zeros(P, device=device, dtype=torch.int32),
+                    img=torch.zeros(P, 3, **f32), drec=torch.zeros(n, B.REC, **f32),
+                    dimg=torch.full((P, 3), 1e-6, **f32))
+
+        def buffers(capacity):
+            keep["vals"] = torch.zeros(max(capacity, 1), device=device, dtype=torch.int32)
+            keep["ws"] = torch.empty(max(B.bin_workspace_bytes(n, capacity, max_tiles), 256), device=device,
+                                     dtype=torch.uint8)
+            tb = B.TuneBuffers()
+            for k in ("d_pairs", "rec", "rect", "vals", "ranges", "gbuf", "last", "img", "drec", "dimg"):
+                setattr(tb, k, keep[k].data_ptr())
+            tb.capacity, tb.max_tiles = int(capacity), int(max_tiles)
+            tb.d_count, tb.d_status = keep["count"].data_ptr(), keep["status"].data_ptr()
+            tb.workspace, tb.workspace_bytes = keep["ws"].data_ptr(), keep["ws"].numel()
+            return tb
+
+        capacity = 16 * n + 1024
+        best, res = B.autotune(base, sub.h, r._scene_s, mlp_out, buffers(capacity), tiles, batches, reps)
+        short = [x for x in res if x.status == B.STATUS_CAPACITY]
+        if short:                       # rerun the candidates whose instances did not fit (counts reported)
+            capacity = int(max(x.instances for x in short) * slack) + 1024
+            retry_tiles = sorted({x.tile for x in short})
+            _, res2 = B.autotune(base, sub.h, r._scene_s, mlp_out, buffers(capacity), retry_tiles, batches, reps)
+            got = {(x.tile, x.batch): x for x in res2}
+            res = [got.get((x.tile, x.batch), x) for x in res]
+            ok = [x for x in res if x.status == 0]
+            fastest = min(ok, key=lambda x: x.ms)
+            best = default_cfg(fastest.tile)
+            best.batch = fastest.batch
+        cfgs.append(best)
+        table[sc] = res
+        del keep
         torch.cuda.empty_cache()
-    best = min(timings, key=timings.get)
-    return best, timings
+    del r
+    torch.cuda.empty_cache()
+    return cfgs, table
 
 
 # ---------------------------------------------------------------------- data parallel
@@ -598,13 +863,12 @@ def shard_pairs(n_pairs: int, rank: int, world: int) -> list:
     return list(range(rank, n_pairs, world))
 
 
-def allreduce_gradients(tensors, group=None):
-    """Sum gradients over the process group: the one exchange of a
-    data-parallel step (renders of different pairs are independent; the
-    parameters are shared)."""
+def exchange_gradients(flat, group=None):
+    """Sum the flat gradient buffer (GradientBuffers.flat) over the process
+    group with one all-reduce: the one exchange of a data-parallel step
+    (renders of different pairs are independent; the parameters are shared)."""
     import torch.distributed as dist
-    for t in tensors:
-        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
 
 
 # ---------------------------------------------------------------------- checkpoint / resume

@@ -34,11 +34,48 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(B.Cfg) == 36
     assert ctypes.sizeof(B.MLP) == 4 * 3 + 4 * 9 + 8 * 16
     assert B.Pair.pixel_offset.offset == 112 and B.Pair.item_offset.offset == 120
+    assert ctypes.sizeof(B.TuneBuffers) == 128 and B.TuneBuffers.workspace_bytes.offset == 80
+    assert ctypes.sizeof(B.TuneResult) == 32 and B.TuneResult.ms.offset == 24
+
+
+def test_autotune_rejects_bad_arguments_before_any_launch():
+    """Host-side checks of sssgs_autotune (no GPU needed): missing buffers,
+    reps out of range, a batch other than 32 or 64, an empty candidate list."""
+    lib = B.load_library()
+    base = B.cfg_default()
+    h = (B.Pair * 1)()
+    h[0].W, h[0].H, h[0].fx, h[0].fy, h[0].g_count = 64, 64, 50.0, 50.0, 10
+    scene = B.Scene()
+    tiles = (ctypes.c_int32 * 2)(8, 16)
+    batches = (ctypes.c_int32 * 1)(32)
+    res = (B.TuneResult * 2)()
+    best = B.Cfg()
+    empty = B.TuneBuffers()
+    rc = lib.sssgs_autotune(ctypes.byref(base), h, 1, ctypes.byref(scene), 16, ctypes.byref(empty), tiles, 2, batches,
+                            1, 3, res, ctypes.byref(best), None)
+    assert rc == B.ERR_INVALID_ARG
+    full = B.TuneBuffers()
+    for k in ("d_pairs", "rec", "rect", "vals", "ranges", "d_count", "d_status", "gbuf", "last", "img", "drec",
+              "dimg"):
+        setattr(full, k, 256)
+    for reps, bt in ((0, 32), (1001, 32), (3, 48)):
+        batches[0] = bt
+        rc = lib.sssgs_autotune(ctypes.byref(base), h, 1, ctypes.byref(scene), 16, ctypes.byref(full), tiles, 2,
+                                batches, 1, reps, res, ctypes.byref(best), None)
+        assert rc == B.ERR_INVALID_ARG, (reps, bt)
+    batches[0] = 32
+    rc = lib.sssgs_autotune(ctypes.byref(base), h, 1, ctypes.byref(scene), 16, ctypes.byref(full), tiles, 0,
+                            batches, 1, 3, res, ctypes.byref(best), None)
+    assert rc == B.ERR_INVALID_ARG
+    full.max_tiles = 10            # 8 x 8 tiles of a 64 x 64 image need 64
+    rc = lib.sssgs_autotune(ctypes.byref(base), h, 1, ctypes.byref(scene), 16, ctypes.byref(full), tiles, 2,
+                            batches, 1, 3, res, ctypes.byref(best), None)
+    assert rc == B.ERR_INVALID_ARG
 
 
 def test_defaults_and_strerror():
     c = B.cfg_default()
-    assert c.tile == 16 and c.reserved == 0
+    assert c.tile == 16 and c.batch == 32
     assert c.alpha_min == pytest.approx(np.float32(1 / 255))
     assert c.alpha_max == pytest.approx(np.float32(0.99))
     assert c.T_min == pytest.approx(np.float32(1e-4))

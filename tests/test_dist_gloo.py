@@ -1,8 +1,9 @@
 """Data-parallel step on CPU (gloo, 2 ranks): each rank renders its shard of
-the view/light pairs (with the FP64 oracle, so no GPU is needed) and the
-gradients are summed with the pipeline's all-reduce; the result must equal the
-single-process sum over all pairs. Covers the sharding and exchange logic the
-multi-GPU benchmark uses."""
+the view/light pairs (with the FP64 oracle, so no GPU is needed), writes the
+scene and network gradients into a Renderer's flat gradient buffer (built on
+the CPU: host-side set-up only) and calls Renderer.exchange_gradients, the
+one all-reduce the multi-GPU benchmark's step makes; the result must equal the
+single-process sum over all pairs, for every scene tensor and every dW, db."""
 import os
 import socket
 
@@ -33,15 +34,21 @@ def _worker(rank, world, port, out_path):
     wl = sg.make_workload("c4", N=400, res=32, n_pairs=5)
     dimg = sg.random_dimg(3, 32 * 32 * 5)
     keys = PL.SCENE_KEYS
-    acc = {k: np.zeros_like(getattr(wl.scenes[0], k)) for k in keys}
+    rend = PL.renderer_for_workload(wl, device="cpu")
+    rend.zero_grads()
     for p in PL.shard_pairs(len(wl.pairs), rank, world):
         r = O.render_pair(wl.scenes[0], wl.pairs[p], wl.mlp, dimg=dimg[p * 1024:(p + 1) * 1024])
         for k in keys:
-            acc[k] += r["grads"][k]
-    tensors = [torch.from_numpy(acc[k]) for k in keys]
-    PL.allreduce_gradients(tensors)
+            rend.grads[k] += torch.from_numpy(r["grads"][k]).float()
+        for l in range(len(rend.dW)):
+            rend.dW[l] += torch.from_numpy(r["dW"][l]).float()
+            rend.db[l] += torch.from_numpy(r["db"][l]).float()
+    rend.exchange_gradients()
     if rank == 0:
-        np.savez(out_path, **{k: t.numpy() for k, t in zip(keys, tensors)})
+        out = {k: rend.grads[k].numpy() for k in keys}
+        out.update({f"W{l}": w.numpy() for l, w in enumerate(rend.dW)})
+        out.update({f"b{l}": b.numpy() for l, b in enumerate(rend.db)})
+        np.savez(out_path, **out)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -60,9 +67,13 @@ def test_two_rank_gradient_allreduce_equals_full_batch(tmp_path):
     for p in range(5):
         r = O.render_pair(wl.scenes[0], wl.pairs[p], wl.mlp, dimg=dimg[p * 1024:(p + 1) * 1024])
         for k in PL.SCENE_KEYS:
-            ref[k] += r["grads"][k]
-    for k in PL.SCENE_KEYS:
-        assert np.allclose(got[k], ref[k], rtol=1e-12, atol=1e-14 * np.abs(ref[k]).max()), k
+            ref[k] = ref[k] + r["grads"][k]
+        for l in range(len(r["dW"])):
+            ref[f"W{l}"] = ref.get(f"W{l}", 0) + r["dW"][l]
+            ref[f"b{l}"] = ref.get(f"b{l}", 0) + r["db"][l]
+    assert len(ref) == len(PL.SCENE_KEYS) + 10
+    for k, v in ref.items():       # float32 buffers: sums of two rank partials, each rounded once
+        assert np.allclose(got[k], v, rtol=1e-5, atol=1e-6 * max(np.abs(v).max(), 1e-30)), k
     assert PL.shard_pairs(5, 0, 2) == [0, 2, 4] and PL.shard_pairs(5, 1, 2) == [1, 3]
 
 
@@ -80,7 +91,7 @@ def _worker_peer_dies(rank, world, port, out_path):
         os._exit(3)                      # dies between steps, before the gradient exchange
     t0 = time.time()
     try:
-        PL.allreduce_gradients([torch.ones(16)])
+        PL.exchange_gradients(torch.ones(16))
         status = "completed"
     except Exception as ex:              # the exchange must fail, not hang
         status = f"error:{type(ex).__name__}"

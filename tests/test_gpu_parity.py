@@ -175,14 +175,30 @@ def test_forward_image_and_gbuffer_match_oracle(name, kw):
 
 
 def test_tile_size_and_fusion_do_not_change_pixels():
-    """Tiles only prune candidates; per-pixel arithmetic and order are the same,
-    so the forward is bit-identical across 8/16/32 tiles and fused/unfused."""
+    """Tiles and splat batches only prune and stage candidates; per-pixel
+    arithmetic and order are the same, so the forward is bit-identical across
+    8/16/32 tiles, batches of 32/64 splats, and fused/unfused kernels."""
     wl = sg.make_workload("c2", N=20000, res=200)
     base = run_gpu(wl, backward=False, tile=16)
-    for tile, fused in [(8, True), (32, True), (16, False)]:
-        g = run_gpu(wl, backward=False, tile=tile, fused=fused)
-        assert np.array_equal(g["img"], base["img"]), (tile, fused)
-        assert np.array_equal(g["gbuf"], base["gbuf"]), (tile, fused)
+    for tile, batch, fused in [(8, 32, True), (32, 32, True), (16, 32, False), (8, 64, True), (16, 64, True),
+                               (32, 64, True), (32, 64, False)]:
+        g = run_gpu(wl, backward=False, tile=tile, fused=fused, batch=batch)
+        assert np.array_equal(g["img"], base["img"]), (tile, batch, fused)
+        assert np.array_equal(g["gbuf"], base["gbuf"]), (tile, batch, fused)
+        if tile == 16:                 # list positions: the same lists only for the same tile edge
+            assert np.array_equal(g["last"], base["last"]), (tile, batch, fused)
+
+
+@pytest.mark.parametrize("tile,batch", [(8, 32), (32, 32), (8, 64), (16, 64), (32, 64)])
+def test_gradients_match_oracle_every_schedule(tile, batch):
+    """The one-warp backward at every tile edge and splat batch (ragged
+    200 x 200 image: 8/16/32 do not divide it evenly, or only at one edge)."""
+    wl = sg.make_workload("c2", N=20000, res=200)
+    ref0, dimg = _masked_dimg(wl, [0], seed=77)
+    ref = oracle_batch(wl, [0], dimg=dimg)
+    g = run_gpu(wl, dimg=dimg, tile=tile, batch=batch)
+    assert_image_close(g["img"], ref0["img"], flagged(ref0["margin"]))
+    assert_grads_close(g["grads"], ref["grads"], SCENE_KEYS)
 
 
 def test_batched_pairs_equal_single_pair_runs():
@@ -330,7 +346,48 @@ def test_uneven_batch_several_scenes_and_resolutions():
     assert len({(p.W, p.H) for p in wl.pairs}) > 1 and len(wl.scenes) == 8
 
 
-def test_autotuner_picks_a_measured_candidate():
-    wl = sg.make_workload("c4", N=3000, res=64, n_pairs=2)
-    best, t = PL.autotune_tile(wl, candidates=(16, 8), precision=B.FP32, steps=1)
-    assert best in (8, 16) and t[best] == min(t.values())
+def test_autotuner_picks_the_fastest_measured_candidate_per_scene():
+    """sssgs_autotune through autotune_schedule on an uneven batch of 8 scenes:
+    every (tile, batch) candidate of every scene is run and timed, and each
+    scene's schedule is its fastest candidate."""
+    wl = sg.make_workload("c5", N=20000, res=(40, 64, 88), n_pairs=2)
+    cfgs, table = PL.autotune_schedule(wl, precision=B.FP32, reps=1)
+    assert len(cfgs) == len(wl.scenes) == len(table)
+    for sc, res in table.items():
+        assert len(res) == 6 and {(x.tile, x.batch) for x in res} == {(t, b) for t in (8, 16, 32) for b in (32, 64)}
+        assert all(x.status == 0 and x.ms > 0 and x.reps == 1 and x.instances > 0 for x in res)
+        fastest = min(res, key=lambda x: x.ms)
+        assert (cfgs[sc].tile, cfgs[sc].batch) == (fastest.tile, fastest.batch)
+        # smaller tiles never give fewer instances
+        inst = {x.tile: x.instances for x in res}
+        assert inst[8] >= inst[16] >= inst[32]
+
+
+def test_per_scene_schedule_matches_oracle_and_single_schedule():
+    """A batch whose scenes run with different tile edges and batches (one run
+    of pairs per scene, each on its own stream, one captured graph): the
+    forward is bit-identical to the single-schedule batch and the gradients
+    match the oracle."""
+    wl = sg.make_workload("c5", N=20000, res=(40, 64, 88), n_pairs=2)
+    pid = list(range(len(wl.pairs)))
+    ref0, dimg = _masked_dimg(wl, pid, seed=41)
+    ref = oracle_batch(wl, pid, dimg=dimg)
+    cfgs = []
+    for sc in range(len(wl.scenes)):
+        c = PL.default_cfg((8, 16, 32)[sc % 3])
+        c.batch = (32, 64)[(sc // 3) % 2]
+        cfgs.append(c)
+    g = run_gpu(wl, precision=B.FP32, dimg=dimg, scene_cfgs=cfgs)
+    assert g["renderer"].groups is not None and len(g["renderer"].groups) == len(wl.scenes)
+    single = run_gpu(wl, precision=B.FP32, backward=False)
+    assert np.array_equal(g["img"], single["img"])
+    assert_image_close(g["img"], ref0["img"], flagged(ref0["margin"]))
+    assert_grads_close(g["grads"], ref["grads"], SCENE_KEYS)
+    # the same step replayed from a captured graph
+    r = g["renderer"]
+    graph = r.capture(dimg=torch.from_numpy(dimg.astype(np.float32)).cuda())
+    r.img.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    r.check_status()
+    assert np.array_equal(r.img.double().cpu().numpy(), single["img"])
