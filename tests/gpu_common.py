@@ -6,11 +6,16 @@ Tolerances (written here, used by every parity test):
                      decisions are not within float32 reach of a threshold
   gradients          per tensor ||g - r||_2 <= 1e-3 ||r||_2 and
                      max |g - r| <= 1e-3 max |r|
-A pixel is "flagged" when the oracle reports an alpha decision within 2e-4
-(relative) of alpha_min/alpha_max or a stop decision within 5e-4 of T_min:
+A pixel is "flagged" when the oracle reports an alpha decision within 1e-4
+(relative) of alpha_min/alpha_max or a stop decision within 1e-4 of T_min:
 float32 rounding of the conic, mean and exp can move such a decision, which
 changes the pixel by a finite jump. Flagged pixels are excluded from the image
 gate and get zero upstream gradient in the gradient tests (both sides).
+The margin is the narrowest of 1e-5, 3e-5, 1e-4 at which no unflagged pixel
+failed the image gate in a measurement over the 1K/128, 100K/512 and 300K/800
+single pairs and sampled pixels of the 64-pair and uneven batches (float32
+flips were seen up to 1.9e-5 on the 300K pair and at 3.5e-5 on the uneven
+batch); it flags about 0.5% of the pixels.
 """
 from __future__ import annotations
 
@@ -23,14 +28,15 @@ from paper_2408_12282_gb300 import pipeline as PL
 
 IMG_TOL = 1e-4
 GRAD_TOL = 1e-3
-FLAG_ALPHA = 2e-4
-FLAG_T = 5e-4
+FLAG_ALPHA = 1e-4
+FLAG_T = 1e-4
+MAX_FLAGGED = 0.01      # flagged pixels above this fraction fail a test
 
 
 def run_gpu(wl, precision=B.FP32, fused=True, tile=None, dimg=None, target=None, l1_scale=1.0,
-            weight=None, pair_slice=None, capacity=None, backward=True):
+            weight=None, pair_slice=None, capacity=None, backward=True, batch=None, scene_cfgs=None):
     r = PL.renderer_for_workload(wl, precision=precision, fused=fused, tile=tile, pair_slice=pair_slice,
-                                 capacity=capacity)
+                                 capacity=capacity, batch=batch, scene_cfgs=scene_cfgs)
     r.fit_capacity()
     r.forward()
     out = {}
@@ -47,7 +53,7 @@ def run_gpu(wl, precision=B.FP32, fused=True, tile=None, dimg=None, target=None,
     out["mlp_out"] = r.mlp_out.double().cpu().numpy()
     out["rec"] = r.rec.double().cpu().numpy()
     out["rect"] = r.rect.cpu().numpy()
-    out["count"] = int(r.count.item())
+    out["count"] = r.n_instances
     out["renderer"] = r
     if backward:
         out["grads"] = {k: v.double().cpu().numpy() for k, v in r.grads.items()}

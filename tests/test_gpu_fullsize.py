@@ -1,14 +1,23 @@
-"""Full-size parity, in the launch configuration the benchmark times.
+"""Full-size parity, in the launch configurations the benchmark times.
 
-* The 300K-Gaussian 800x800 pair (tensor-core network, fused kernels): every
-  pixel and every gradient tensor against the oracle with the BF16-emulating
-  network (gates of test_gpu_tc: bf16 decision flips are the only expected
-  differences).
-* The 64-pair 300K batch replayed from a captured CUDA graph with the fused
-  L1 loss, as in bench.py: sampled pixels of two pairs against the oracle, and
-  those pairs bit-identical to single-pair renders.
-* The same for the light-stage batch, the uneven batch of 50K-1M Gaussian
-  scenes at 400-1600 px, and the ray-traced visibility of the 64-pair batch.
+* The 300K-Gaussian 800x800 pair with the FP32 network through the fused
+  kernels: every unflagged pixel within 1e-4 and every gradient tensor within
+  rel-L2 1e-3 and max 1e-3 max|ref| of the FP64 oracle.
+* The same pair with the tensor-core (BF16) network against the oracle with
+  the BF16-emulating network: image max within 1e-4; gradients within 1e-3
+  rel-L2 and max, except the tensors listed in BF16_REL / BF16_MAX, whose
+  looser gates are set from a measurement of this pair (bf16 rounding and
+  ReLU decisions taken on float32 sums by the tensor cores and on FP64 sums by
+  the oracle differ for a few rows; they reach mu through the Fourier input,
+  whose derivative carries the 2^k pi factors of the encoding).
+* The 64-pair 300K batch, the light-stage batch and the uneven batch of
+  50K-1M Gaussian scenes at 400-1600 px, each replayed from a captured CUDA
+  graph as in bench.py: sampled pixels of four pairs against the oracle.
+  With the FP32 network the gate is the plain max 1e-4; with the BF16 network
+  99.9% of the sampled pixels within 1e-4 and all within 2e-4 (measured: 1 of
+  10,000 and 3 of 4,800 sampled pixels of the 64-pair batch at 1.06e-4 to
+  1.57e-4, none of them near a raster decision).
+* The ray-traced visibility of the 64-pair batch.
 """
 import numpy as np
 import pytest
@@ -16,11 +25,19 @@ import torch
 
 import oracle as O
 import scenegen as sg
-from gpu_common import flagged, grad_errors, oracle_batch, run_gpu
+from gpu_common import (MAX_FLAGGED, assert_grads_close, assert_image_close, flagged, grad_errors, oracle_batch,
+                        run_gpu)
 from paper_2408_12282_gb300 import binding as B
 from paper_2408_12282_gb300 import pipeline as PL
 
 pytestmark = pytest.mark.gpu
+
+# BF16 network vs the BF16-emulating oracle, 300K 800x800 pair (measured with
+# flag margin 1e-4: rel-L2 of v 1.3e-3; max of mu 5.4e-3, v 4.9e-3, W3
+# 2.1e-3, b3 1.5e-3; every other tensor within 1e-3 on both measures)
+BF16_REL = {"vis": 2e-3}
+BF16_MAX = {"mu": 1e-2, "vis": 1e-2, "W3": 3e-3, "b3": 3e-3}
+BF16_SAMPLE_P999, BF16_SAMPLE_MAX = 1e-4, 2e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,128 +45,154 @@ def _lib(gpu_lib):
     return gpu_lib
 
 
-def test_full_300k_800_pair_image_and_gradients():
+def test_full_300k_800_pair_fp32_strict():
+    """The 300K-Gaussian 800x800 pair with the FP32 network through the fused
+    render kernels, at the full gates: every unflagged pixel within 1e-4 of
+    the FP64 oracle (max, not a quantile), every gradient tensor -- the ten
+    scene tensors and every dW, db -- within rel-L2 1e-3 and max 1e-3 max|ref|."""
+    wl = sg.make_workload("c3")
+    ref0 = oracle_batch(wl, [0])
+    fl = flagged(ref0["margin"])
+    assert fl.mean() < MAX_FLAGGED
+    dimg = sg.random_dimg(123, ref0["img"].shape[0])
+    dimg[fl] = 0.0
+    ref = oracle_batch(wl, [0], dimg=dimg)
+    g = run_gpu(wl, precision=B.FP32, dimg=dimg)
+    worst = assert_image_close(g["img"], ref0["img"], fl)
+    assert_image_close(g["gbuf"], ref0["gbuf"], fl, what="gbuf")
+    rep = assert_grads_close(g["grads"], ref["grads"], PL.SCENE_KEYS)
+    for l in range(len(g["dW"])):
+        rep.update(assert_grads_close({f"W{l}": g["dW"][l], f"b{l}": g["db"][l]},
+                                      {f"W{l}": ref["dW"][l], f"b{l}": ref["db"][l]}, [f"W{l}", f"b{l}"]))
+    print(f"\nfull 300K/800 FP32: {fl.mean():.2%} flagged, image max {worst:.2e}; gradients (rel-L2, max):",
+          {k: f"{a:.1e}/{b:.1e}" for k, (a, b) in rep.items()})
+
+
+def test_full_300k_800_pair_bf16():
+    """The same pair with the tensor-core network against the oracle's
+    BF16-emulating network: image max within 1e-4 on every unflagged pixel;
+    gradients per tensor at 1e-3 (rel-L2 and max), with the measured
+    exceptions of BF16_REL / BF16_MAX. The error against the pure FP64 network
+    is printed per image and per tensor for the record."""
     wl = sg.make_workload("c3")
     ref0 = oracle_batch(wl, [0], bf16=True)
     fl = flagged(ref0["margin"])
+    assert fl.mean() < MAX_FLAGGED
     dimg = sg.random_dimg(123, ref0["img"].shape[0])
     dimg[fl] = 0.0
     ref = oracle_batch(wl, [0], dimg=dimg, bf16=True)
     g = run_gpu(wl, precision=B.BF16, dimg=dimg)
-    ok = ~fl
-    e = np.abs(g["img"][ok] - ref0["img"][ok]).max(axis=1)
-    print(f"\nfull 300K/800 pair: {fl.mean():.2%} flagged; image max {e.max():.2e} p99.9 {np.quantile(e, 0.999):.2e}")
-    assert fl.mean() < 0.05
-    assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 5e-3
-    errs = {k: grad_errors(g["grads"][k], ref["grads"][k])[0] for k in PL.SCENE_KEYS}
-    errs.update({f"W{l}": grad_errors(g["dW"][l], ref["dW"][l])[0] for l in range(len(g["dW"]))})
-    print("gradient rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
-    assert all(v <= 2e-3 for v in errs.values()), errs
+    worst = assert_image_close(g["img"], ref0["img"], fl)
+    errs = {k: grad_errors(g["grads"][k], ref["grads"][k]) for k in PL.SCENE_KEYS}
+    for l in range(len(g["dW"])):
+        errs[f"W{l}"] = grad_errors(g["dW"][l], ref["dW"][l])
+        errs[f"b{l}"] = grad_errors(g["db"][l], ref["db"][l])
+    print(f"\nfull 300K/800 BF16: {fl.mean():.2%} flagged, image max {worst:.2e}; gradients (rel-L2, max):",
+          {k: f"{a:.1e}/{b:.1e}" for k, (a, b) in errs.items()})
+    bad = {k: v for k, v in errs.items() if v[0] > BF16_REL.get(k, 1e-3) or v[1] > BF16_MAX.get(k, 1e-3)}
+    assert not bad, bad
 
 
-def test_full_64_pair_batch_graph_replay_sampled():
-    wl = sg.make_workload("c4")
-    r = PL.renderer_for_workload(wl, precision=B.BF16)
+def _graph_batch(wl, precision, multilight=False):
+    if multilight:
+        r = PL.multilight_renderer_for_workload(wl, precision=precision)
+        n_px = r.pairs.n_pixels
+    else:
+        r = PL.renderer_for_workload(wl, precision=precision)
+        n_px = r.table.n_pixels
     r.fit_capacity()
-    target = torch.zeros(r.table.n_pixels, 3, device="cuda")
-    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * r.table.n_pixels))
+    target = torch.zeros(n_px, 3, device="cuda")
+    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * n_px))
     graph.replay()
     graph.replay()
     torch.cuda.synchronize()
     r.check_status()
-    img = r.img.double().cpu().numpy()
-    rng = np.random.default_rng(5)
-    off = 0
+    return r
+
+
+def _sampled_errors(wl, img, pairs, n_px, seed, bf16):
+    """|gpu - oracle| / max(1, |oracle|) per sampled unflagged pixel of the
+    given pairs, and the flagged fraction."""
     offs = [0]
     for p in wl.pairs:
         offs.append(offs[-1] + p.W * p.H)
-    for p in (7, 41):
+    rng = np.random.default_rng(seed)
+    es, fls = [], []
+    for p in pairs:
         pair = wl.pairs[p]
         pix = O.all_pixels(pair.W, pair.H)
-        sel = rng.choice(len(pix), 1500, replace=False)
-        res = O.render_pair(wl.scenes[0], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=True)
+        sel = rng.choice(len(pix), min(n_px, len(pix)), replace=False)
+        res = O.render_pair(wl.scenes[pair.scene], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=bf16)
+        assert (res["ncontrib"] > 0).mean() > 0.05
         fl = flagged(res["margin"])
         got = img[offs[p] + sel]
-        e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
-        print(f"\npair {p}: {fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
-        assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
-        one = PL.renderer_for_workload(wl, precision=B.BF16, pair_slice=slice(p, p + 1))
-        one.fit_capacity()
-        one.forward()
-        torch.cuda.synchronize()
-        assert torch.equal(one.img, r.img[offs[p]:offs[p + 1]])
-        del one
-        torch.cuda.empty_cache()
+        e = (np.abs(got - res["img"]) / np.maximum(1.0, np.abs(res["img"]))).max(axis=1)
+        es.append(e[~fl])
+        fls.append(fl)
+    return np.concatenate(es), float(np.concatenate(fls).mean())
+
+
+def _check_sampled(tag, e, flag_frac, bf16):
+    print(f"\n{tag}: {e.size} sampled pixels, {flag_frac:.2%} flagged, max {e.max():.2e}, "
+          f"p99.9 {np.quantile(e, 0.999):.2e}, above 1e-4: {int((e > 1e-4).sum())}")
+    assert flag_frac < MAX_FLAGGED
+    if bf16:
+        assert np.quantile(e, 0.999) <= BF16_SAMPLE_P999 and e.max() <= BF16_SAMPLE_MAX
+    else:
+        assert e.max() <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [B.FP32, B.BF16])
+def test_full_64_pair_batch_graph_replay_sampled(precision):
+    """The 64-pair 300K batch (800x800) replayed from a captured graph with the
+    fused L1 loss: 1,000 sampled pixels of each of four pairs against the
+    oracle, and two pairs bit-identical to single-pair renders."""
+    wl = sg.make_workload("c4")
+    r = _graph_batch(wl, precision)
+    img = r.img.double().cpu().numpy()
+    bf16 = precision == B.BF16
+    e, ff = _sampled_errors(wl, img, (7, 20, 41, 63), 1000, 5, bf16)
+    _check_sampled(f"64-pair batch ({'BF16' if bf16 else 'FP32'} network)", e, ff, bf16)
+    if bf16:
+        offs = [0]
+        for p in wl.pairs:
+            offs.append(offs[-1] + p.W * p.H)
+        for p in (7, 41):
+            one = PL.renderer_for_workload(wl, precision=B.BF16, pair_slice=slice(p, p + 1))
+            one.fit_capacity()
+            one.forward()
+            torch.cuda.synchronize()
+            assert torch.equal(one.img, r.img[offs[p]:offs[p + 1]])
+            del one
+            torch.cuda.empty_cache()
 
 
 def test_full_light_stage_batch_graph_replay_sampled():
     """The 8 views x 8 lights light-stage batch (300K, 800x800) through the
     many-light kernels, replayed from a captured graph with the fused L1 loss
-    as in bench.py: sampled pixels of two (view, light) pairs against the
-    oracle rendering that pair on its own."""
-    import oracle as O2
+    as in bench.py: 1,000 sampled pixels of each of four (view, light) pairs
+    against the oracle rendering that pair on its own."""
     wl = sg.make_workload("c6")
-    r = PL.multilight_renderer_for_workload(wl, precision=B.BF16)
-    r.fit_capacity()
-    target = torch.zeros(r.pairs.n_pixels, 3, device="cuda")
-    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * r.pairs.n_pixels))
-    graph.replay()
-    graph.replay()
-    torch.cuda.synchronize()
-    r.check_status()
-    img = r.img.double().cpu().numpy()
+    r = _graph_batch(wl, B.BF16, multilight=True)
     assert np.isfinite(r.grads["mu"].cpu().numpy()).all()
-    rng = np.random.default_rng(6)
-    offs = [0]
-    for p in wl.pairs:
-        offs.append(offs[-1] + p.W * p.H)
-    for p in (3, 58):                  # view 0 light 3, view 7 light 2
-        pair = wl.pairs[p]
-        pix = O2.all_pixels(pair.W, pair.H)
-        sel = rng.choice(len(pix), 1500, replace=False)
-        res = O2.render_pair(wl.scenes[0], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=True)
-        fl = flagged(res["margin"])
-        got = img[offs[p] + sel]
-        e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
-        print(f"\nlight-stage pair {p}: {fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
-        assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
+    e, ff = _sampled_errors(wl, r.img.double().cpu().numpy(), (3, 21, 40, 58), 1000, 6, True)
+    _check_sampled("light-stage batch (BF16 network)", e, ff, True)
 
 
-def test_full_uneven_batch_graph_replay_sampled():
+@pytest.mark.parametrize("precision", [B.FP32, B.BF16])
+def test_full_uneven_batch_graph_replay_sampled(precision):
     """The uneven batch (8 scenes of 50K-1M Gaussians, 8 pairs each at
-    400-1600 px) replayed from a captured graph with the fused L1 loss, as in
-    bench.py: sampled pixels of the smallest scene's first image and of the
-    1M-Gaussian scene's largest image against the oracle rendering that pair
-    on its own."""
+    400-1600 px) replayed from a captured graph with the fused L1 loss:
+    sampled pixels of the smallest scene's first image, the 1M-Gaussian
+    scene's largest image and two more pairs against the oracle."""
     wl = sg.make_workload("c5")
-    r = PL.renderer_for_workload(wl, precision=B.BF16)
-    r.fit_capacity()
-    target = torch.zeros(r.table.n_pixels, 3, device="cuda")
-    graph = r.capture(target=target, l1_scale=1.0 / (3.0 * r.table.n_pixels))
-    graph.replay()
-    graph.replay()
-    torch.cuda.synchronize()
-    r.check_status()
-    img = r.img.double().cpu().numpy()
+    r = _graph_batch(wl, precision)
     assert all(torch.isfinite(g).all().item() for g in r.grads.values())
-    offs = [0]
-    for p in wl.pairs:
-        offs.append(offs[-1] + p.W * p.H)
     small = next(p for p, q in enumerate(wl.pairs) if q.scene == 0)
     big = max((p for p, q in enumerate(wl.pairs) if q.scene == len(wl.scenes) - 1), key=lambda p: wl.pairs[p].W)
-    rng = np.random.default_rng(8)
-    for p in (small, big):
-        pair = wl.pairs[p]
-        pix = O.all_pixels(pair.W, pair.H)
-        sel = rng.choice(len(pix), 1500, replace=False)
-        res = O.render_pair(wl.scenes[pair.scene], pair, wl.mlp, pixels=pix[sel].astype(np.int32), bf16=True)
-        fl = flagged(res["margin"])
-        got = img[offs[p] + sel]
-        e = np.abs(got[~fl] - res["img"][~fl]).max(axis=1)
-        print(f"\nuneven batch pair {p} (scene {pair.scene}, {wl.scenes[pair.scene].N} Gaussians, {pair.W}x{pair.H}): "
-              f"{fl.mean():.2%} flagged, max {e.max():.2e}, p99 {np.quantile(e, 0.99):.2e}")
-        assert (res["ncontrib"] > 0).mean() > 0.05
-        assert np.quantile(e, 0.99) <= 1e-4 and e.max() <= 5e-3
+    bf16 = precision == B.BF16
+    e, ff = _sampled_errors(wl, r.img.double().cpu().numpy(), (small, 17, 38, big), 1000, 8, bf16)
+    _check_sampled(f"uneven batch ({'BF16' if bf16 else 'FP32'} network)", e, ff, bf16)
 
 
 def test_full_batch_visibility_trace_sampled():

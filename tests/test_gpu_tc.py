@@ -75,10 +75,11 @@ def test_bf16_network_backward_matches_bf16_oracle(N, n_pairs, zero_frac):
     within ~1e-4 of zero (relative to the layer) changes sign when an
     upstream bf16 rounding flips, which changes that row's gradient by a
     finite amount. Re-running the oracle's bf16 network with FP32 instead of
-    FP64 sums reproduces the same spread (about 8e-4 relative per tensor at
-    40K rows), so the gate is: per tensor rel-L2 <= 2e-3 at 40K rows, and at
-    9K rows (where one such row weighs more) at most 0.1% of rows off by more
-    than 1e-2 relative and rel-L2 <= 1e-2.
+    FP64 sums reproduces the same spread, so the gate is: at 40K rows weight
+    and bias gradients rel-L2 <= 1e-3 (measured at most 8.1e-4) and the input
+    gradients <= 1.5e-3 (measured 1.03e-3); at 9K rows (where one such row
+    weighs more) at most 0.1% of rows off by more than 1e-2 relative and
+    rel-L2 <= 1e-2.
 
     With zero_frac > 0 that fraction of rows gets a zero upstream gradient
     (what occluded Gaussians get): the kernel leaves them out, and their input
@@ -127,7 +128,7 @@ def test_bf16_network_backward_matches_bf16_oracle(N, n_pairs, zero_frac):
     print("\nbf16 backward rel-L2 errors:", {k: f"{v:.2e}" for k, v in errs.items()},
           f"rows >1e-2: {frac_bad:.4%}")
     if int((~zero).sum()) >= 40000:
-        assert all(v < 2e-3 for v in errs.values()), errs
+        assert all(v < (1.5e-3 if k == "dx" else 1e-3) for k, v in errs.items()), errs
     else:
         assert frac_bad <= 1e-3
         assert all(v < 1e-2 for v in errs.values()), errs
@@ -138,11 +139,14 @@ def test_bf16_pipeline_image_and_gradients():
     reduced to 20K Gaussians x 2 pairs at 96x96) vs the oracle with the
     BF16-emulating network. Raster-flagged pixels (see gpu_common) are
     excluded and get zero upstream gradient. bf16 decisions that flip between
-    float32 and FP64 sums move a Gaussian's L_SSS / L_in by up to ~1e-2, which
-    reaches a pixel weighted by that Gaussian's compositing weight, so the
-    image gate is statistical: 99.9% of pixels within 1e-4, all within 5e-3.
-    Gradients: per tensor rel-L2 <= 2e-3. The error against the FP64 network
-    is printed for the record."""
+    float32 and FP64 sums move a Gaussian's L_SSS / L_in by a few bf16 ulps,
+    which reaches a pixel weighted by that Gaussian's compositing weight: the
+    image gate is 99.9% of pixels within 1e-4 and all within 2e-4 (the
+    measured worst pixels of the full-size batches are at 1.1-1.6e-4).
+    Gradients: per tensor rel-L2 <= 1e-3, and 2e-3 for mu and v, which reach
+    the network through its inputs (measured here 1.3e-3 and 1.2e-3; 3.6e-4
+    and 1.3e-3 on the full-size pair). The error against the FP64 network is
+    printed for the record."""
     from gpu_common import flagged, oracle_batch, run_gpu, grad_errors
     wl = sg.make_workload("c4", N=20000, res=96, n_pairs=2)
     ref0 = oracle_batch(wl, [0, 1], bf16=True)
@@ -163,6 +167,6 @@ def test_bf16_pipeline_image_and_gradients():
     print("grad rel-L2 vs bf16 oracle:", {k: f"{v:.1e}" for k, v in gerr.items()})
     print("grad rel-L2 vs fp64 oracle:", {k: f"{v:.1e}" for k, v in gerr64.items()})
     print("dW rel-L2 vs bf16 oracle:", [f"{v:.1e}" for v in werr])
-    assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 5e-3
-    assert all(v <= 2e-3 for v in gerr.values()), gerr
-    assert all(v <= 2e-3 for v in werr), werr
+    assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 2e-4
+    assert all(v <= (2e-3 if k in ("mu", "vis") else 1e-3) for k, v in gerr.items()), gerr
+    assert all(v <= 1e-3 for v in werr), werr
