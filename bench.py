@@ -101,7 +101,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------------------- CPU oracle sample
+# ---------------------------------------------------------------------------- CPU leg (the oracle)
+#
+# The oracle runs only here, in subprocesses on the host cores: (1) the timed
+# CPU baseline, (2) the reference arm, (3) the oracle's values at pixels
+# sampled from the timed GPU batch, which the bench compares with the batch's
+# images (the `parity` object of the JSON line).
 
 _CPU_SAMPLE = r"""
 import json, sys, time
@@ -129,18 +134,63 @@ full = t_mlp + t_raster * stride
 print(json.dumps({"t_mlp": t_mlp, "t_sample": t_all, "t_full_est": full, "pixels": int(sel.shape[0])}))
 """
 
+_CPU_PARITY = r"""
+import json, sys, time
+sys.path.insert(0, ROOT)
+import numpy as np
+import scenegen as sg, oracle as O
+wl = sg.make_workload(WORKLOAD, net=NET, n_pairs=N_PAIRS)
+spec = np.load(SPEC)
+out = {}
+t0 = time.perf_counter()
+for p in spec["pairs"].tolist():
+    pr = wl.pairs[p]
+    px = np.ascontiguousarray(spec[f"pix_{p}"], np.int32)
+    r = O.render_pair(wl.scenes[pr.scene], pr, wl.mlp, pixels=px, bf16=BF16)
+    out[f"img_{p}"] = r["img"]
+    out[f"margin_{p}"] = r["margin"]
+    if BF16:
+        out[f"img64_{p}"] = O.render_pair(wl.scenes[pr.scene], pr, wl.mlp, pixels=px)["img"]
+np.savez(OUT, **out)
+print(json.dumps({"t": time.perf_counter() - t0}))
+"""
 
-def cpu_oracle_sample(workload: str, stride: int, threads: int, net=None):
+
+def _run_cpu(code, threads):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = (_CPU_SAMPLE.replace("ROOT", repr(ROOT)).replace("WORKLOAD", repr(workload)).replace("STRIDE", str(stride))
-            .replace("NET", repr(net)))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_oracle_sample(workload: str, stride: int, threads: int, net=None):
+    code = (_CPU_SAMPLE.replace("ROOT", repr(ROOT)).replace("WORKLOAD", repr(workload)).replace("STRIDE", str(stride))
+            .replace("NET", repr(net)))
+    return _run_cpu(code, threads)
+
+
+def cpu_oracle_pixels(workload: str, net, n_pairs, pixels: dict, bf16: bool):
+    """The oracle's image values at the given pixels {pair: (n x 2) int array}
+    of the workload (with the BF16-emulating network if bf16, plus the pure
+    FP64 network's values), and the decision margins; all host cores."""
+    import tempfile
+    import numpy as np
+    with tempfile.TemporaryDirectory() as td:
+        spec = os.path.join(td, "spec.npz")
+        res = os.path.join(td, "out.npz")
+        np.savez(spec, pairs=np.array(sorted(pixels)), **{f"pix_{p}": v for p, v in pixels.items()})
+        code = (_CPU_PARITY.replace("ROOT", repr(ROOT)).replace("WORKLOAD", repr(workload))
+                .replace("NET", repr(net)).replace("N_PAIRS", repr(n_pairs)).replace("SPEC", repr(spec))
+                .replace("OUT", repr(res))
+                .replace("BF16", repr(bool(bf16))))
+        t = _run_cpu(code, os.cpu_count() or 1)
+        with np.load(res) as z:
+            got = {k: z[k] for k in z.files}
+    return got, t["t"]
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -151,18 +201,25 @@ def run_reference(args):
         return
     threads = os.cpu_count() or 1
     stride = 16
-    times = []
+    times, walls = [], []
     for i in range(args.warmup + args.steps):
+        w0 = time.perf_counter()
         d = cpu_oracle_sample(args.workload, stride, threads, args.net)
+        w1 = time.perf_counter()
         if i >= args.warmup:
             times.append(d["t_full_est"])
+            walls.append(w1 - w0)
     t = sum(times) / len(times)
     value = 1.0 / t
-    sample = (f"one view/light pair of workload {args.workload}: full network fwd+bwd over all Gaussians "
-              f"(numpy, {threads} BLAS threads), raster fwd+bwd on every {stride}th pixel row (C, one thread), "
-              f"raster time scaled by {stride}")
+    wall = sum(walls) / len(walls)
+    sample = (f"one view/light pair of workload {args.workload} per step: full network fwd+bwd over all Gaussians "
+              f"(numpy, {threads} BLAS threads) and raster fwd+bwd on every {stride}th pixel row (C, one thread); "
+              f"value = 1 / (network time + {stride} x raster-sample time), an extrapolation to a whole render "
+              f"({t:.1f} s); ms_per_step is the measured wall time of one sample step (process start and scene "
+              f"generation included)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall,
+            "extrapolated_s_per_render": t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
@@ -183,7 +240,9 @@ def _config(args):
               "8 lights each of the 112-light stage (7 rings x 16, r=4 upper hemisphere), 800x800, PE6 MLP "
               "64-128x4-4; geometry shared by the lights of a view",
     }
-    cfg = {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": args.tile,
+    tile = ("per scene, autotuned (see schedule)" if args.tile == "auto" and args.shading == "deferred"
+            and not getattr(args, "vis_sh", False) else (16 if args.tile == "auto" else int(args.tile)))
+    cfg = {"workload": f"{args.workload}: {desc.get(args.workload, args.workload)}", "tile": tile,
            "loss": ("App. E: 0.8 L1 + 0.2 D-SSIM vs target rendered from perturbed parameters "
                     "+ 0.02 incident-light constraint" if args.loss == "paper"
                     else "L1 vs target rendered from perturbed parameters"),
@@ -262,8 +321,11 @@ def render_source_sha():
     return h.hexdigest()
 
 
-def kernel_traffic(stage, workload, n_pairs):
-    if stage not in KERNEL_TRAFFIC or workload not in ("c3", "c4"):
+def kernel_traffic(stage, workload, n_pairs, tile_batch=(16, 32)):
+    """DRAM bytes of one launch of a fused render kernel on this workload:
+    only for the kernel source and the schedule (16 x 16 tiles, batches of 32
+    splats) the capture was taken on; None otherwise."""
+    if stage not in KERNEL_TRAFFIC or workload not in ("c3", "c4") or tuple(tile_batch) != (16, 32):
         return None
     sha, per_pair = KERNEL_TRAFFIC[stage]
     if render_source_sha() != sha:
@@ -276,6 +338,53 @@ def mlp_flops(widths, rows):
     for a, b in zip(widths[:-1], widths[1:]):
         f += 2 * a * b
     return f * rows
+
+
+# Parity of the timed batch: pixels whose oracle alpha or stop decision lies
+# within this relative distance of its threshold can flip between float32
+# and FP64 (a finite jump) and are counted but left out of the gate (the
+# margin of the parity tests). Gate: every sampled pixel within 1e-4 of the
+# oracle; with the BF16 network against the BF16-emulating oracle, 99.9%
+# within 1e-4 and all within 2e-4 (the tests' gate for the batches).
+PARITY_FLAG_MARGIN = 1e-4
+PARITY_GATE = 1e-4
+PARITY_GATE_BF16_MAX = 2e-4
+
+
+def parity_report(args, n_pairs, par_pix, par_got, bf16):
+    import numpy as np
+    try:
+        ref, t_par = cpu_oracle_pixels(args.workload, args.net, args.pairs, par_pix, bf16)
+    except Exception as ex:  # report, do not hide
+        return {"error": f"{ex}"[:300]}
+    e_all, e64_all, n_flag = [], [], 0
+    for p in par_pix:
+        rimg = ref[f"img_{p}"]
+        m = ref[f"margin_{p}"]
+        fl = (m[:, 0] < PARITY_FLAG_MARGIN) | (m[:, 1] < PARITY_FLAG_MARGIN)
+        n_flag += int(fl.sum())
+        e = (np.abs(par_got[p] - rimg) / np.maximum(1.0, np.abs(rimg))).max(axis=1)
+        e_all.append(e[~fl])
+        if bf16:
+            r64 = ref[f"img64_{p}"]
+            e64_all.append((np.abs(par_got[p] - r64) / np.maximum(1.0, np.abs(r64))).max(axis=1)[~fl])
+    e = np.concatenate(e_all)
+    p999 = float(np.quantile(e, 0.999))
+    ok = (p999 <= PARITY_GATE and e.max() <= PARITY_GATE_BF16_MAX) if bf16 else e.max() <= PARITY_GATE
+    out = {"pairs": sorted(par_pix), "pixels": int(sum(len(v) for v in par_pix.values())),
+           "flag_margin": PARITY_FLAG_MARGIN, "flagged": n_flag,
+           "gate": (f"p99.9 <= {PARITY_GATE}, max <= {PARITY_GATE_BF16_MAX}" if bf16 else f"max <= {PARITY_GATE}"),
+           "max_err": float(e.max()), "p999_err": p999,
+           "failing": int((e > PARITY_GATE).sum()), "pass": bool(ok),
+           "oracle": ("FP64 raster with the BF16-emulating network (the GPU's network precision)" if bf16
+                      else "FP64 raster and network"),
+           "what": "max over the sampled unflagged pixels of |gpu - oracle| / max(1, |oracle|), per channel, "
+                   "taken from the images of the last timed step", "oracle_seconds": t_par}
+    if bf16:
+        e64 = np.concatenate(e64_all)
+        out["vs_fp64_network"] = {"max_err": float(e64.max()), "p999_err": float(np.quantile(e64, 0.999)),
+                                  "mean_err": float(e64.mean())}
+    return out
 
 
 def run_ours(args):
@@ -299,8 +408,23 @@ def run_ours(args):
     wl = sg.make_workload(args.workload, seed_offset=rank, n_pairs=args.pairs, net=args.net)
     precision = B.BF16 if (wl.mlp.precision == "bf16" and not args.fp32_mlp) else B.FP32
     vis_sh = sg.vis_sh_coeffs(77 + rank, sum(sc.N for sc in wl.scenes)) if args.vis_sh else None
-    r = PL.renderer_for_workload(wl, precision=precision, tile=args.tile, vis_sh=vis_sh, shading=args.shading)
+    # schedule: tile edge and per-block splat batch per scene, measured by the
+    # library's autotuner (deferred path), or fixed by --tile / --batch
+    scene_cfgs, tune = None, None
+    tile_fixed = None if args.tile == "auto" else int(args.tile)
+    if tile_fixed is None and (args.shading != "deferred" or args.vis_sh):
+        tile_fixed = 16                 # the per-run schedule covers the fused deferred path only
+    if tile_fixed is None:
+        scene_cfgs, tune = PL.autotune_schedule(wl, precision=precision, reps=3)
+    r = PL.renderer_for_workload(wl, precision=precision, tile=tile_fixed, batch=args.batch, vis_sh=vis_sh,
+                                 shading=args.shading, scene_cfgs=scene_cfgs)
     n_inst = r.fit_capacity()
+    schedule = None
+    if scene_cfgs is not None:
+        schedule = [{"scene": sc, "gaussians": wl.scenes[sc].N, "tile": c.tile, "batch": c.batch,
+                     "candidates_ms": {f"{x.tile}x{x.tile}/{x.batch}": (round(x.ms, 4) if x.status == 0 else None)
+                                       for x in tune[sc]}}
+                    for sc, c in enumerate(scene_cfgs)]
     trace = None
     if args.vis_sh:
         # ray-traced visibility target (BVH build + one ray per item), timed once
@@ -323,14 +447,13 @@ def run_ours(args):
     tgt_scenes = ([wl.target_scene] if wl.target_scene is not None and len(wl.scenes) == 1 else
                   [sg.perturbed(s, 4242 + 97 * rank + i) for i, s in enumerate(wl.scenes)])
     wl_t = sg.Workload(wl.name, tgt_scenes, wl.pairs, wl.mlp, wl.tile)
-    rt = PL.renderer_for_workload(wl_t, precision=precision, tile=args.tile)
+    rt = PL.renderer_for_workload(wl_t, precision=precision)
     rt.fit_capacity()
     rt.forward()
     target = rt.img.clone()
     del rt
     torch.cuda.empty_cache()
     l1_scale = 1.0 / (3.0 * table.n_pixels)
-    grads_flat = [g for g in r.grads.values()] + r.dW + r.db
 
     graph = None
     graph_launches = 0
@@ -346,7 +469,7 @@ def run_ours(args):
             r.forward()
             r.backward(target=target, l1_scale=l1_scale, loss=args.loss)
         if world > 1:
-            PL.allreduce_gradients(grads_flat)
+            r.exchange_gradients()
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -376,6 +499,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = graph_launches if graph is not None else (B.launch_count() - l0) // args.steps
     clocks = sampler.stop()
+    # pixels sampled from the timed batch's images for the parity check (the
+    # oracle's values come from the CPU leg below)
+    par_pix, par_got = {}, {}
+    parity_ok = args.shading == "deferred" and not args.vis_sh
+    if rank == 0 and world == 1 and not args.skip_cpu and parity_ok and args.parity_pixels > 0:
+        import numpy as np
+        rng = np.random.default_rng(2024)
+        picks = sorted(set(np.linspace(0, n_pairs - 1, min(4, n_pairs)).round().astype(int).tolist()))
+        for p in picks:
+            pr = table.h[p]
+            n_px = pr.W * pr.H
+            sel = np.sort(rng.choice(n_px, min(args.parity_pixels, n_px), replace=False))
+            par_pix[p] = np.stack([sel % pr.W, sel // pr.W], 1).astype(np.int32)
+            idx = torch.from_numpy(pr.pixel_offset + sel).to("cuda")
+            par_got[p] = r.img[idx].double().cpu().numpy()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
@@ -393,6 +531,7 @@ def run_ours(args):
     stats_b = torch.zeros(2, dtype=torch.int64, device="cuda")
     if args.vis_sh:
         stage_ms["vis_sh"] = 0.0
+    r.stats_fwd, r.stats_bwd = stats_f, stats_b
     for _ in range(reps if args.shading == "deferred" else 0):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
         ev_v = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -401,13 +540,13 @@ def run_ours(args):
             B.vis_sh_fwd(table.h, table.d, r._scene_s, r.vis_sh, r.vis_item)
             ev_v[1].record(st)
         ev[0].record(st)
-        B.mlp_fwd(r._mlp_s, table.h, table.d, r._scene_s, r.mlp_out, r.status)
+        r.run_stage("mlp_fwd")
         ev[1].record(st)
-        B.project_fwd(r.cfg, table.h, table.d, r._scene_s, r.mlp_out, r.rec, r.rect)
+        r.run_stage("project_fwd")
         ev[2].record(st)
-        B.bin_sort(r.cfg, table.h, table.d, r.rec, r.rect, r.capacity, r.vals, r.ranges, r.count, r.status, r.ws_bin)
+        r.run_stage("bin_sort")
         ev[3].record(st)
-        B.render_fwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, stats_f)
+        r.run_stage("render_fwd")
         ev[4].record(st)
         r.zero_grads()
         e_z = torch.cuda.Event(enable_timing=True)
@@ -419,18 +558,16 @@ def run_ours(args):
             e_l[1].record(st)
         e_z.record(st)
         if args.loss == "paper":
-            B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, r.dimg_loss,
-                         None, None, 1.0, r.drec, stats_b)
+            r.run_stage("render_bwd", dimg=r.dimg_loss)
             e_l[2].record(st)
             B.incident_loss(table.h, table.d, r.rec, 0.02, r.drec, r.loss)
             e_l[3].record(st)
         else:
-            B.render_bwd(r.cfg, table.h, table.d, r.rec, r.vals, r.ranges, r.gbuf, r.last, r.img, None, target,
-                         None, l1_scale, r.drec, stats_b)
+            r.run_stage("render_bwd", target=target, l1_scale=l1_scale)
         ev[5].record(st)
-        B.mlp_bwd(r._mlp_s, table.h, table.d, r._scene_s, r.drec, r._mlp_g, r.dx_items, r.ws_mlp, r.status)
+        r.run_stage("mlp_bwd")
         ev[6].record(st)
-        B.project_bwd(r.cfg, table.h, table.d, r._scene_s, r.drec, r.dx_items, r._grad_s)
+        r.run_stage("project_bwd")
         ev[7].record(st)
         if args.vis_sh:
             ev_v[2].record(st)
@@ -484,7 +621,8 @@ def run_ours(args):
     elif dom in alu_flops:
         ach = alu_flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / ALU_PEAK_TFLOPS, "traffic": kernel_traffic(dom, args.workload, n_pairs),
+                "frac": ach / ALU_PEAK_TFLOPS, "traffic": kernel_traffic(dom, args.workload, n_pairs, (r.cfg.tile, r.cfg.batch) if r.groups is None
+                                          else (0, 0)),
                 "traffic_unit": "DRAM bytes per launch (ncu on an 8-pair launch, scaled per pair)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
                 "work": {"contributions": contrib_b if dom == "render_bwd" else contrib_f,
@@ -508,35 +646,80 @@ def run_ours(args):
                      "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "algorithmic_bytes": by}
     step_hbm_frac = total_bytes / (ms_max * 1e-3) / 1e9 / hbm
 
-    # ---------------- plain unbatched FP32 path (per-pair launches, unfused, CUDA-core network)
+    # ---------------- the same step with the untuned schedule (16 x 16 tiles, 32-splat batches)
+    untuned = None
+    if schedule is not None and any((c["tile"], c["batch"]) != (16, 32) for c in schedule) and not args.no_graph:
+        r0 = PL.renderer_for_workload(wl, precision=precision, tile=16, batch=32)
+        r0.fit_capacity()
+        g0 = r0.capture(target=target, l1_scale=l1_scale, loss=args.loss)
+        for _ in range(max(args.warmup, 3)):
+            g0.replay()
+        torch.cuda.synchronize()
+        u0 = torch.cuda.Event(enable_timing=True)
+        u1 = torch.cuda.Event(enable_timing=True)
+        u0.record(st)
+        for _ in range(args.steps):
+            g0.replay()
+        u1.record(st)
+        torch.cuda.synchronize()
+        ums = u0.elapsed_time(u1) / args.steps
+        untuned = {"renders_per_s": n_pairs * 1000.0 / ums, "ms_per_step": ums,
+                   "what": "the same step with every scene on 16 x 16 tiles and 32-splat batches"}
+        del r0, g0
+        torch.cuda.empty_cache()
+
+    # ---------------- unbatched per-pair paths: the plain FP32 baseline, and the
+    # same with the tensor-core network, and with the fused kernels, which
+    # split the batched path's speedup into network, fusion and batching
     plain = None
+    speedup_split = None
     if not args.skip_plain:
         k = min(args.plain_pairs, n_pairs)
-        rp = PL.renderer_for_workload(wl, precision=B.FP32, fused=False, tile=args.tile, pair_slice=slice(0, 1))
-        rp.fit_capacity()
-        rp.set_capacity(int(1.5 * n_inst / n_pairs) + 4096)
-        tables = [PL.PairTable([wl.pairs[i]], rp.cfg, [0], [n_gauss]) for i in range(k)]
-        dimg_p = torch.full((rp.table.n_pixels, 3), l1_scale, device="cuda")
+        reps_p = 3
 
-        def plain_step():
-            for tb in tables:
-                rp.table = tb
-                rp.forward()
-                rp.backward(dimg=dimg_p)
-        plain_step()
-        torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(st)
-        plain_step()
-        p1.record(st)
-        torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1)
-        plain = {"renders_per_s": k * 1000.0 / pms, "pairs_timed": k,
-                 "what": "per-pair launches, unfused composite and shade, FP32 CUDA-core network",
-                 "speedup_of_batched": value / world / (k * 1000.0 / pms)}
-        del rp
-        torch.cuda.empty_cache()
+        def per_pair(prec, fused):
+            # one renderer per pair, each with buffers of its own pair's size
+            rends = []
+            for i in range(k):
+                rp = PL.renderer_for_workload(wl, precision=prec, fused=fused, tile=16,
+                                              pair_slice=slice(i, i + 1))
+                rp.fit_capacity()
+                rends.append((rp, torch.full((rp.table.n_pixels, 3), l1_scale, device="cuda")))
+
+            def run():
+                for rp, d in rends:
+                    rp.forward()
+                    rp.backward(dimg=d)
+            run()
+            torch.cuda.synchronize()
+            rates = []
+            for _ in range(reps_p):
+                p0 = torch.cuda.Event(enable_timing=True)
+                p1 = torch.cuda.Event(enable_timing=True)
+                p0.record(st)
+                run()
+                p1.record(st)
+                torch.cuda.synchronize()
+                rates.append(k * 1000.0 / p0.elapsed_time(p1))
+            del rends
+            torch.cuda.empty_cache()
+            return sorted(rates)[len(rates) // 2], rates
+
+        pf, pf_all = per_pair(B.FP32, False)
+        plain = {"renders_per_s": pf, "reps": pf_all, "pairs_timed": k,
+                 "what": "per-pair launches, unfused composite and shade, FP32 CUDA-core network; median of "
+                         f"{reps_p} repetitions over {k} pairs",
+                 "speedup_of_batched": value / world / pf}
+        if precision == B.BF16:
+            pb, pb_all = per_pair(B.BF16, False)
+            pu, pu_all = per_pair(B.BF16, True)
+            speedup_split = {
+                "plain_bf16_network_renders_per_s": pb, "per_pair_fused_renders_per_s": pu,
+                "network": pb / pf, "fusion": pu / pb, "batching": value / world / pu,
+                "what": ("plain FP32 -> tensor-core BF16 network (unfused, per pair) -> fused composite+shade "
+                         "(per pair; these three on 16 x 16 tiles) -> one batched launch per stage over all pairs "
+                         "under a CUDA graph, with the bench's schedule; the three factors multiply to "
+                         "speedup_of_batched")}
 
     # ---------------- end to end through the public API with host buffers
     e2e = None
@@ -561,7 +744,7 @@ def run_ours(args):
                 r.forward()
                 r.backward(target=target, l1_scale=l1_scale, loss=args.loss)
             if world > 1:
-                PL.allreduce_gradients(grads_flat)
+                r.exchange_gradients()
             if loss_host is not None:
                 loss_host.copy_(r.loss, non_blocking=True)
             for k2, v in host_out.items():
@@ -592,16 +775,21 @@ def run_ours(args):
         except Exception as ex:  # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
 
+    parity = None
+    if par_pix:
+        parity = parity_report(args, n_pairs, par_pix, par_got, precision == B.BF16)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16+f32" if precision == B.BF16 else "f32",
-                "data": "synthetic", "config": _config(args),
+                "data": "synthetic", "config": _config(args), "schedule": schedule, "untuned_schedule": untuned,
+                "parity": parity,
                 "roofline": roof, "step_hbm_frac_of_algorithmic": step_hbm_frac,
                 "stage_ms": stage_ms, "loss_roofline": loss_roof, "visibility_trace": trace, "instances": n_inst, "items": n_items, "mlp_bwd_rows": n_active, "pixels": n_pixels,
                 "contributions_per_step": {"forward": contrib_f, "backward": contrib_b},
                 "cuda_graph": graph is not None,
-                "plain_fp32": plain, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+                "plain_fp32": plain, "speedup_split": speedup_split, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -657,7 +845,6 @@ def run_ours_ml(args):
     del rt
     torch.cuda.empty_cache()
     l1_scale = 1.0 / (3.0 * r.pairs.n_pixels)
-    grads_flat = [g for g in r.grads.values()] + r.dW + r.db
     c0 = B.launch_count()
     graph = r.capture(target=target, l1_scale=l1_scale)
     graph_launches = (B.launch_count() - c0) // 2
@@ -665,7 +852,7 @@ def run_ours_ml(args):
     def step():
         graph.replay()
         if world > 1:
-            PL.allreduce_gradients(grads_flat)
+            r.exchange_gradients()
 
     for _ in range(args.warmup):
         step()
@@ -791,7 +978,7 @@ def run_ours_ml(args):
             target.copy_(host_tgt, non_blocking=True)
             graph.replay()
             if world > 1:
-                PL.allreduce_gradients(grads_flat)
+                r.exchange_gradients()
             for k2, t in host_out.items():
                 t.copy_(r.grads[k2], non_blocking=True)
         for _ in range(args.warmup):       # same warm-up as the device-timed loop
@@ -844,7 +1031,10 @@ def main():
                     help="replace the workload's network by the paper's (App. E)")
     ap.add_argument("--pairs", type=int, default=None,
                     help="override the number of view/light pairs (smaller cases for profiling)")
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", default="auto", choices=["auto", "8", "16", "32"],
+                    help="tile edge; auto: per-scene tile edge and splat batch from the library's autotuner")
+    ap.add_argument("--batch", type=int, default=None, choices=[None, 32, 64],
+                    help="per-block splat batch of the render kernels with a fixed --tile (default 32)")
     ap.add_argument("--views", type=int, default=None, help="c6: views per batch (default 8)")
     ap.add_argument("--lights", type=int, default=None, help="c6: lights per view, 1/2/4/8 (default 8)")
     ap.add_argument("--loss", default="l1", choices=["l1", "paper"],
@@ -856,7 +1046,9 @@ def main():
     ap.add_argument("--vis-sh", action="store_true",
                     help="SH visibility term per Gaussian (v evaluated at each pair's light) with the ray-traced "
                          "visibility loss; also times the BVH build and the tracing")
-    ap.add_argument("--plain-pairs", type=int, default=4)
+    ap.add_argument("--plain-pairs", type=int, default=8)
+    ap.add_argument("--parity-pixels", type=int, default=1000,
+                    help="pixels per sampled pair (4 pairs) compared with the oracle; 0 skips the check")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
