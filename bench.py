@@ -306,8 +306,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # raster_common.cuh) and for workloads made of such pairs; otherwise null.
 TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("5d56c5a2c34af8132c2dbc4eff46949b4f7e384f5a34f41e2b28c9948bb5a861", 108.68e6),
-    "render_fwd": ("5d56c5a2c34af8132c2dbc4eff46949b4f7e384f5a34f41e2b28c9948bb5a861", 70.47e6),
+    "render_bwd": ("65e227eeff4ace16be2a938efba96d036bfe4ff69420ffc552c623ed812a0e30", 108.64e6),
+    "render_fwd": ("65e227eeff4ace16be2a938efba96d036bfe4ff69420ffc552c623ed812a0e30", 70.91e6),
 }
 
 
@@ -769,7 +769,7 @@ def run_ours(args):
         try:
             d = cpu_oracle_sample(args.workload, 16, 1, args.net)
             cpu = {"value": 1.0 / d["t_full_est"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": (f"one pair of {args.workload}: network fwd+bwd over all {n_gauss} Gaussians "
+                   "sample": (f"one pair of {args.workload}: network fwd+bwd over all {wl.scenes[wl.pairs[0].scene].N} Gaussians of its scene "
                               f"({d['t_mlp']:.1f} s) + raster fwd+bwd on every 16th pixel row "
                               f"({d['t_sample'] - d['t_mlp']:.1f} s) scaled by 16; single thread")}
         except Exception as ex:  # report, do not hide
