@@ -2,10 +2,13 @@
 //
 // Two stable LSD radix sorts replace one wide-key sort:
 //   1. items (pair, Gaussian) by (pair, float32 depth bits)   -- n_items keys
-//   2. instances, emitted in that order, by global tile id     -- few key bits
-// Stability of (2) keeps the depth order inside every tile, so the result is
-// the order (tile, depth, item) with 8-bit digits over ~18 tile bits instead
-// of ~50 key bits over all instances.
+//   2. instances, emitted in that order, by the tile index within their pair
+//      (the instances already come out pair by pair, so the pair needs no
+//      pass)                                                  -- ~12 key bits
+// Stability of (2) keeps the depth order inside every (pair, tile) run, so
+// every tile's list is in (depth, item) order; runs of the same local tile
+// of different pairs sit next to each other and the per-tile ranges point
+// to them.
 //
 // Each radix pass is reduce-then-scan: a per-block digit histogram (one
 // shared-memory histogram per warp, plain atomics), a device scan of the
@@ -276,14 +279,14 @@ static void radix_pass(const K* kin, const uint32_t* vin, K* kout, uint32_t* vou
 // ping-pong; returns the index (0: kA/vA, 1: kB/vB) holding the result.
 template <typename K>
 static int radix_sort(K* kA, uint32_t* vA, K* kB, uint32_t* vB, const int64_t* d_n, int64_t cap, int bits,
-                      uint32_t* hist, uint32_t* part32, cudaStream_t st) {
+                      uint32_t* hist, uint32_t* part32, cudaStream_t st, int lo = 0) {
     int nblocks = (int)((cap + RS_TILE - 1) / RS_TILE);
-    if (nblocks == 0) return 0;
+    if (nblocks == 0 || bits <= 0) return 0;
     const int np = (bits + 9) / 10;
     const int per = (bits + np - 1) / np;
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += per) {
-        const int nb = bits - shift < per ? bits - shift : per;
+    for (int shift = lo; shift < lo + bits; shift += per) {
+        const int nb = lo + bits - shift < per ? lo + bits - shift : per;
         K* kin = cur ? kB : kA;
         uint32_t* vin = cur ? vB : vA;
         K* kout = cur ? kA : kB;
@@ -297,6 +300,7 @@ static int radix_sort(K* kA, uint32_t* vA, K* kB, uint32_t* vB, const int64_t* d
 }
 
 static int passes(int bits) {
+    if (bits <= 0) return 0;
     const int np = (bits + 9) / 10;
     const int per = (bits + np - 1) / np;
     return (bits + per - 1) / per;
@@ -358,13 +362,17 @@ __global__ void k_set_count(const uint64_t* __restrict__ off, int64_t n_items, i
 // output is the contiguous range [off[s0], off[s0 + 256]), so the block fills
 // it position by position (coalesced stores): each position finds its item by
 // binary search over the block's offsets, then its tile inside the item's
-// rectangle (row-major order).
+// rectangle (row-major order). The instance key is the pair-local tile index
+// above the pair index, (local tile << pbits) | pair: instances come out in
+// pair order (items are sorted by pair first), so a stable sort of the keys'
+// pair bits would leave them in place, and sorting the local-tile bits alone
+// gives every (pair, tile) its contiguous, depth-ordered run.
 __global__ void __launch_bounds__(256) k_emit(const sssgs_pair* __restrict__ pairs, int64_t n_items,
                                               const uint64_t* __restrict__ dkeys, const uint32_t* __restrict__ dvals,
                                               const int4* __restrict__ rect, const uint64_t* __restrict__ off,
-                                              int64_t cap, uint32_t* __restrict__ ikeys,
+                                              int64_t cap, int pbits, uint32_t* __restrict__ ikeys,
                                               uint32_t* __restrict__ ivals) {
-    __shared__ uint32_t s_off[257], s_item[256], s_base[256], s_w[256], s_tx[256];
+    __shared__ uint32_t s_off[257], s_item[256], s_base[256], s_w[256], s_tx[256], s_pair[256];
     const int t = threadIdx.x;
     const int64_t s0 = (int64_t)blockIdx.x * 256;
     const int nb = (int)min((int64_t)256, n_items - s0);
@@ -376,14 +384,17 @@ __global__ void __launch_bounds__(256) k_emit(const sssgs_pair* __restrict__ pai
         s_off[t] = (uint32_t)(off[s] - B0);
         s_item[t] = m;
         if (r.x <= r.y && r.z <= r.w) {
-            const sssgs_pair& P = pairs[(int)(dkeys[s] >> 32)];
-            s_base[t] = (uint32_t)(P.tile_offset + r.z * P.tiles_x + r.x);
+            const int p = (int)(dkeys[s] >> 32);
+            const sssgs_pair& P = pairs[p];
+            s_base[t] = (uint32_t)(r.z * P.tiles_x + r.x);
             s_w[t] = (uint32_t)(r.y - r.x + 1);
             s_tx[t] = (uint32_t)P.tiles_x;
+            s_pair[t] = (uint32_t)p;
         } else {
             s_base[t] = 0;
             s_w[t] = 1;
             s_tx[t] = 0;
+            s_pair[t] = 0;
         }
     }
     if (t == 0) s_off[nb] = (uint32_t)(off[s0 + nb] - B0);
@@ -399,14 +410,16 @@ __global__ void __launch_bounds__(256) k_emit(const sssgs_pair* __restrict__ pai
         }
         const uint32_t q = rel - s_off[lo], w = s_w[lo];
         const uint32_t dy = q / w, dx = q - dy * w;
-        ikeys[pos] = s_base[lo] + dy * s_tx[lo] + dx;
+        ikeys[pos] = ((s_base[lo] + dy * s_tx[lo] + dx) << pbits) | s_pair[lo];
         ivals[pos] = s_item[lo];
     }
 }
 
-// Per-tile [start, end) from the sorted tile keys, four keys per thread.
+// Per-tile [start, end) from the sorted instance keys, four keys per thread;
+// a key (local tile << pbits) | pair names global tile tile_offset[pair] +
+// local tile.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* d_n, int64_t cap,
-                         uint2* __restrict__ ranges) {
+                         const sssgs_pair* __restrict__ pairs, int pbits, uint2* __restrict__ ranges) {
     const int64_t n = eff_n(d_n, cap);
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (s >= n) return;
@@ -418,8 +431,13 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* d_n, 
         const int64_t i = s + j - 1;
         if (i >= n) break;
         const uint32_t kj = k[j];
-        if (i == 0 || k[j - 1] != kj) ranges[kj].x = (uint32_t)i;
-        if (i == n - 1 || (j < 4 ? k[j + 1] : k[5]) != kj) ranges[kj].y = (uint32_t)(i + 1);
+        const bool first = i == 0 || k[j - 1] != kj;
+        const bool lastk = i == n - 1 || (j < 4 ? k[j + 1] : k[5]) != kj;
+        if (first || lastk) {
+            const uint32_t g = (uint32_t)pairs[kj & ((1u << pbits) - 1u)].tile_offset + (kj >> pbits);
+            if (first) ranges[g].x = (uint32_t)i;
+            if (lastk) ranges[g].y = (uint32_t)(i + 1);
+        }
     }
 }
 
@@ -479,6 +497,11 @@ extern "C" int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, c
     int64_t n_tiles = (int64_t)h_pairs[n_pairs - 1].tile_offset +
                       (int64_t)h_pairs[n_pairs - 1].tiles_x * h_pairs[n_pairs - 1].tiles_y;
     if (n_items >= ((int64_t)1 << 32)) return SSSGS_ERR_INVALID_ARG;
+    int64_t max_local = 1;
+    for (int p = 0; p < n_pairs; ++p)
+        max_local = std::max<int64_t>(max_local, (int64_t)h_pairs[p].tiles_x * h_pairs[p].tiles_y);
+    const int local_tile_bits = max_local > 1 ? bits_for(max_local) : 0;
+    if ((n_pairs > 1 ? bits_for(n_pairs) : 0) + local_tile_bits > 32) return SSSGS_ERR_INVALID_ARG;
     BinLayout L = bin_layout(n_items, capacity);
     if (!workspace || workspace_bytes < L.total) return SSSGS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 255) return SSSGS_ERR_INVALID_ARG;
@@ -518,18 +541,19 @@ extern "C" int sssgs_bin_sort(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, c
     sssgs::note_launches(1);
     if (capacity == 0) return launch_status();
     // 3. emit into the buffer that the tile sort will finish in `vals`
-    int tbits = bits_for(n_tiles);
-    int np = passes(tbits);
+    const int tpbits = n_pairs > 1 ? bits_for(n_pairs) : 0;   // pair bits of the instance keys
+    const int lbits = local_tile_bits;                         // pair-local tile bits
+    int np = passes(lbits);
     uint32_t* v0 = (np % 2 == 0) ? vals : ivW;
     uint32_t* v1 = (np % 2 == 0) ? ivW : vals;
-    k_emit<<<gb, 256, 0, st>>>(d_pairs, n_items, dk, dv, rect4, cnt, capacity, ikA, v0);
+    k_emit<<<gb, 256, 0, st>>>(d_pairs, n_items, dk, dv, rect4, cnt, capacity, tpbits, ikA, v0);
     sssgs::note_launches(1);
-    // 4. stable sort by tile
-    int r2 = radix_sort<uint32_t>(ikA, v0, ikB, v1, d_count, capacity, tbits, hist, part32, st);
+    // 4. stable sort by the local tile bits (the pair bits are in order already)
+    int r2 = radix_sort<uint32_t>(ikA, v0, ikB, v1, d_count, capacity, lbits, hist, part32, st, tpbits);
     uint32_t* ik = r2 ? ikB : ikA;
     // 5. per-tile ranges
     unsigned gr = (unsigned)((capacity + 1023) / 1024);
-    k_ranges<<<gr, 256, 0, st>>>(ik, d_count, capacity, (uint2*)ranges);
+    k_ranges<<<gr, 256, 0, st>>>(ik, d_count, capacity, d_pairs, tpbits, (uint2*)ranges);
     sssgs::note_launches(1);
     return launch_status();
 }

@@ -124,3 +124,29 @@ def assert_grads_close(gpu_grads, ref_grads, keys, tol=GRAD_TOL):
     bad = {k: v for k, v in report.items() if v[0] > tol or v[1] > tol}
     assert not bad, f"gradient mismatch (rel L2, max rel): {bad}"
     return report
+
+
+def assert_tile_lists_equal(vals, ranges, ovals, oranges, n):
+    """Every tile's instance list (its run vals[start:end)) equals the
+    oracle's, bit for bit, and the runs of all tiles partition [0, n). The
+    order of the runs in the buffer is not part of the result: the library
+    keeps the runs of one pair-local tile index of all pairs together."""
+    vals = np.asarray(vals, np.uint32)
+    ovals = np.asarray(ovals, np.uint32)
+    r = np.asarray(ranges, np.int64).reshape(-1, 2)
+    o = np.asarray(oranges, np.int64).reshape(-1, 2)
+    assert r.shape == o.shape
+    lens, olens = r[:, 1] - r[:, 0], o[:, 1] - o[:, 0]
+    assert np.array_equal(lens, olens), "tile list lengths differ"
+    live = np.flatnonzero(lens > 0)
+    if live.size == 0:
+        assert n == 0
+        return
+    assert int(lens.sum()) == n
+    starts = r[live, 0]
+    order = np.argsort(starts)
+    ends = r[live, 1][order]
+    assert starts[order][0] == 0 and np.array_equal(starts[order][1:], ends[:-1]) and ends[-1] == n
+    idx_g = np.concatenate([np.arange(a, b) for a, b in r[live]])
+    idx_o = np.concatenate([np.arange(a, b) for a, b in o[live]])
+    assert np.array_equal(vals[idx_g], ovals[idx_o]), "tile lists differ"

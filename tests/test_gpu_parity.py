@@ -11,7 +11,8 @@ import torch
 
 import oracle as O
 import scenegen as sg
-from gpu_common import (assert_grads_close, assert_image_close, flagged, oracle_batch, run_gpu, IMG_TOL)
+from gpu_common import (assert_grads_close, assert_image_close, assert_tile_lists_equal, flagged, oracle_batch,
+                        run_gpu, IMG_TOL)
 from paper_2408_12282_gb300 import binding as B
 from paper_2408_12282_gb300 import pipeline as PL
 
@@ -113,17 +114,16 @@ def test_bin_sort_bit_exact(n_pairs, N, tx, ty):
     n, keys, ovals, oranges = O.bin_sort(item_pair, rect, depth.view(np.uint32), np.full(n_pairs, tx),
                                          np.arange(n_pairs) * tx * ty, n_pairs * tx * ty)
     assert count == n == n_inst and status == 0
-    assert np.array_equal(vals[:n], ovals)
-    assert np.array_equal(ranges, oranges)
+    assert_tile_lists_equal(vals[:n], ranges, ovals, oranges, n)
 
 
 @pytest.mark.parametrize("name,kw", [("c2", {}), ("c4", dict(n_pairs=4))])
 def test_bin_sort_real_scene_bit_exact(name, kw):
     """Tile lists of real scenes: the GPU's own float32 tile rectangles and
     depth keys (the projection's output) fed to the oracle's plain stable sort
-    give exactly the GPU's lists. Binning is an integer function of those
-    values, so the comparison is bit for bit: the 100K blob at 512x512, and
-    four pairs of the 300K 800x800 batch (12M instances)."""
+    give exactly the GPU's list for every tile. Binning is an integer function
+    of those values, so the comparison is bit for bit: the 100K blob at
+    512x512, and four pairs of the 300K 800x800 batch (12M instances)."""
     wl = sg.make_workload(name, **kw)
     r = PL.renderer_for_workload(wl, precision=B.FP32)
     n_gpu = r.fit_capacity()
@@ -140,8 +140,8 @@ def test_bin_sort_real_scene_bit_exact(name, kw):
     live = rect[:, 0] <= rect[:, 1]
     assert live.mean() > 0.5 and n > 10 * n_pairs * 1000
     assert n == n_gpu
-    assert np.array_equal(r.vals[:n].cpu().numpy().view(np.uint32), ovals)
-    assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32), oranges)
+    assert_tile_lists_equal(r.vals[:n].cpu().numpy().view(np.uint32), r.ranges.cpu().numpy().view(np.uint32),
+                            ovals, oranges, n)
 
 
 def test_bin_sort_capacity_overflow_is_flagged_not_trapped():
