@@ -289,13 +289,18 @@ int sssgs_shade_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs
                     sssgs_stream stream);
 
 /* a3 backward: back-to-front replay from the stored final T (no per-pixel
- * lists kept). Accumulates per-item gradient records into drec[n_items*24]. */
+ * lists kept). Accumulates per-item gradient records into drec[n_items*24].
+ * The unfused path: 8 x 8 and 16 x 16 tiles (SSSGS_ERR_UNSUPPORTED for 32 x
+ * 32; the fused sssgs_render_bwd takes every tile edge). */
 int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,
                         int n_pairs, const float* rec, const uint32_t* vals, const uint32_t* ranges,
                         const float* gbuf, const uint32_t* last, const float* dgbuf,
                         float* drec, sssgs_stream stream);
 
 /* Fused a3+a4 forward: composite then shade in one pass; writes gbuf, last, img.
+ * One 32-thread block per 8 x 4 sub-tile of every tile of every pair (tile
+ * edge cfg->tile: 8, 16 or 32; cfg->batch splats staged per round); images
+ * are bit-identical across tile edges and batches.
  * d_stats (device uint64[2], may be NULL) accumulates the number of
  * contributions (pixel-Gaussian pairs composited) and the tile-list positions
  * each pixel considered (up to the splat that stopped it, else the list end). */
@@ -306,6 +311,10 @@ int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
 /* Fused a4+a3 backward. Upstream gradient either dimg[n_pixels*3], or (dimg ==
  * NULL) the L1 loss  l1_scale * sum |img - target|  with optional per-pixel
  * weights (NULL = 1): dimg = l1_scale * w * sign(img - target). Accumulates drec.
+ * One 32-thread block per 8 x 8 sub-tile (tile edge 8, 16 or 32). Errors:
+ * SSSGS_ERR_INVALID_ARG for a missing buffer, misaligned records, G-buffer,
+ * pair table or ranges (16 bytes), a tile edge other than 8/16/32 or a batch
+ * other than 0/32/64; SSSGS_ERR_CUDA if the launch fails.
  * d_stats (device uint64[2], may be NULL) accumulates the contributions
  * replayed and the alpha evaluations (list positions below each pixel's end). */
 int sssgs_render_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssgs_pair* d_pairs,

@@ -792,12 +792,15 @@ def multilight_renderer_for_workload(wl, precision=None, capacity=None, device="
 
 
 def autotune_schedule(wl, precision=None, tiles=(8, 16, 32), batches=(32, 64), reps=3, device="cuda",
-                      slack: float = 1.1):
+                      slack: float = 1.1, instances_per_item: float = 16.0):
     """Pick the tile edge and per-block splat batch of every scene of a
     workload by measurement (sssgs_autotune): for each scene, its pairs'
     schedule-dependent stages (projection, binning + sort, fused render
     forward and backward) are timed on the device for every candidate.
-    Returns (one B.Cfg per scene, {scene: [TuneResult, ...]}). Blocking."""
+    Returns (one B.Cfg per scene, {scene: [TuneResult, ...]}). Blocking.
+    The first trial sizes the instance buffers at instances_per_item per
+    (pair, Gaussian); candidates that need more are rerun with buffers sized
+    from their reported counts."""
     base = default_cfg(16)
     r = renderer_for_workload(wl, precision=precision, device=device)
     r.run_stage("mlp_fwd")
@@ -833,7 +836,7 @@ def autotune_schedule(wl, precision=None, tiles=(8, 16, 32), batches=(32, 64), r
             tb.workspace, tb.workspace_bytes = keep["ws"].data_ptr(), keep["ws"].numel()
             return tb
 
-        capacity = 16 * n + 1024
+        capacity = int(instances_per_item * n) + 1024
         best, res = B.autotune(base, sub.h, r._scene_s, mlp_out, buffers(capacity), tiles, batches, reps)
         short = [x for x in res if x.status == B.STATUS_CAPACITY]
         if short:                       # rerun the candidates whose instances did not fit (counts reported)

@@ -363,6 +363,50 @@ def test_autotuner_picks_the_fastest_measured_candidate_per_scene():
         assert inst[8] >= inst[16] >= inst[32]
 
 
+def test_autotuner_reruns_candidates_that_exceed_the_first_capacity():
+    """First trial buffers far too small for every candidate (no candidate
+    fits: sssgs_autotune reports every instance count and returns
+    SSSGS_ERR_WORKSPACE): the candidates are rerun with buffers sized from
+    their counts, and the result is the same kind of complete table."""
+    wl = sg.make_workload("c5", N=20000, res=(40, 64, 88), n_pairs=2)
+    cfgs, table = PL.autotune_schedule(wl, precision=B.FP32, reps=1, instances_per_item=0.0)
+    for sc, res in table.items():
+        assert all(x.status == 0 and x.ms > 0 and x.instances > 0 for x in res)
+        fastest = min(res, key=lambda x: x.ms)
+        assert (cfgs[sc].tile, cfgs[sc].batch) == (fastest.tile, fastest.batch)
+
+
+def test_per_scene_schedule_with_the_paper_losses():
+    """The App. E training losses (image loss over the whole batch, then the
+    per-run render backward) on a per-scene schedule: the same losses and
+    gradients as with one schedule."""
+    wl = sg.make_workload("c5", N=20000, res=(40, 64, 88), n_pairs=2)
+    cfgs = []
+    for sc in range(len(wl.scenes)):
+        c = PL.default_cfg((8, 16, 32)[sc % 3])
+        c.batch = (32, 64)[sc % 2]
+        cfgs.append(c)
+    ra = PL.renderer_for_workload(wl, precision=B.FP32, scene_cfgs=cfgs)
+    rb = PL.renderer_for_workload(wl, precision=B.FP32)
+    assert ra.groups is not None and rb.groups is None
+    target = None
+    for r in (ra, rb):
+        r.fit_capacity()
+        r.forward()
+        if target is None:
+            target = torch.rand_like(r.img)
+        r.backward(target=target, loss="paper")
+    torch.cuda.synchronize()
+    ra.check_status()
+    rb.check_status()
+    assert torch.equal(ra.img, rb.img)
+    assert torch.allclose(ra.loss, rb.loss, rtol=1e-5, atol=0)
+    for k in SCENE_KEYS:
+        num = float((ra.grads[k] - rb.grads[k]).norm())
+        den = float(rb.grads[k].norm())
+        assert num <= 1e-5 * max(den, 1e-30), (k, num, den)
+
+
 def test_per_scene_schedule_matches_oracle_and_single_schedule():
     """A batch whose scenes run with different tile edges and batches (one run
     of pairs per scene, each on its own stream, one captured graph): the
