@@ -293,7 +293,7 @@ def algorithmic_bytes(stage, n_items, n_pixels, n_inst, n_gauss, n_pairs):
 # shading and its backward; an FMA counts 2)
 FLOP_EVAL = 14
 FLOP_FWD_CONTRIB = 47
-FLOP_BWD_CONTRIB = 105
+FLOP_BWD_CONTRIB = 102
 FLOP_SHADE_FWD = 120
 FLOP_SHADE_BWD = 300
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

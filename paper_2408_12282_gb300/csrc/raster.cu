@@ -462,7 +462,13 @@ __device__ __forceinline__ void bwd_pixel_setup(PixBwd& p, bool inside, int64_t 
 // 20 resident blocks per SM: 96 registers (a 40-byte spill) and ~21 warps per
 // SM measured faster than 124 registers and 16 warps (29.4 vs 31.7 ms).
 // One block per 8 x 8 sub-tile of a TILE x TILE tile ((TILE/8)^2 per tile).
-template <int TILE, int BATCH, int MODE>
+// The composited visibility channel (feature 14) is a G-buffer output that
+// the deferred shading does not read, so its upstream gradient is exactly 0
+// with the fused upstreams (dimg, L1): the kernel leaves it out of the dot
+// products and reduces 20 gradient values per splat (field 20 of the
+// gradient record stays as the caller zeroed it). STATS adds the work
+// counters.
+template <int TILE, int BATCH, int MODE, bool STATS>
 __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                          int n_pairs, const float4* __restrict__ rec,
                                                          const uint32_t* __restrict__ vals,
@@ -475,7 +481,7 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                                                          const float* __restrict__ weight, float l1_scale,
                                                          float* __restrict__ drec,
                                                          unsigned long long* __restrict__ stats) {
-    constexpr int NG = 6 + SSSGS_NF, RS = 36, R = BATCH / 32;
+    constexpr int NG = 5 + SSSGS_NF, RS = 36, R = BATCH / 32;    // geometry 6 + features 0..13
     using ST = SubTile<TILE, 8, 8>;
     constexpr uint32_t NONE = 0xFFFFFFFFu;
     __shared__ __align__(16) float4 s_rec[2][6][BATCH];
@@ -505,16 +511,14 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
     const float px_x = i + 0.5f, px_y0 = j0 + 0.5f;     // centres of this lane's two pixels (y and y + 1)
     // The two pixels' replay state in float2 form for the paired FP32
-    // instructions: dF of each pixel as component pairs (2k, 2k+1), the last
-    // pair padded with 0; T and Q as (pixel 0, pixel 1).
-    float2 dF0[8], dF1[8];
+    // instructions: dF of each pixel as component pairs (2k, 2k+1) of
+    // features 0..13; T and Q as (pixel 0, pixel 1).
+    float2 dF0[7], dF1[7];
 #pragma unroll
     for (int kk = 0; kk < 7; ++kk) {
         dF0[kk] = make_float2(p[0].dF[2 * kk], p[0].dF[2 * kk + 1]);
         dF1[kk] = make_float2(p[1].dF[2 * kk], p[1].dF[2 * kk + 1]);
     }
-    dF0[7] = make_float2(p[0].dF[14], 0.f);
-    dF1[7] = make_float2(p[1].dF[14], 0.f);
     float2 Tp = make_float2(p[0].T, p[1].T), Qp = make_float2(p[0].Q, p[1].Q);
     const uint32_t last0 = p[0].lastc, last1 = p[1].lastc;
     const float x0 = bx + 0.5f, y0 = by + 0.5f;
@@ -584,14 +588,13 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                 if (!__any_sync(SSSGS_FULL, act0 || act1)) continue;
                 {   // both pixels' terms, summed, straight into this lane's reduction column
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
-                    const float g5 = s_rec[buf][5][k].x;
-                    const float2 fp[8] = {make_float2(g1.z, g1.w), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w),
+                    const float2 fp[7] = {make_float2(g1.z, g1.w), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w),
                                           make_float2(g3.x, g3.y), make_float2(g3.z, g3.w), make_float2(g4.x, g4.y),
-                                          make_float2(g4.z, g4.w), make_float2(g5, 0.f)};
+                                          make_float2(g4.z, g4.w)};
                     // dF . f of each pixel (even and odd components summed separately)
                     float2 d0 = __fmul2_rn(dF0[0], fp[0]), d1 = __fmul2_rn(dF1[0], fp[0]);
 #pragma unroll
-                    for (int kk = 1; kk < 8; ++kk) {
+                    for (int kk = 1; kk < 7; ++kk) {
                         d0 = __ffma2_rn(dF0[kk], fp[kk], d0);
                         d1 = __ffma2_rn(dF1[kk], fp[kk], d1);
                     }
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                     const float2 dg = make_float2(geo0 ? dgr.x : 0.f, geo1 ? dgr.y : 0.f);
                     Qp = __ffma2_rn(w, dot, Qp);
                     Tp = make_float2(act0 ? Ti.x : Tp.x, act1 ? Ti.y : Tp.y);
-                    n_use += (uint32_t)act0 + (uint32_t)act1;
+                    if (STATS) n_use += (uint32_t)act0 + (uint32_t)act1;
                     float* col = s_red + lane;
                     // features: w0 dF0 + w1 dF1, component pairs
                     const float2 w0b = make_float2(w.x, w.x), w1b = make_float2(w.y, w.y);
@@ -621,7 +624,6 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                         col[(6 + 2 * kk) * RS] = cv.x;
                         col[(7 + 2 * kk) * RS] = cv.y;
                     }
-                    col[20 * RS] = w.x * dF0[7].x + w.y * dF1[7].x;
                     // geometry: the two pixels share dx (same column)
                     const float dx = e0.dx;
                     const float2 dy = make_float2(e0.dy, e1.dy);
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
             }
         }
     }
-    if (stats) {
+    if (STATS) {
         unsigned long long u = n_use;
         unsigned long long v = (last0 > rg.x ? last0 - rg.x : 0) + (last1 > rg.x ? last1 - rg.x : 0);
 #pragma unroll
@@ -746,9 +748,14 @@ int launch_bwd_warp_t(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tile
                       const float* img, const float* dimg, const float* target, const float* weight, float l1,
                       float* drec, cudaStream_t st, unsigned long long* stats) {
     constexpr int NSUB = (TILE / 8) * (TILE / 8);
-    k_composite_bwd_warp<TILE, BATCH, MODE><<<NSUB * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals,
-                                                                      (const uint2*)ranges, gbuf, last, img, dimg,
-                                                                      target, weight, l1, drec, stats);
+    if (stats)
+        k_composite_bwd_warp<TILE, BATCH, MODE, true><<<NSUB * tiles, 32, 0, st>>>(
+            *cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf, last, img, dimg, target, weight, l1,
+            drec, stats);
+    else
+        k_composite_bwd_warp<TILE, BATCH, MODE, false><<<NSUB * tiles, 32, 0, st>>>(
+            *cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf, last, img, dimg, target, weight, l1,
+            drec, nullptr);
     sssgs::note_launches(1);
     return launch_status();
 }
