@@ -306,8 +306,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # raster_common.cuh) and for workloads made of such pairs; otherwise null.
 TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("65e227eeff4ace16be2a938efba96d036bfe4ff69420ffc552c623ed812a0e30", 108.64e6),
-    "render_fwd": ("65e227eeff4ace16be2a938efba96d036bfe4ff69420ffc552c623ed812a0e30", 70.91e6),
+    "render_bwd": ("a20fa1809821821a96fc2b4a1b552d8db3a1117dcece2880f62e6a0ff58bf08f", 108.19e6),
+    "render_fwd": ("a20fa1809821821a96fc2b4a1b552d8db3a1117dcece2880f62e6a0ff58bf08f", 70.42e6),
 }
 
 
