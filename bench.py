@@ -302,9 +302,10 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per 300K / 800x800 pair of the fused render kernels,
 # from one ncu capture of an 8-pair launch of the same scene
 # (profiles/k_composite_*_warp_300k_800_8pairs.md), divided by 8. Valid only
-# for the kernel sources they were taken on (sha256 of raster.cu followed by
-# raster_common.cuh) and for workloads made of such pairs; otherwise null.
-TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh")
+# for the kernel sources they were taken on (sha256 of raster.cu, then
+# raster_common.cuh, then common.cuh) and for workloads made of such pairs;
+# otherwise null.
+TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh", "common.cuh")
 KERNEL_TRAFFIC = {
     "render_bwd": ("a20fa1809821821a96fc2b4a1b552d8db3a1117dcece2880f62e6a0ff58bf08f", 108.19e6),
     "render_fwd": ("a20fa1809821821a96fc2b4a1b552d8db3a1117dcece2880f62e6a0ff58bf08f", 70.42e6),

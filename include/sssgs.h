@@ -298,9 +298,9 @@ int sssgs_composite_bwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const s
                         float* drec, sssgs_stream stream);
 
 /* Fused a3+a4 forward: composite then shade in one pass; writes gbuf, last, img.
- * One 32-thread block per 8 x 4 sub-tile of every tile of every pair (tile
- * edge cfg->tile: 8, 16 or 32; cfg->batch splats staged per round); images
- * are bit-identical across tile edges and batches.
+ * One 32-thread block per 8 x 8 sub-tile (two pixels per thread) of every
+ * tile of every pair (tile edge cfg->tile: 8, 16 or 32; cfg->batch splats
+ * staged per round); images are bit-identical across tile edges and batches.
  * d_stats (device uint64[2], may be NULL) accumulates the number of
  * contributions (pixel-Gaussian pairs composited) and the tile-list positions
  * each pixel considered (up to the splat that stopped it, else the list end). */
@@ -310,7 +310,9 @@ int sssgs_render_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_pairs, const sssg
 
 /* Fused a4+a3 backward. Upstream gradient either dimg[n_pixels*3], or (dimg ==
  * NULL) the L1 loss  l1_scale * sum |img - target|  with optional per-pixel
- * weights (NULL = 1): dimg = l1_scale * w * sign(img - target). Accumulates drec.
+ * weights (NULL = 1): dimg = l1_scale * w * sign(img - target). Accumulates drec;
+ * its visibility field (20) is left untouched, since the shading does not read
+ * the visibility channel and its gradient is exactly zero.
  * One 32-thread block per 8 x 8 sub-tile (tile edge 8, 16 or 32). Errors:
  * SSSGS_ERR_INVALID_ARG for a missing buffer, misaligned records, G-buffer,
  * pair table or ranges (16 bytes), a tile edge other than 8/16/32 or a batch
@@ -425,7 +427,9 @@ int sssgs_render_ml_fwd(const sssgs_cfg* cfg, const sssgs_pair* h_views, const s
  * gradient per (view, light) image in pair pixel order: dimg, or (dimg ==
  * NULL) the L1 loss l1_scale * sum |img - target|. Accumulates the per-view
  * gradient records drec[n_view_items * 24] (geometry and the light-independent
- * features; fields 16..19 untouched) and dmlp[rows * 4] = dL/d(L_SSS 3, L_in)
+ * features; fields 16..20 untouched, 20 being the visibility feature, whose
+ * gradient is exactly zero because the shading does not read it) and
+ * dmlp[rows * 4] = dL/d(L_SSS 3, L_in)
  * per (view, light, item) row in mlp_out's layout, for
  * sssgs_mlp_bwd_strided(dout = dmlp, dout_stride = 4) on the pair table.
  * Errors as for sssgs_render_ml_fwd, and SSSGS_ERR_INVALID_ARG without drec,

@@ -61,8 +61,9 @@ __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_fl
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 
 // Per-pixel alpha of one splat (Eq. 3 and the alpha definition after it).
-// Both the forward and the backward replay call exactly this, so their
-// float32 decisions agree bit for bit.
+// Every compositing kernel, forward and backward replay alike, calls this or
+// its two-pixel form below (whose paired instructions round each component
+// as these scalar ones do), so their float32 decisions agree bit for bit.
 struct AlphaEval {
     float alpha;     // clamped alpha
     float G;         // exp(-p)
@@ -86,6 +87,35 @@ __device__ __forceinline__ AlphaEval eval_alpha(float4 g0, float4 g1, float px, 
     r.alpha = fminf(a_max, araw);
     r.use = (p >= 0.f) && (r.alpha >= a_min);
     return r;
+}
+
+// The same for two pixels of one column (x = px, y = py0 and py1): the
+// per-pixel steps run as paired FP32 instructions, each component rounded
+// exactly like the scalar operation above (a - b as a + (-b), which is the
+// same IEEE result), so both pixels get eval_alpha's results bit for bit.
+__device__ __forceinline__ void eval_alpha2(float4 g0, float4 g1, float px, float py0, float py1, float a_min,
+                                            float a_max, AlphaEval& r0, AlphaEval& r1) {
+    const float dx = __fsub_rn(g0.x, px);
+    const float dxx = __fmul_rn(dx, dx);
+    const float2 dy = __fadd2_rn(make_float2(g0.y, g0.y), make_float2(-py0, -py1));
+    const float2 dyy = __fmul2_rn(dy, dy);
+    const float2 dxy = __fmul2_rn(make_float2(dx, dx), dy);
+    const float hc = __fmul_rn(0.5f, g1.x), ha = __fmul_rn(0.5f, g0.z);
+    const float2 inner = __ffma2_rn(make_float2(hc, hc), dyy, __fmul2_rn(make_float2(g0.w, g0.w), dxy));
+    const float2 p = __ffma2_rn(make_float2(ha, ha), make_float2(dxx, dxx), inner);
+    r0.dx = dx;
+    r1.dx = dx;
+    r0.dy = dy.x;
+    r1.dy = dy.y;
+    r0.G = __expf(-p.x);
+    r1.G = __expf(-p.y);
+    const float2 araw = __fmul2_rn(make_float2(g1.y, g1.y), make_float2(r0.G, r1.G));
+    r0.clamped = araw.x > a_max;
+    r1.clamped = araw.y > a_max;
+    r0.alpha = fminf(a_max, araw.x);
+    r1.alpha = fminf(a_max, araw.y);
+    r0.use = (p.x >= 0.f) && (r0.alpha >= a_min);
+    r1.use = (p.y >= 0.f) && (r1.alpha >= a_min);
 }
 
 }  // namespace sssgs

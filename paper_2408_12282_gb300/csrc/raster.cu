@@ -1,34 +1,35 @@
 // Per-pixel compositing (Eq. 3) into the deferred G-buffer and deferred
 // shading (Eq. 4, Eq. 7), forward and backward.
 //
-// One CTA per image tile, one thread per pixel. Each CTA walks its tile's
-// depth-ordered instance list in batches: every thread loads one packed 96-B
-// record (six 16-B loads) into shared memory, then all pixels of the tile
-// consume the batch from shared memory (broadcast reads). A pixel stops when
-// its transmittance would drop below T_min; a warp whose lanes have all
-// stopped skips the batch, and the CTA stops loading once every pixel is done
-// (__syncthreads_count).
+// The fused kernels run one 32-thread block per 8 x 8 sub-tile of an image
+// tile, two pixels per lane. Each walks its tile's depth-ordered instance
+// list in batches: every lane loads packed 96-B records (six 16-B copies)
+// into a shared-memory double buffer, a ballot of the lanes' sub-tile tests
+// lists the splats the warp visits, and the warp reads each visited record
+// by broadcast. The forward stops a pixel when its transmittance would drop
+// below T_min and the warp once all its pixels have stopped.
 //
 // The backward replays each pixel's list back to front starting from the final
 // transmittance stored by the forward (T_i = T_{i+1} / (1 - alpha_i)), so no
-// per-pixel list is kept. Per-Gaussian gradients are summed over the 32 pixels
-// of a warp through a per-warp shared-memory transpose (each lane stores its
-// 21 values in a column, lane k then sums row k with eight 16-byte loads) and
-// issued as one 21-lane fire-and-forget add per warp, instead of one atomic
-// per pixel.
+// per-pixel list is kept. Per-Gaussian gradients are summed over the pixels
+// of a warp through a shared-memory transpose (each lane stores its values in
+// a column, lane k then sums row k with eight 16-byte loads) and issued as
+// one fire-and-forget add per reduced row and warp, instead of one atomic per
+// pixel. A block-per-tile backward (one thread per pixel) serves the unfused
+// path, whose upstream is a G-buffer gradient.
 #include "raster_common.cuh"
+
 
 namespace sssgs {
 
 // ---------------------------------------------------------------- composite forward, one warp per sub-tile
 //
-// Each block is a single warp that owns an 8 x 4 sub-tile of a TILE x TILE
-// tile (TILE = 8, 16 or 32: (TILE/8) x (TILE/4) sub-tiles per tile), one
-// pixel per lane; there is no block barrier and a warp stops as soon as its
-// own pixels are done. The tile's list is walked front to back in batches of
-// BATCH splats (32 or 64: one or two per lane) through a cp.async double
-// buffer in shared memory; a ballot of each lane's exact sub-tile test lists
-// the splats the warp visits.
+// Each block is a single warp that owns an 8 x 8 sub-tile of a TILE x TILE
+// tile (TILE = 8, 16 or 32: (TILE/8)^2 sub-tiles per tile); there is no
+// block barrier and a warp stops as soon as its own pixels are done. The
+// tile's list is walked front to back in batches of BATCH splats (32 or 64:
+// one or two per lane) through a cp.async double buffer in shared memory; a
+// ballot of each lane's exact sub-tile test lists the splats the warp visits.
 
 // Sub-tile origin of block `blk` for SW x SH sub-tiles of TILE x TILE tiles.
 template <int TILE, int SW, int SH>
@@ -44,16 +45,24 @@ struct SubTile {
     }
 };
 
+// Lane l holds pixels (l & 7, 2 (l >> 3)) and the one below, as in the
+// backward. A visited splat's records are read once for both pixels, the
+// two alpha evaluations share their column terms and run as paired FP32
+// instructions, the G-buffer sums advance as pairs (one paired FMA per
+// feature) and the two pixels' chains are independent work for the
+// scheduler. A pixel that does not take the splat adds w = 0 (F + 0 * g = F
+// exactly: F is never -0), so each pixel's float32 result is the one a lane
+// of its own would compute.
 template <int TILE, int BATCH, bool SHADE>
 __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
-                                                             int n_pairs, const float4* __restrict__ rec,
-                                                             const uint32_t* __restrict__ vals,
-                                                             const uint2* __restrict__ ranges,
-                                                             float* __restrict__ gbuf, uint32_t* __restrict__ last,
-                                                             float* __restrict__ img,
-                                                             unsigned long long* __restrict__ stats) {
+                                                              int n_pairs, const float4* __restrict__ rec,
+                                                              const uint32_t* __restrict__ vals,
+                                                              const uint2* __restrict__ ranges,
+                                                              float* __restrict__ gbuf, uint32_t* __restrict__ last,
+                                                              float* __restrict__ img,
+                                                              unsigned long long* __restrict__ stats) {
     constexpr int R = BATCH / 32;                 // records per lane per batch
-    using ST = SubTile<TILE, 8, 4>;
+    using ST = SubTile<TILE, 8, 8>;
     constexpr uint32_t NONE = 0xFFFFFFFFu;
     __shared__ __align__(16) float4 s_rec[2][6][BATCH];
     __shared__ __align__(16) sssgs_pair sP;
@@ -65,17 +74,19 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
     __syncwarp();
     const ST st(blockIdx.x, sP);
     const int tile = st.tile, bx = st.bx, by = st.by;
-    const int i = bx + (lane & 7), j = by + (lane >> 3);
+    const int i = bx + (lane & 7), j0 = by + (lane >> 3) * 2;
     const uint2 rg = ranges[tile];
     const float a_min = cfg.alpha_min, a_max = cfg.alpha_max, T_min = cfg.T_min;
     const float x0 = bx + 0.5f, y0 = by + 0.5f;
-    const float px = (float)i + 0.5f, py = (float)j + 0.5f;
-    float T = 1.f, F[SSSGS_NF];
-    uint32_t lastc = 0;
-    bool done = !(i < sP.W && j < sP.H);
-    uint32_t stop = done ? rg.x : rg.y;
+    const float px = (float)i + 0.5f, py0 = (float)j0 + 0.5f, py1 = py0 + 1.f;
+    const bool in0 = i < sP.W && j0 < sP.H, in1 = i < sP.W && j0 + 1 < sP.H;
+    float2 F[SSSGS_NF];                           // (pixel 0, pixel 1) of each G-buffer channel
+    float T0 = 1.f, T1 = 1.f;
+    uint32_t last0 = 0, last1 = 0;
+    bool done0 = !in0, done1 = !in1;
+    uint32_t stop0 = done0 ? rg.x : rg.y, stop1 = done1 ? rg.x : rg.y;
 #pragma unroll
-    for (int k = 0; k < SSSGS_NF; ++k) F[k] = 0.f;
+    for (int k = 0; k < SSSGS_NF; ++k) F[k] = make_float2(0.f, 0.f);
     uint32_t n_use = 0;
     const int nb = (int)((rg.y - rg.x + BATCH - 1) / BATCH);
     auto entry = [&](int t, int r) -> uint32_t {
@@ -95,7 +106,7 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
         }
         cp_async_commit();
     };
-    if (nb > 0 && !__all_sync(SSSGS_FULL, done)) {
+    if (nb > 0 && !__all_sync(SSSGS_FULL, done0 && done1)) {
         uint32_t it0[R], it1[R], it2[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) it0[r] = entry(0, r);
@@ -116,7 +127,7 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
                     const int s = 32 * r + lane;
                     const float4 g0 = s_rec[buf][0][s], g1 = s_rec[buf][1][s], g5 = s_rec[buf][5][s];
                     pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
-                                             y0 + 3.f);
+                                             y0 + 7.f);
                 }
                 bits[r] = __ballot_sync(SSSGS_FULL, pass);
             }
@@ -127,29 +138,42 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
                 while (bits[r]) {          // warp-uniform loop; finished lanes idle
                     const int k = 32 * r + __ffs(bits[r]) - 1;
                     bits[r] &= bits[r] - 1;
-                    if (done) continue;
+                    if (done0 && done1) continue;
                     const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
-                    const AlphaEval e = eval_alpha(g0, g1, px, py, a_min, a_max);
-                    if (!e.use) continue;
-                    const float Tn = T * (1.f - e.alpha);
-                    if (Tn < T_min) {
-                        done = true;
-                        stop = base + k + 1;
-                        continue;
+                    AlphaEval e0, e1;
+                    eval_alpha2(g0, g1, px, py0, py1, a_min, a_max, e0, e1);
+                    bool u0 = !done0 && e0.use, u1 = !done1 && e1.use;
+                    const float Tn0 = T0 * (1.f - e0.alpha), Tn1 = T1 * (1.f - e1.alpha);
+                    if (u0 && Tn0 < T_min) {
+                        done0 = true;
+                        stop0 = base + k + 1;
+                        u0 = false;
                     }
-                    ++n_use;
-                    const float w = T * e.alpha;
+                    if (u1 && Tn1 < T_min) {
+                        done1 = true;
+                        stop1 = base + k + 1;
+                        u1 = false;
+                    }
+                    if (!(u0 || u1)) continue;
+                    n_use += (uint32_t)u0 + (uint32_t)u1;
+                    const float2 w = make_float2(u0 ? T0 * e0.alpha : 0.f, u1 ? T1 * e1.alpha : 0.f);
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
                     const float g5 = s_rec[buf][5][k].x;
-                    F[0] += w * g1.z;  F[1] += w * g1.w;  F[2] += w * g2.x;  F[3] += w * g2.y;
-                    F[4] += w * g2.z;  F[5] += w * g2.w;  F[6] += w * g3.x;  F[7] += w * g3.y;
-                    F[8] += w * g3.z;  F[9] += w * g3.w;  F[10] += w * g4.x; F[11] += w * g4.y;
-                    F[12] += w * g4.z; F[13] += w * g4.w; F[14] += w * g5;
-                    T = Tn;
-                    lastc = base + k + 1;
+                    const float f[SSSGS_NF] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y,
+                                               g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
+#pragma unroll
+                    for (int c = 0; c < SSSGS_NF; ++c) F[c] = __ffma2_rn(w, make_float2(f[c], f[c]), F[c]);
+                    if (u0) {
+                        T0 = Tn0;
+                        last0 = base + k + 1;
+                    }
+                    if (u1) {
+                        T1 = Tn1;
+                        last1 = base + k + 1;
+                    }
                 }
             }
-            if (__all_sync(SSSGS_FULL, done)) break;
+            if (__all_sync(SSSGS_FULL, done0 && done1)) break;
             __syncwarp();
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -160,7 +184,7 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
         cp_async_wait_all();
     }
     if (stats) {   // contributions, and list positions each pixel considered
-        unsigned long long u = n_use, v = stop - rg.x;
+        unsigned long long u = n_use, v = (unsigned long long)(in0 ? stop0 - rg.x : 0) + (in1 ? stop1 - rg.x : 0);
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
             u += __shfl_xor_sync(SSSGS_FULL, u, o);
@@ -171,20 +195,28 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
             atomicAdd(stats + 1, v);
         }
     }
-    if (!(i < sP.W && j < sP.H)) return;
-    const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
-    float4* go = reinterpret_cast<float4*>(gbuf + SSSGS_GBUF * pix);
-    go[0] = make_float4(F[0], F[1], F[2], F[3]);
-    go[1] = make_float4(F[4], F[5], F[6], F[7]);
-    go[2] = make_float4(F[8], F[9], F[10], F[11]);
-    go[3] = make_float4(F[12], F[13], F[14], T);
-    last[pix] = lastc;
-    if (SHADE) {
-        float o[3];
-        shade_px<false>(F, T, px, py, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
-        img[3 * pix] = o[0];
-        img[3 * pix + 1] = o[1];
-        img[3 * pix + 2] = o[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (!(q ? in1 : in0)) continue;
+        const int j = j0 + q;
+        const int64_t pix = sP.pixel_offset + (int64_t)j * sP.W + i;
+        float Fq[SSSGS_NF];
+#pragma unroll
+        for (int c = 0; c < SSSGS_NF; ++c) Fq[c] = q ? F[c].y : F[c].x;
+        const float T = q ? T1 : T0;
+        float4* go = reinterpret_cast<float4*>(gbuf + SSSGS_GBUF * pix);
+        go[0] = make_float4(Fq[0], Fq[1], Fq[2], Fq[3]);
+        go[1] = make_float4(Fq[4], Fq[5], Fq[6], Fq[7]);
+        go[2] = make_float4(Fq[8], Fq[9], Fq[10], Fq[11]);
+        go[3] = make_float4(Fq[12], Fq[13], Fq[14], T);
+        last[pix] = q ? last1 : last0;
+        if (SHADE) {
+            float o[3];
+            shade_px<false>(Fq, T, px, q ? py1 : py0, sP, cfg.A_eps, o, nullptr, nullptr, nullptr);
+            img[3 * pix] = o[0];
+            img[3 * pix + 1] = o[1];
+            img[3 * pix + 2] = o[2];
+        }
     }
 }
 
@@ -581,8 +613,8 @@ __global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, co
                 const int k = 32 * r + kb;
                 const uint32_t pos = lo + k;
                 const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
-                const AlphaEval e0 = eval_alpha(g0, g1, px_x, px_y0, a_min, a_max);
-                const AlphaEval e1 = eval_alpha(g0, g1, px_x, px_y0 + 1.f, a_min, a_max);
+                AlphaEval e0, e1;
+                eval_alpha2(g0, g1, px_x, px_y0, px_y0 + 1.f, a_min, a_max, e0, e1);
                 const bool act0 = (pos < last0) && e0.use;
                 const bool act1 = (pos < last1) && e1.use;
                 if (!__any_sync(SSSGS_FULL, act0 || act1)) continue;
@@ -698,12 +730,12 @@ bool args_ok(const sssgs_cfg* cfg, const sssgs_pair* h, const sssgs_pair* d, int
 int tiles_of(const sssgs_pair* h, int n) { return h[n - 1].tile_offset + h[n - 1].tiles_x * h[n - 1].tiles_y; }
 bool a16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-// One-warp forward: (TILE/8) x (TILE/4) blocks of 32 threads per tile.
+// One-warp forward: (TILE/8)^2 blocks of 32 threads per tile.
 template <int TILE, int BATCH, bool SHADE>
 int launch_fwd_warp_t(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tiles, const float* rec,
                       const uint32_t* vals, const uint32_t* ranges, float* gbuf, uint32_t* last, float* img,
                       cudaStream_t st, unsigned long long* stats) {
-    constexpr int NSUB = (TILE / 8) * (TILE / 4);
+    constexpr int NSUB = (TILE / 8) * (TILE / 8);
     k_composite_fwd_warp<TILE, BATCH, SHADE><<<NSUB * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals,
                                                                        (const uint2*)ranges, gbuf, last, img,
                                                                        stats);

@@ -235,14 +235,16 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
 }
 
 // Backward. Per pixel, the shading backward of every light gives dL/dF: the
-// light-independent part summed over the lights (dgeo 10 + dvis), the light
+// light-independent part summed over the lights (dgeo 10), the light
 // channels per light (dlf), and dL/dT_final summed. The replay then follows
 // the single-light kernel: T_i = T_{i+1} / (1 - alpha_i), dL/dalpha_i =
 // T_i (dF . f_i) - Q / (1 - alpha_i), Q accumulating w (dF . f) from
-// dL/dT_final * T_final, with dF . f running over all 11 + 4 L channels.
+// dL/dT_final * T_final, with dF . f running over the 10 + 4 L channels the
+// shading reads.
 // Reduction rows per splat: 0..5 geometry (mean 2, conic 3, opacity),
-// 6..15 the ten light-independent features, 16 vis, 17 + 4 l + c light l's
-// channel c.
+// 6..15 the ten light-independent features, 16 + 4 l + c light l's channel c.
+// The visibility channel has no row: the shading does not read it, so its
+// upstream gradient is exactly zero (the caller's cleared drec keeps it).
 template <int L>
 __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
     sssgs_cfg cfg, const sssgs_pair* __restrict__ views, int n_views, const float* __restrict__ lights,
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
     const uint2* __restrict__ ranges, const float* __restrict__ gbuf, const uint32_t* __restrict__ last,
     const float* __restrict__ img, const float* __restrict__ dimg, const float* __restrict__ target,
     float l1_scale, float* __restrict__ drec, float* __restrict__ dmlp, unsigned long long* __restrict__ stats) {
-    constexpr int GB = ML_GEO + 4 * L, NG = 17 + 4 * L, RS = 36;
+    constexpr int GB = ML_GEO + 4 * L, NG = 16 + 4 * L, RS = 36;
     constexpr int NR = NG < 32 ? NG : 32;                 // rows the transpose buffer holds at once
     __shared__ __align__(16) float4 s_rec[2][5][32];     // record float4s 0..3, 5
     __shared__ __align__(16) float4 s_lf[2][L][32];
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
     const uint2 rg = ranges[tile];
     const float px = i + 0.5f, py = j + 0.5f;
     // per-pixel upstream: shading backward of every light
-    float dgeo[10], dvis = 0.f, dlf[L][4], T = 1.f, Q = 0.f;
+    float dgeo[10], dlf[L][4], T = 1.f, Q = 0.f;
     uint32_t lastc = 0;
 #pragma unroll
     for (int k = 0; k < 10; ++k) dgeo[k] = 0.f;
@@ -317,7 +319,6 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
             for (int k = 0; k < 10; ++k) dgeo[k] += dF[k];
 #pragma unroll
             for (int c = 0; c < 4; ++c) dlf[l][c] = dF[10 + c];
-            dvis += dF[14];
             dT += dTl;
         }
         Q = dT * T;
@@ -376,8 +377,7 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
                 {
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k];
                     const float f[10] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w};
-                    const float fv = s_rec[buf][4][k].x;
-                    float dot = dvis * fv;
+                    float dot = 0.f;
 #pragma unroll
                     for (int kk = 0; kk < 10; ++kk) dot = fmaf(dgeo[kk], f[kk], dot);
 #pragma unroll
@@ -409,12 +409,11 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
                     col[5 * RS] = dg;
 #pragma unroll
                     for (int kk = 0; kk < 10; ++kk) col[(6 + kk) * RS] = w * dgeo[kk];
-                    col[16 * RS] = w * dvis;
                     if constexpr (NG <= NR) {          // all rows in one transpose
 #pragma unroll
                         for (int l = 0; l < L; ++l)
 #pragma unroll
-                            for (int c = 0; c < 4; ++c) col[(17 + 4 * l + c) * RS] = w * dlf[l][c];
+                            for (int c = 0; c < 4; ++c) col[(16 + 4 * l + c) * RS] = w * dlf[l][c];
                     }
                     wk = w;
                 }
@@ -439,11 +438,10 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::BWD) k_render_ml_bwd(
                 auto light_add = [&](int r, float sum) {   // light row r = 4 l + c
                     atomicAdd(dmlp + 4 * ml_row(sP, L, r >> 2, item) + (r & 3), sum);
                 };
-                if (lane < 17) {
-                    const float sum = row_sum(lane);
-                    atomicAdd(drec + (int64_t)SSSGS_REC * item + (lane < 16 ? lane : 20), sum);
+                if (lane < 16) {
+                    atomicAdd(drec + (int64_t)SSSGS_REC * item + lane, row_sum(lane));
                 } else if (NG <= NR && lane < NG) {
-                    light_add(lane - 17, row_sum(lane));
+                    light_add(lane - 16, row_sum(lane));
                 }
                 if constexpr (NG > NR) {               // light channels in a second transpose
                     __syncwarp();
