@@ -307,8 +307,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # otherwise null.
 TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh", "common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("a20fa1809821821a96fc2b4a1b552d8db3a1117dcece2880f62e6a0ff58bf08f", 108.19e6),
-    "render_fwd": ("a20fa1809821821a96fc2b4a1b552d8db3a1117dcece2880f62e6a0ff58bf08f", 70.42e6),
+    "render_bwd": ("25be028c606efaa61dcd0521bf9d987c19e7dcb78dac74b168311dd149e18079", 108.40e6),
+    "render_fwd": ("25be028c606efaa61dcd0521bf9d987c19e7dcb78dac74b168311dd149e18079", 83.27e6),
 }
 
 

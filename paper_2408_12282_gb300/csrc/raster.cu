@@ -19,6 +19,13 @@
 // path, whose upstream is a G-buffer gradient.
 #include "raster_common.cuh"
 
+#ifndef SSSGS_FWD_MINB
+#define SSSGS_FWD_MINB 32
+#endif
+#ifndef SSSGS_BWD_MINB
+#define SSSGS_BWD_MINB 20
+#endif
+
 
 namespace sssgs {
 
@@ -53,8 +60,8 @@ struct SubTile {
 // scheduler. A pixel that does not take the splat adds w = 0 (F + 0 * g = F
 // exactly: F is never -0), so each pixel's float32 result is the one a lane
 // of its own would compute.
-template <int TILE, int BATCH, bool SHADE>
-__global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+template <int TILE, int BATCH, bool SHADE, bool STATS>
+__global__ void __launch_bounds__(32, SSSGS_FWD_MINB) k_composite_fwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                               int n_pairs, const float4* __restrict__ rec,
                                                               const uint32_t* __restrict__ vals,
                                                               const uint2* __restrict__ ranges,
@@ -84,7 +91,7 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
     float T0 = 1.f, T1 = 1.f;
     uint32_t last0 = 0, last1 = 0;
     bool done0 = !in0, done1 = !in1;
-    uint32_t stop0 = done0 ? rg.x : rg.y, stop1 = done1 ? rg.x : rg.y;
+    uint32_t stop0 = done0 ? rg.x : rg.y, stop1 = done1 ? rg.x : rg.y;   // read only with STATS
 #pragma unroll
     for (int k = 0; k < SSSGS_NF; ++k) F[k] = make_float2(0.f, 0.f);
     uint32_t n_use = 0;
@@ -146,16 +153,16 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
                     const float Tn0 = T0 * (1.f - e0.alpha), Tn1 = T1 * (1.f - e1.alpha);
                     if (u0 && Tn0 < T_min) {
                         done0 = true;
-                        stop0 = base + k + 1;
+                        if (STATS) stop0 = base + k + 1;
                         u0 = false;
                     }
                     if (u1 && Tn1 < T_min) {
                         done1 = true;
-                        stop1 = base + k + 1;
+                        if (STATS) stop1 = base + k + 1;
                         u1 = false;
                     }
                     if (!(u0 || u1)) continue;
-                    n_use += (uint32_t)u0 + (uint32_t)u1;
+                    if (STATS) n_use += (uint32_t)u0 + (uint32_t)u1;
                     const float2 w = make_float2(u0 ? T0 * e0.alpha : 0.f, u1 ? T1 * e1.alpha : 0.f);
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
                     const float g5 = s_rec[buf][5][k].x;
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(32, 16) k_composite_fwd_warp(sssgs_cfg cfg, co
         }
         cp_async_wait_all();
     }
-    if (stats) {   // contributions, and list positions each pixel considered
+    if (STATS) {   // contributions, and list positions each pixel considered
         unsigned long long u = n_use, v = (unsigned long long)(in0 ? stop0 - rg.x : 0) + (in1 ? stop1 - rg.x : 0);
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -501,7 +508,7 @@ __device__ __forceinline__ void bwd_pixel_setup(PixBwd& p, bool inside, int64_t 
 // gradient record stays as the caller zeroed it). STATS adds the work
 // counters.
 template <int TILE, int BATCH, int MODE, bool STATS>
-__global__ void __launch_bounds__(32, 20) k_composite_bwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
+__global__ void __launch_bounds__(32, SSSGS_BWD_MINB) k_composite_bwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                          int n_pairs, const float4* __restrict__ rec,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint2* __restrict__ ranges,
@@ -736,9 +743,12 @@ int launch_fwd_warp_t(const sssgs_cfg* cfg, const sssgs_pair* d, int n, int tile
                       const uint32_t* vals, const uint32_t* ranges, float* gbuf, uint32_t* last, float* img,
                       cudaStream_t st, unsigned long long* stats) {
     constexpr int NSUB = (TILE / 8) * (TILE / 8);
-    k_composite_fwd_warp<TILE, BATCH, SHADE><<<NSUB * tiles, 32, 0, st>>>(*cfg, d, n, (const float4*)rec, vals,
-                                                                       (const uint2*)ranges, gbuf, last, img,
-                                                                       stats);
+    if (stats)
+        k_composite_fwd_warp<TILE, BATCH, SHADE, true><<<NSUB * tiles, 32, 0, st>>>(
+            *cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf, last, img, stats);
+    else
+        k_composite_fwd_warp<TILE, BATCH, SHADE, false><<<NSUB * tiles, 32, 0, st>>>(
+            *cfg, d, n, (const float4*)rec, vals, (const uint2*)ranges, gbuf, last, img, nullptr);
     sssgs::note_launches(1);
     return launch_status();
 }
