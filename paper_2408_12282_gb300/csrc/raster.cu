@@ -19,13 +19,16 @@
 // path, whose upstream is a G-buffer gradient.
 #include "raster_common.cuh"
 
+// Resident one-warp blocks per SM the fused kernels are built for (the
+// register cap follows): the forward at 32, the SM's block limit (64
+// registers, a small spill), measured faster than 20-28; the backward at 20
+// (96 registers), measured faster than 24.
 #ifndef SSSGS_FWD_MINB
 #define SSSGS_FWD_MINB 32
 #endif
 #ifndef SSSGS_BWD_MINB
 #define SSSGS_BWD_MINB 20
 #endif
-
 
 namespace sssgs {
 
@@ -59,7 +62,8 @@ struct SubTile {
 // feature) and the two pixels' chains are independent work for the
 // scheduler. A pixel that does not take the splat adds w = 0 (F + 0 * g = F
 // exactly: F is never -0), so each pixel's float32 result is the one a lane
-// of its own would compute.
+// of its own would compute, and the warp skips a visit only when none of its
+// pixels takes the splat: lanes never diverge inside a visit.
 template <int TILE, int BATCH, bool SHADE, bool STATS>
 __global__ void __launch_bounds__(32, SSSGS_FWD_MINB) k_composite_fwd_warp(sssgs_cfg cfg, const sssgs_pair* __restrict__ pairs,
                                                               int n_pairs, const float4* __restrict__ rec,
@@ -145,7 +149,6 @@ __global__ void __launch_bounds__(32, SSSGS_FWD_MINB) k_composite_fwd_warp(sssgs
                 while (bits[r]) {          // warp-uniform loop; finished lanes idle
                     const int k = 32 * r + __ffs(bits[r]) - 1;
                     bits[r] &= bits[r] - 1;
-                    if (done0 && done1) continue;
                     const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
                     AlphaEval e0, e1;
                     eval_alpha2(g0, g1, px, py0, py1, a_min, a_max, e0, e1);
@@ -161,7 +164,8 @@ __global__ void __launch_bounds__(32, SSSGS_FWD_MINB) k_composite_fwd_warp(sssgs
                         if (STATS) stop1 = base + k + 1;
                         u1 = false;
                     }
-                    if (!(u0 || u1)) continue;
+                    // warp-uniform skip: the lanes never diverge inside a visit
+                    if (!__any_sync(SSSGS_FULL, u0 || u1)) continue;
                     if (STATS) n_use += (uint32_t)u0 + (uint32_t)u1;
                     const float2 w = make_float2(u0 ? T0 * e0.alpha : 0.f, u1 ? T1 * e1.alpha : 0.f);
                     const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k], g4 = s_rec[buf][4][k];
@@ -170,14 +174,10 @@ __global__ void __launch_bounds__(32, SSSGS_FWD_MINB) k_composite_fwd_warp(sssgs
                                                g3.z, g3.w, g4.x, g4.y, g4.z, g4.w, g5};
 #pragma unroll
                     for (int c = 0; c < SSSGS_NF; ++c) F[c] = __ffma2_rn(w, make_float2(f[c], f[c]), F[c]);
-                    if (u0) {
-                        T0 = Tn0;
-                        last0 = base + k + 1;
-                    }
-                    if (u1) {
-                        T1 = Tn1;
-                        last1 = base + k + 1;
-                    }
+                    T0 = u0 ? Tn0 : T0;
+                    T1 = u1 ? Tn1 : T1;
+                    last0 = u0 ? base + k + 1 : last0;
+                    last1 = u1 ? base + k + 1 : last1;
                 }
             }
             if (__all_sync(SSSGS_FULL, done0 && done1)) break;

@@ -138,18 +138,20 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
             while (bits) {
                 const int k = __ffs(bits) - 1;
                 bits &= bits - 1;
-                if (done) continue;
+                // warp-uniform visit: a lane that does not take the splat adds
+                // weight 0 (exact: the sums are never -0), so lanes never diverge
                 const float4 g0 = s_rec[buf][0][k], g1 = s_rec[buf][1][k];
                 const AlphaEval e = eval_alpha(g0, g1, px, py, a_min, a_max);
-                if (!e.use) continue;
+                bool u = !done && e.use;
                 const float Tn = T * (1.f - e.alpha);
-                if (Tn < T_min) {
+                if (u && Tn < T_min) {
                     done = true;
                     stop = base + k + 1;
-                    continue;
+                    u = false;
                 }
-                ++n_use;
-                const float w = T * e.alpha;
+                if (!__any_sync(SSSGS_FULL, u)) continue;
+                n_use += (uint32_t)u;
+                const float w = u ? T * e.alpha : 0.f;
                 const float2 ww = make_float2(w, w);
                 const float4 g2 = s_rec[buf][2][k], g3 = s_rec[buf][3][k];
                 geo2[0] = __ffma2_rn(ww, make_float2(g1.z, g1.w), geo2[0]);
@@ -164,8 +166,8 @@ __global__ void __launch_bounds__(32, MlBlocks<L>::FWD) k_render_ml_fwd(
                     lf2[l][0] = __ffma2_rn(ww, make_float2(v.x, v.y), lf2[l][0]);
                     lf2[l][1] = __ffma2_rn(ww, make_float2(v.z, v.w), lf2[l][1]);
                 }
-                T = Tn;
-                lastc = base + k + 1;
+                T = u ? Tn : T;
+                lastc = u ? base + k + 1 : lastc;
             }
             if (__all_sync(SSSGS_FULL, done)) break;
             __syncwarp();
