@@ -307,8 +307,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # otherwise null.
 TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh", "common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("25be028c606efaa61dcd0521bf9d987c19e7dcb78dac74b168311dd149e18079", 108.40e6),
-    "render_fwd": ("25be028c606efaa61dcd0521bf9d987c19e7dcb78dac74b168311dd149e18079", 83.27e6),
+    "render_bwd": ("f829334662678eee74bb0ac5e19a2a12ff8acc0095cf97c5939759fd7a46b3c0", 108.34e6),
+    "render_fwd": ("f829334662678eee74bb0ac5e19a2a12ff8acc0095cf97c5939759fd7a46b3c0", 83.43e6),
 }
 
 
