@@ -133,13 +133,13 @@ __global__ void __launch_bounds__(32, SSSGS_FWD_MINB) k_composite_fwd_warp(sssgs
             uint32_t bits[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                bool pass = false;
-                if (it0[r] != NONE) {
-                    const int s = 32 * r + lane;
-                    const float4 g0 = s_rec[buf][0][s], g1 = s_rec[buf][1][s], g5 = s_rec[buf][5][s];
-                    pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
-                                             y0 + 7.f);
-                }
+                // every slot is tested (an empty slot holds stale or
+                // unwritten shared data, harmless to compare) and empty ones are masked out
+                const int s = 32 * r + lane;
+                const float4 g0 = s_rec[buf][0][s], g1 = s_rec[buf][1][s], g5 = s_rec[buf][5][s];
+                const bool pass = (it0[r] != NONE) &
+                                  ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f,
+                                                    y0, y0 + 7.f);
                 bits[r] = __ballot_sync(SSSGS_FULL, pass);
             }
             __syncwarp();
@@ -600,13 +600,11 @@ __global__ void __launch_bounds__(32, SSSGS_BWD_MINB) k_composite_bwd_warp(sssgs
             uint32_t bits[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                bool pass = false;
                 const int sl = 32 * r + lane;
-                if (it0[r] != NONE) {
-                    const float4 g0 = s_rec[buf][0][sl], g1 = s_rec[buf][1][sl], g5 = s_rec[buf][5][sl];
-                    pass = ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f, y0,
-                                             y0 + 7.f);
-                }
+                const float4 g0 = s_rec[buf][0][sl], g1 = s_rec[buf][1][sl], g5 = s_rec[buf][5][sl];
+                const bool pass = (it0[r] != NONE) &
+                                  ellipse_meets_box(g0.x, g0.y, g0.z, g0.w, g1.x, g5.y, g5.z, g5.w, x0, x0 + 7.f,
+                                                    y0, y0 + 7.f);
                 s_item[buf][sl] = it0[r];
                 bits[r] = __ballot_sync(SSSGS_FULL, pass);
             }

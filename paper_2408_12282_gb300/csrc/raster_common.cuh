@@ -208,7 +208,8 @@ __device__ __forceinline__ TilePix tile_pixel(const sssgs_pair& P, int tile, int
 // this one fails.
 __device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, float b, float c, float ia, float ic,
                                                   float lim, float x0, float x1, float y0, float y1) {
-    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+    // both cases evaluated, no early return: the lanes of a warp do not diverge
+    const bool inside = (mx >= x0) & (mx <= x1) & (my >= y0) & (my <= y1);
     float best = 3.0e38f;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -222,7 +223,7 @@ __device__ __forceinline__ bool ellipse_meets_box(float mx, float my, float a, f
         const float dx = fminf(fmaxf(-b * dy * ia, x0 - mx), x1 - mx);
         best = fminf(best, 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy);
     }
-    return best <= lim;
+    return inside | (best <= lim);
 }
 
 // Bit w set: the splat can reach warp w's SW x SH sub-tile of this tile
