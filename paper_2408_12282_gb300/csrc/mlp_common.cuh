@@ -22,8 +22,10 @@ __device__ __forceinline__ float vis_of(const sssgs_scene& sc, int64_t g, int64_
     return sc.vis_item ? __ldg(sc.vis_item + m) : __ldg(sc.vis + g);
 }
 
+// pad = false: the caller has zeroed x, so the columns past the features are
+// left alone (a register array then sees no runtime index).
 __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
-                                            int64_t g, int64_t m, float* x) {
+                                            int64_t g, int64_t m, float* x, bool pad = true) {
     const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
     const float3 C = cam_center(P);
     float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
@@ -57,7 +59,8 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
                 x[21 + 6 * k + c] = co;
             }
         }
-        for (int k = 42; k < net.w[0]; ++k) x[k] = 0.f;
+        if (pad)
+            for (int k = 42; k < net.w[0]; ++k) x[k] = 0.f;
         return;
     }
     const float mm[3] = {m0, m1, m2};
@@ -78,28 +81,32 @@ __device__ __forceinline__ void build_input(const MlpDev& net, const sssgs_pair&
     x[45] = sc.normal[3 * g]; x[46] = sc.normal[3 * g + 1]; x[47] = sc.normal[3 * g + 2];
     x[48] = li;
     x[49] = vis_of(sc, g, m);
-    for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
+    if (pad)
+        for (int k = 50; k < net.w[0]; ++k) x[k] = 0.f;
 }
 
 // Input gradient dX (row) -> (dmu, dn, dv, dquat, dlog_s) of item m, written
 // to dx[SSSGS_DX] (the last 7 are zero for the BASIC and PE6 inputs).
-__device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
-                                               int64_t g, const float* dX, float* dx) {
+// KIND is the network kind (compile time, so a register array dX sees no
+// runtime index); input_backward dispatches on net.kind.
+template <int KIND>
+__device__ __forceinline__ void input_backward_k(const sssgs_pair& P, const sssgs_scene& sc, int64_t g,
+                                                 const float* dX, float* dx) {
     const float m0 = sc.mu[3 * g], m1 = sc.mu[3 * g + 1], m2 = sc.mu[3 * g + 2];
     const float3 C = cam_center(P);
     float3 Vo = make_float3(C.x - m0, C.y - m1, C.z - m2);
     float3 Vi = make_float3(P.light[0] - m0, P.light[1] - m1, P.light[2] - m2);
     const float lo = sqrtf(dot3(Vo, Vo)), li = sqrtf(dot3(Vi, Vi));
     const float3 wo = (1.f / lo) * Vo, wi = (1.f / li) * Vi;
-    int o_mu = -1, o_wo, o_wi;
+    constexpr int o_mu = KIND == SSSGS_MLP_BASIC ? 0 : (KIND == SSSGS_MLP_PAPER ? -1 : 36);
+    constexpr int o_wo = KIND == SSSGS_MLP_BASIC ? 3 : (KIND == SSSGS_MLP_PAPER ? 13 : 39);
+    constexpr int o_wi = KIND == SSSGS_MLP_BASIC ? 6 : (KIND == SSSGS_MLP_PAPER ? 10 : 42);
     float dmu[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 7; k < SSSGS_DX; ++k) dx[k] = 0.f;
-    if (net.kind == SSSGS_MLP_BASIC) {
-        o_mu = 0; o_wo = 3; o_wi = 6;
+    if constexpr (KIND == SSSGS_MLP_BASIC) {
         dx[3] = dx[4] = dx[5] = dx[6] = 0.f;
-    } else if (net.kind == SSSGS_MLP_PAPER) {
-        o_wi = 10; o_wo = 13;
+    } else if constexpr (KIND == SSSGS_MLP_PAPER) {
         const float mm[3] = {m0, m1, m2};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -124,7 +131,6 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
 #pragma unroll
         for (int k = 0; k < 3; ++k) dx[11 + k] = dX[7 + k] * expf(sc.log_s[3 * g + k]);
     } else {
-        o_mu = 36; o_wo = 39; o_wi = 42;
         const float mm[3] = {m0, m1, m2};
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -140,7 +146,7 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
         dx[6] = dX[49];
         dmu[0] -= dX[48] * wi.x; dmu[1] -= dX[48] * wi.y; dmu[2] -= dX[48] * wi.z;
     }
-    if (o_mu >= 0) {
+    if constexpr (o_mu >= 0) {
         dmu[0] += dX[o_mu]; dmu[1] += dX[o_mu + 1]; dmu[2] += dX[o_mu + 2];
     }
     // d unit(P - mu) / d mu applied to g:  -(g - w (w.g)) / |P - mu|
@@ -151,6 +157,13 @@ __device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pa
     dx[0] = dmu[0] + bo.x + bi.x;
     dx[1] = dmu[1] + bo.y + bi.y;
     dx[2] = dmu[2] + bo.z + bi.z;
+}
+
+__device__ __forceinline__ void input_backward(const MlpDev& net, const sssgs_pair& P, const sssgs_scene& sc,
+                                               int64_t g, const float* dX, float* dx) {
+    if (net.kind == SSSGS_MLP_BASIC) input_backward_k<SSSGS_MLP_BASIC>(P, sc, g, dX, dx);
+    else if (net.kind == SSSGS_MLP_PAPER) input_backward_k<SSSGS_MLP_PAPER>(P, sc, g, dX, dx);
+    else input_backward_k<SSSGS_MLP_PE6>(P, sc, g, dX, dx);
 }
 
 // PE6 input (64 features, fixed layout) with compile-time indices, so the

@@ -31,6 +31,7 @@ struct TcLayout {
     uint32_t offA;                     // activation tile
     uint32_t offBias;                  // FP32 biases
     uint32_t offBar;                   // mbarrier + TMEM address
+    uint32_t offTab;                   // per-layer table (TcLayerTab) in shared memory
     uint32_t total;
     int Np[SSSGS_MAX_LAYERS];          // padded output widths
     int biasOff[SSSGS_MAX_LAYERS];
@@ -55,9 +56,19 @@ __host__ __device__ inline TcLayout tc_layout(const MlpDev& net) {
     o = (o + 15) & ~15u;
     T.offBar = o;
     o += 64 + 8 * 256;                           // mbarriers, TMEM address, flags, pair offsets
+    T.offTab = o;
+    o += SSSGS_MAX_LAYERS * 16;
     T.total = o;
     return T;
 }
+
+// One layer's geometry, copied to shared memory at kernel start: a runtime
+// index into the parameter tables would be served from local memory, and with
+// the shared-memory carve-out these kernels take nearly every such load misses
+// L1 and waits on L2 inside each layer round.
+struct TcLayerTab {
+    int K, Np, offW, bias;
+};
 
 // Convert layer weights (FP32, out x in, row-major) into BF16 operand images.
 __device__ __forceinline__ void stage_weights_bf16(const MlpDev& net, const TcLayout& T, uint8_t* smem, float* sbias) {
@@ -107,6 +118,9 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
         tc::fence_mbar_init();
     }
     for (int p = tid; p < n_pairs && p < TC_MAX_SMEM_PAIRS; p += blockDim.x) s_off[p] = pairs[p].item_offset;
+    TcLayerTab* s_tab = reinterpret_cast<TcLayerTab*>(smem + T.offTab);
+    if (tid == 0)
+        for (int l = 0; l < net.L; ++l) s_tab[l] = TcLayerTab{net.w[l], T.Np[l], (int)T.offW[l], T.biasOff[l]};
     stage_weights_bf16(net, T, smem, sbias);
     tc::fence_async_smem();
     tc::fence_before();
@@ -136,11 +150,12 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
         tc::fence_before();
         named_sync(1 + wg, 128);
         for (int l = 0; l < net.L; ++l) {
-            const int K = net.w[l], N = T.Np[l];
+            const TcLayerTab lt = s_tab[l];
+            const int K = lt.K, N = lt.Np;
             if (t == 0) {
                 tc::fence_after();
                 const uint32_t idesc = tc::idesc_bf16(TC_ROWS, N, false, false);
-                const uint32_t w_addr = tc::smem_u32(smem + T.offW[l]);
+                const uint32_t w_addr = tc::smem_u32(smem + lt.offW);
                 const uint32_t sbo = (uint32_t)(K / 8) * 128u;
                 for (int k = 0; k < K / 16; ++k) {
                     const uint64_t ad = tc::make_desc(a_addr + k * 256, 128, sbo);
@@ -155,7 +170,7 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
             tc::fence_after();
             if (!got) s_fail[wg] = 1;
             if (got) {
-                const float* bl = sbias + T.biasOff[l];
+                const float* bl = sbias + lt.bias;
                 if (l < net.L - 1) {
                     for (int c0 = 0; c0 < N; c0 += 64) {
                         float v[64];
@@ -359,6 +374,28 @@ int launch_active_rows(const float* dout, int64_t dstride, int64_t n, uint8_t* f
     return 3;
 }
 
+// Per-layer geometry of the backward network in closed form. The backward
+// runs the fixed widths w = [64, 128, ..., 128, 4] (the host checks them and
+// this geometry against tc_bwd_layout), so a layer's input width, activation
+// and weight-image offsets, bias offset and TMEM column follow from its
+// index. A runtime index into the kernel's parameter tables would be served
+// from local memory, and with the shared-memory carve-out this kernel takes
+// nearly every such load misses L1 and waits on L2 inside each round.
+struct BwdGeom {
+    int L;
+    __host__ __device__ __forceinline__ int kin(int l) const { return l == 0 ? 64 : 128; }
+    __host__ __device__ __forceinline__ int np(int l) const { return l == L - 1 ? 16 : 128; }
+    // H_l in shared memory, and weight image l in the global workspace
+    __host__ __device__ __forceinline__ uint32_t off(int l) const {
+        return l == 0 ? 0u : 16384u + (uint32_t)(l - 1) * 32768u;
+    }
+    __host__ __device__ __forceinline__ uint32_t wbytes(int l) const {
+        return l == 0 ? 16384u : (l == L - 1 ? 4096u : 32768u);
+    }
+    __host__ __device__ __forceinline__ int bias(int l) const { return 128 * l; }
+    __host__ __device__ __forceinline__ int colw(int l) const { return 128 * l; }   // hidden layers 1 .. L-2
+};
+
 __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, TcBwdLayout T,
                                                               const uint8_t* __restrict__ gimg,
                                                               const sssgs_pair* __restrict__ pairs, int n_pairs,
@@ -397,8 +434,14 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     // constants: ones operand (16 x 128, K-major), biases, last-layer db partials
     for (int i = tid; i < 16 * TC_ROWS / 2; i += blockDim.x)
         reinterpret_cast<uint32_t*>(smem + T.offOnes)[i] = 0x3F803F80u;   // two bf16 1.0
-    for (int l = 0; l < L; ++l)
-        for (int n = tid; n < T.Np[l]; n += blockDim.x) sbias[T.biasOff[l] + n] = n < net.w[l + 1] ? net.b[l][n] : 0.f;
+    const BwdGeom G{L};
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const float* bsrc = l == 0 ? net.b[0] : l == 1 ? net.b[1] : l == 2 ? net.b[2] : l == 3 ? net.b[3]
+                          : l == 4 ? net.b[4] : l == 5 ? net.b[5] : l == 6 ? net.b[6] : net.b[7];
+        const int nw = l == L - 1 ? 4 : 128;
+        for (int n = tid; n < G.np(l); n += blockDim.x) sbias[G.bias(l) + n] = n < nw ? bsrc[n] : 0.f;
+    }
     if (tid < 16) sdbL[tid] = 0.f;
     tc::fence_async_smem();
     tc::fence_before();
@@ -430,8 +473,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     const int64_t n_tiles = (n_rows + TC_ROWS - 1) / TC_ROWS;
     if (tid == 0 && (int64_t)blockIdx.x < n_tiles) {   // first weights
         const int l0 = layer_of_use(0);
-        tc::mbar_arrive_expect_tx(bar_w0, T.wbytes[l0]);
-        tc::bulk_g2s(tc::smem_u32(smem + T.offW[0]), gimg + T.gW[l0], T.wbytes[l0], bar_w0);
+        tc::mbar_arrive_expect_tx(bar_w0, G.wbytes(l0));
+        tc::bulk_g2s(tc::smem_u32(smem + T.offW[0]), gimg + G.off(l0), G.wbytes(l0), bar_w0);
     }
     // thread 0: prefetch the next use, then wait for this use's weights
     auto begin_use = [&]() -> bool {
@@ -442,8 +485,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             const int64_t nt = (int64_t)blockIdx.x + (int64_t)(nu / uses_per_tile) * gridDim.x;
             if (nt < n_tiles) {
                 const uint32_t nb = (nu & 1) ? bar_w1 : bar_w0;
-                tc::mbar_arrive_expect_tx(nb, T.wbytes[ln]);
-                tc::bulk_g2s(tc::smem_u32(smem + T.offW[nu & 1]), gimg + T.gW[ln], T.wbytes[ln], nb);
+                tc::mbar_arrive_expect_tx(nb, G.wbytes(ln));
+                tc::bulk_g2s(tc::smem_u32(smem + ((nu & 1) ? T.offW[1] : T.offW[0])), gimg + G.off(ln), G.wbytes(ln), nb);
             }
             got = tc::mbar_wait((use & 1) ? bar_w1 : bar_w0, (use & 1) ? ph_w1 : ph_w0);
             tc::fence_after();
@@ -506,10 +549,10 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
             for (int k = 0; k < 18; ++k) x[k] = 0.f;
             if (valid) pe6_fourier<0, 3>(cur.q.mu, x);
-            store8_bf16(smem + T.offH[0], t, 0, 64, x);
-            store8_bf16(smem + T.offH[0], t, 8, 64, x + 8);
-            store1_bf16(smem + T.offH[0], t, 16, 64, x[16]);
-            store1_bf16(smem + T.offH[0], t, 17, 64, x[17]);
+            store8_bf16(smem + G.off(0), t, 0, 64, x);
+            store8_bf16(smem + G.off(0), t, 8, 64, x + 8);
+            store1_bf16(smem + G.off(0), t, 16, 64, x[16]);
+            store1_bf16(smem + G.off(0), t, 17, 64, x[17]);
         } else {
             float x[46];
 #pragma unroll
@@ -519,20 +562,20 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 pe6_direct(pairs[pidx], cur.q.mu, cur.q.n, cur.q.v, x + 18);
             }
 #pragma unroll
-            for (int c = 18; c < 24; ++c) store1_bf16(smem + T.offH[0], t, c, 64, x[c - 18]);
+            for (int c = 18; c < 24; ++c) store1_bf16(smem + G.off(0), t, c, 64, x[c - 18]);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) store8_bf16(smem + T.offH[0], t, 24 + 8 * q, 64, x + 6 + 8 * q);
+            for (int q = 0; q < 5; ++q) store8_bf16(smem + G.off(0), t, 24 + 8 * q, 64, x + 6 + 8 * q);
         }
         ok = sync_all(true);
         // ---------------- forward recompute
         for (int l = 0; l < L && ok; ++l) {
-            const int K = net.w[l], Np = T.Np[l];
+            const int K = G.kin(l), Np = G.np(l);
             bool mine = begin_use();
             ++use;
             if (tid == 0) {
                 const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Np, false, false);
-                const uint32_t a0 = tc::smem_u32(smem + T.offH[l]);
-                const uint32_t b0 = tc::smem_u32(smem + T.offW[(use - 1) & 1]);
+                const uint32_t a0 = tc::smem_u32(smem + G.off(l));
+                const uint32_t b0 = tc::smem_u32(smem + (((use - 1) & 1) ? T.offW[1] : T.offW[0]));
                 const uint32_t sbo = (uint32_t)(K / 8) * 128u;
                 for (int k = 0; k < K / 16; ++k)
                     tc::mma_bf16(tmem, tc::make_desc(a0 + k * 256, 128, sbo), tc::make_desc(b0 + k * 256, 128, sbo),
@@ -541,9 +584,9 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             }
             __syncwarp();
             mine = wait_mma() && mine;
-            const float* bl = sbias + T.biasOff[l];
+            const float* bl = sbias + G.bias(l);
             if (l < L - 1) {
-                const int N = net.w[l + 1];
+                const int N = 128;
                 if (N == 128) {
                     const int c0 = wg * 64;
                     float v[64];
@@ -551,7 +594,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
                     for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) store8_bf16(smem + T.offH[l + 1], t, c0 + 8 * q, N, v + 8 * q);
+                    for (int q = 0; q < 8; ++q) store8_bf16(smem + G.off(l + 1), t, c0 + 8 * q, N, v + 8 * q);
                 } else {
                     for (int c0 = wg * (N / 2); c0 < (wg + 1) * (N / 2); c0 += 32) {
                         float v[32];
@@ -559,7 +602,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) store8_bf16(smem + T.offH[l + 1], t, c0 + 8 * q, N, v + 8 * q);
+                        for (int q = 0; q < 4; ++q) store8_bf16(smem + G.off(l + 1), t, c0 + 8 * q, N, v + 8 * q);
                     }
                 }
             } else if (wg == 0) {
@@ -598,25 +641,25 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         }
         // ---------------- backward
         for (int l = L - 1; l >= 0 && ok; --l) {
-            const int Kin = net.w[l];
+            const int Kin = G.kin(l);
             const bool last = (l == L - 1);
-            const int Nout = last ? 16 : net.w[l + 1];        // dZ_{l+1} columns (padded for the last layer)
-            const uint8_t* dzbuf = last ? sDZL : smem + T.offH[l + 1];
+            const int Nout = last ? 16 : 128;        // dZ_{l+1} columns (padded for the last layer)
+            const uint8_t* dzbuf = last ? sDZL : smem + G.off(l + 1);
             const uint32_t dz_addr = tc::smem_u32(dzbuf);
             const uint32_t dz_sr = (uint32_t)(Nout / 8) * 128u;
-            const uint32_t h_addr = tc::smem_u32(smem + T.offH[l]);
+            const uint32_t h_addr = tc::smem_u32(smem + G.off(l));
             const uint32_t h_sr = (uint32_t)(Kin / 8) * 128u;
             bool mine = begin_use();
             ++use;
-            const uint32_t w_addr = tc::smem_u32(smem + T.offW[(use - 1) & 1]);
+            const uint32_t w_addr = tc::smem_u32(smem + (((use - 1) & 1) ? T.offW[1] : T.offW[0]));
             const uint32_t w_sr = (uint32_t)(Kin / 8) * 128u;    // weight image: rows = outputs, C = Kin
             const int halves = Kin > 64 ? 2 : 1;
             if (tid == 0) {
                 // per-tile or accumulated weight gradient, K' = 128 rows
-                if (T.colW[l] >= 0 && l >= 1 && l <= L - 2) {
+                if (l >= 1 && l <= L - 2) {
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin, true, true);
                     for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16(tmem + T.colW[l], tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
+                        tc::mma_bf16(tmem + G.colw(l), tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
                                      tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128), idesc,
                                      (any_tile || k > 0) ? 1u : 0u);
                 } else if (last) {      // dW_{L-1}^T = H_{L-1}^T dZ_L  -> [Kin x 16]
@@ -688,7 +731,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                     for (int c0 = 32 * wg; c0 < ncols; c0 += 64) {
                         float v[32];
                         tc::tmem_ld32(tmem + lane_off + c0, v);
-                        uint8_t* hb = smem + T.offH[l];
+                        uint8_t* hb = smem + G.off(l);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int c = cbase + c0 + 8 * q;
@@ -758,26 +801,33 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         if (tid == 0 && status) atomicOr(status, SSSGS_STATUS_TIMEOUT);
     } else if (any_tile) {
         // flush: dW of hidden layers from TMEM, dW_0 / dW_{L-1} / db from registers
-        for (int l = 1; l <= L - 2; ++l) {
-            const int Kin = net.w[l];
-            for (int c0 = 32 * wg; c0 < Kin; c0 += 64) {
+        // (layer indices unrolled, so no parameter table is indexed at run time)
+#pragma unroll
+        for (int l = 1; l < SSSGS_MAX_LAYERS - 1; ++l) {
+            if (l > L - 2) break;
+            for (int c0 = 32 * wg; c0 < 128; c0 += 64) {
                 float v[32];
-                tc::tmem_ld32(tmem + lane_off + T.colW[l] + c0, v);
-                if (t < net.w[l + 1])
-                    for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[l][t * Kin + c0 + j], v[j]);
+                tc::tmem_ld32(tmem + lane_off + G.colw(l) + c0, v);
+                for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[l][t * 128 + c0 + j], v[j]);
             }
         }
-        if (t < net.w[1])
-            for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[0][t * net.w[0] + 32 * wg + j], acc0[j]);
+        for (int j = 0; j < 32; ++j) atomicAdd(&gr.W[0][t * 64 + 32 * wg + j], acc0[j]);
+        float* dWL = gr.W[0];
+        float* dbL = gr.b[0];
+#pragma unroll
+        for (int l = 1; l < SSSGS_MAX_LAYERS; ++l)
+            if (l == L - 1) {
+                dWL = gr.W[l];
+                dbL = gr.b[l];
+            }
         if (wg == 0) {
-            if (t < net.w[L - 1])
-                for (int c = 0; c < net.w[L]; ++c) atomicAdd(&gr.W[L - 1][c * net.w[L - 1] + t], accL[c]);
+            for (int c = 0; c < 4; ++c) atomicAdd(&dWL[c * 128 + t], accL[c]);
 #pragma unroll
             for (int j = 0; j < SSSGS_MAX_LAYERS; ++j)
-                if (j <= L - 2 && gr.b[j] && t < net.w[j + 1]) atomicAdd(&gr.b[j][t], dbacc[j]);
+                if (j <= L - 2 && gr.b[j]) atomicAdd(&gr.b[j][t], dbacc[j]);
         }
         __syncthreads();
-        if (gr.b[L - 1] && tid < net.w[L]) atomicAdd(&gr.b[L - 1][tid], sdbL[tid]);
+        if (dbL && tid < 4) atomicAdd(&dbL[tid], sdbL[tid]);
     }
     tc::fence_before();
     __syncthreads();
@@ -868,6 +918,12 @@ int sssgs_mlp_bwd_tc(const sssgs_mlp* mlp, const sssgs_pair* h_pairs, const sssg
     if (T.colW[0] > 512 || T.total > 227 * 1024 || net.w[1] != 128) return SSSGS_ERR_UNSUPPORTED;
     for (int l = 1; l < net.L; ++l)
         if (net.w[l] != 128) return SSSGS_ERR_UNSUPPORTED;
+    const BwdGeom G{net.L};
+    for (int l = 0; l < net.L; ++l)
+        if (G.kin(l) != net.w[l] || G.np(l) != T.Np[l] || G.off(l) != T.offH[l] || G.off(l) != T.gW[l] ||
+            G.wbytes(l) != T.wbytes[l] || G.bias(l) != T.biasOff[l] ||
+            (l >= 1 && l <= net.L - 2 && G.colw(l) != T.colW[l]))
+            return SSSGS_ERR_UNSUPPORTED;
     int64_t n = h_pairs[n_pairs - 1].item_offset + h_pairs[n_pairs - 1].g_count;
     if (n == 0) return SSSGS_OK;
     if (n >= ((int64_t)1 << 32)) return SSSGS_ERR_INVALID_ARG;    // row list holds u32 item ids

@@ -68,6 +68,13 @@ struct PSmem {
     static constexpr uint32_t TOTAL = LANE0 + PLANES * LANE_BYTES;
 };
 static_assert(PSmem::W(NCH) <= PSmem::ONES, "weight images overlap");
+
+// Offset of chain layer l's input tile within a lane. Computed, not looked
+// up: a runtime index into a local array of tile pointers is served from local
+// memory, and with this kernel's shared-memory carve-out such loads miss L1.
+__host__ __device__ constexpr uint32_t act_off(int l) {
+    return l == 0 ? PSmem::X : (l == 1 ? PSmem::H1 : (l == 2 ? PSmem::H2 : (l == 3 ? PSmem::T : PSmem::G)));
+}
 static_assert(PSmem::TOTAL <= 227 * 1024, "shared memory budget");
 
 // Weight (n, k) of chain layer l and bias n, from the caller's six matrices.
@@ -111,7 +118,6 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
     volatile int* s_fail = reinterpret_cast<volatile int*>(smem + PSmem::BAR + 40);
     int64_t* s_off = reinterpret_cast<int64_t*>(smem + PSmem::PAIRS);
     uint8_t* lane = smem + PSmem::LANE0 + wg * PSmem::LANE_BYTES;
-    uint8_t* act[NCH] = {lane + PSmem::X, lane + PSmem::H1, lane + PSmem::H2, lane + PSmem::T, lane + PSmem::G};
     uint8_t* sDZ = lane + PSmem::DZ;
 
     if (tid < 32) {
@@ -170,13 +176,13 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
     auto mma_fwd = [&](int l) {
         const int K = kin(l);
         const uint32_t idesc = tc::idesc_bf16(PR, nout(l), false, false);
-        const uint32_t a = tc::smem_u32(act[l]), w = tc::smem_u32(smem + PSmem::W(l));
+        const uint32_t a = tc::smem_u32((lane + act_off(l))), w = tc::smem_u32(smem + PSmem::W(l));
         for (int k = 0; k < K / 16; ++k) tc::mma_bf16(work, kmaj(a + k * 256, K), kmaj(w + k * 256, K), idesc, k > 0 ? 1u : 0u);
     };
     // dW_l += dZ^T H_l, db_l += dZ^T 1, D(work) = dZ W_l (dZ in sDZ, C = 64)
     auto mma_bwd = [&](int l) {
         const int K = kin(l), No = nout(l);
-        const uint32_t dz = tc::smem_u32(sDZ), h = tc::smem_u32(act[l]);
+        const uint32_t dz = tc::smem_u32(sDZ), h = tc::smem_u32((lane + act_off(l)));
         const uint32_t ones = tc::smem_u32(smem + PSmem::ONES), w = tc::smem_u32(smem + PSmem::W(l));
         const uint32_t hsr = (uint32_t)(K / 8) * 128u;
         const uint32_t idw = tc::idesc_bf16(PR, K, true, true), idb = tc::idesc_bf16(PR, 16, true, false);
@@ -205,9 +211,9 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
 #pragma unroll
             for (int k = 0; k < 48; ++k) x[k] = 0.f;
             if (valid)
-                build_input(net, pairs[pidx], sc, pairs[pidx].g_begin + (m - pairs[pidx].item_offset), m, x);
+                build_input(net, pairs[pidx], sc, pairs[pidx].g_begin + (m - pairs[pidx].item_offset), m, x, false);
 #pragma unroll
-            for (int c = 0; c < 48; c += 8) store8_bf16(act[0], t, c, 48, x + c);
+            for (int c = 0; c < 48; c += 8) store8_bf16((lane + act_off(0)), t, c, 48, x + c);
         }
         ok = round_end();
         // ---- forward
@@ -228,14 +234,14 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
 #pragma unroll
                     for (int j = 0; j < 64; ++j) v[j] = lrelu(v[j] + bl[j]);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) store8_bf16(act[1], t, 8 * q, 64, v + 8 * q);
+                    for (int q = 0; q < 8; ++q) store8_bf16((lane + act_off(1)), t, 8 * q, 64, v + 8 * q);
                 } else if (l < 4) {
                     float v[32];
                     tc::tmem_ld32(work_l, v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = lrelu(v[j] + bl[j]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) store8_bf16(act[l + 1], t, 8 * q, 32, v + 8 * q);
+                    for (int q = 0; q < 4; ++q) store8_bf16((lane + act_off(l + 1)), t, 8 * q, 32, v + 8 * q);
                     if (l == 3) {   // SSS head: logits in columns 32..34
                         float h[16];
                         tc::tmem_ld16(work_l + 32, h);
@@ -278,11 +284,13 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
             if (s_fail[wg] == 0) {
                 const int K = kin(l);   // width of dH_l
                 if (l > 0) {
-                    // dZ_l = bf16(dH_l * act'(H_l)), H_l = act[l] (Leaky-ReLU output)
+                    // dZ_l = bf16(dH_l * act'(H_l)), H_l = (lane + act_off(l)) (Leaky-ReLU output)
                     float v[64];
                     if (K == 64) tc::tmem_ld64(work_l, v); else tc::tmem_ld32(work_l, v);
-                    for (int c0 = 0; c0 < K; c0 += 8) {
-                        const uint4 hq = load8_packed(act[l], t, c0, K);
+#pragma unroll
+                    for (int c0 = 0; c0 < 64; c0 += 8) {
+                        if (c0 >= K) break;
+                        const uint4 hq = load8_packed((lane + act_off(l)), t, c0, K);
                         const float hv[8] = {tc::bf16_lo(hq.x), tc::bf16_hi(hq.x), tc::bf16_lo(hq.y), tc::bf16_hi(hq.y),
                                              tc::bf16_lo(hq.z), tc::bf16_hi(hq.z), tc::bf16_lo(hq.w), tc::bf16_hi(hq.w)};
                         float o[8];
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
                     if (valid) {
                         float dx[SSSGS_DX];
                         const sssgs_pair& P = pairs[pidx];
-                        input_backward(net, P, sc, P.g_begin + (m - P.item_offset), dX, dx);
+                        input_backward_k<SSSGS_MLP_PAPER>(P, sc, P.g_begin + (m - P.item_offset), dX, dx);
 #pragma unroll
                         for (int k = 0; k < SSSGS_DX; ++k) dx_items[(int64_t)SSSGS_DX * m + k] = dx[k];
                     }
