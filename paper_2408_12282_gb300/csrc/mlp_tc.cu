@@ -152,19 +152,17 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
         for (int l = 0; l < net.L; ++l) {
             const TcLayerTab lt = s_tab[l];
             const int K = lt.K, N = lt.Np;
-            if (t == 0) {
+            if (t < 32) {   // the lane group's first warp; lane 0 issues
                 tc::fence_after();
                 const uint32_t idesc = tc::idesc_bf16(TC_ROWS, N, false, false);
-                const uint32_t w_addr = tc::smem_u32(smem + lt.offW);
                 const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-                for (int k = 0; k < K / 16; ++k) {
-                    const uint64_t ad = tc::make_desc(a_addr + k * 256, 128, sbo);
-                    const uint64_t bd = tc::make_desc(w_addr + k * 256, 128, sbo);
-                    tc::mma_bf16(tmem, ad, bd, idesc, k > 0 ? 1u : 0u);
-                }
-                tc::mma_commit(bar);
+                const tc::Desc2 da = tc::desc2(a_addr, 128, sbo);
+                const tc::Desc2 dw = tc::desc2(tc::smem_u32(smem + lt.offW), 128, sbo);
+#pragma unroll
+                for (int k = 0; k < TC_MAXW / 16; ++k)
+                    if (k < K / 16) tc::mma_bf16_w(tmem, da, k * 256, dw, k * 256, idesc, k > 0 ? 1u : 0u, t);
+                tc::mma_commit_w(bar, t);
             }
-            __syncwarp();
             const bool got = tc::mbar_wait(bar, phase);
             phase ^= 1;
             tc::fence_after();
@@ -225,7 +223,7 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
 
 struct TcBwdLayout {
     uint32_t offH[SSSGS_MAX_LAYERS];   // layer inputs (later dZ, in place)
-    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offDx, offBar, offPairs;
+    uint32_t offDZL, offOnes, offW[2], offBias, offDbL, offDx, offBar, offPairs, offGb;
     uint32_t total;
     uint32_t gW[SSSGS_MAX_LAYERS];     // weight image offsets in the global workspace
     uint32_t wbytes[SSSGS_MAX_LAYERS];
@@ -264,6 +262,7 @@ __host__ __device__ inline TcBwdLayout tc_bwd_layout(const MlpDev& net) {
     T.offDx = o;   o += 7 * TC_ROWS * 4;
     T.offBar = o;  o += 32;
     T.offPairs = o; o += 8 * 256;
+    T.offGb = o;   o += 4 * 256;
     T.total = o;
     T.gtotal = g;
     T.colW[0] = col;          // > 512 signals "does not fit" to the host check
@@ -412,6 +411,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     const int tid = threadIdx.x, lane = tid & 31, wg = tid >> 7, t = tid & 127, warp = (tid >> 5) & 3;
     const int L = net.L;
     int64_t* s_off = reinterpret_cast<int64_t*>(smem + T.offPairs);
+    int* s_gb = reinterpret_cast<int*>(smem + T.offGb);
     float* sbias = reinterpret_cast<float*>(smem + T.offBias);
     float* sdbL = reinterpret_cast<float*>(smem + T.offDbL);
     const uint32_t bar_m = tc::smem_u32(smem + T.offBar);
@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         tc::tmem_alloc(tc::smem_u32(s_tmem), 512);
         tc::tmem_relinquish();
     }
-    for (int p = tid; p < n_pairs && p < TC_MAX_SMEM_PAIRS; p += blockDim.x) s_off[p] = pairs[p].item_offset;
+    for (int p = tid; p < n_pairs && p < TC_MAX_SMEM_PAIRS; p += blockDim.x) {
+        s_off[p] = pairs[p].item_offset;
+        s_gb[p] = pairs[p].g_begin;
+    }
     if (tid == 0) {
         tc::mbar_init(bar_m, 1);
         tc::mbar_init(bar_w0, 1);
@@ -460,8 +463,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
 #pragma unroll
     for (int j = 0; j < SSSGS_MAX_LAYERS; ++j) dbacc[j] = 0.f;
 
-    uint32_t ph_m = 0, ph_w0 = 0, ph_w1 = 0;
-    uint32_t use = 0;            // weight-use counter (2L uses per tile)
+    uint32_t ph_m = 0;
+    uint32_t use = 0;            // weight uses begun (2L per tile); use u reads slot u & 1
     bool ok = true, any_tile = false;
     const int uses_per_tile = 2 * L;
     auto layer_of_use = [&](uint32_t u) -> int {
@@ -471,28 +474,37 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     // rows = the active items (see k_active_count)
     const int64_t n_rows = *n_active;
     const int64_t n_tiles = (n_rows + TC_ROWS - 1) / TC_ROWS;
-    if (tid == 0 && (int64_t)blockIdx.x < n_tiles) {   // first weights
-        const int l0 = layer_of_use(0);
-        tc::mbar_arrive_expect_tx(bar_w0, G.wbytes(l0));
-        tc::bulk_g2s(tc::smem_u32(smem + T.offW[0]), gimg + G.off(l0), G.wbytes(l0), bar_w0);
+    const uint32_t wslot0 = tc::smem_u32(smem + T.offW[0]), wslot1 = tc::smem_u32(smem + T.offW[1]);
+    // Weight images stream into two slots. The copy for use u + 2 starts as
+    // soon as the MMAs of use u have completed (its slot's release), so it
+    // has the rest of use u and all of use u + 1 to land. Thread 0 copies;
+    // fetched = one past the last use copied.
+    uint32_t fetched = 0;
+    auto fetch_use = [&](uint32_t u) {
+        const int64_t tl = (int64_t)blockIdx.x + (int64_t)(u / (uint32_t)uses_per_tile) * gridDim.x;
+        if (tl < n_tiles) {
+            const int lu = layer_of_use(u);
+            const uint32_t b = (u & 1) ? bar_w1 : bar_w0;
+            tc::mbar_arrive_expect_tx(b, G.wbytes(lu));
+            tc::bulk_g2s((u & 1) ? wslot1 : wslot0, gimg + G.off(lu), G.wbytes(lu), b);
+            fetched = u + 1;
+        }
+    };
+    if (tid == 0) {
+        fetch_use(0);
+        fetch_use(1);
     }
-    // thread 0: prefetch the next use, then wait for this use's weights
+    // warp 0 (which issues the MMAs): wait for this use's weights
     auto begin_use = [&]() -> bool {
         bool got = true;
-        if (tid == 0) {
-            const uint32_t nu = use + 1;
-            const int ln = layer_of_use(nu);
-            const int64_t nt = (int64_t)blockIdx.x + (int64_t)(nu / uses_per_tile) * gridDim.x;
-            if (nt < n_tiles) {
-                const uint32_t nb = (nu & 1) ? bar_w1 : bar_w0;
-                tc::mbar_arrive_expect_tx(nb, G.wbytes(ln));
-                tc::bulk_g2s(tc::smem_u32(smem + ((nu & 1) ? T.offW[1] : T.offW[0])), gimg + G.off(ln), G.wbytes(ln), nb);
-            }
-            got = tc::mbar_wait((use & 1) ? bar_w1 : bar_w0, (use & 1) ? ph_w1 : ph_w0);
+        if (tid < 32) {
+            got = tc::mbar_wait((use & 1) ? bar_w1 : bar_w0, (use >> 1) & 1u);
             tc::fence_after();
         }
-        if (use & 1) ph_w1 ^= 1u; else ph_w0 ^= 1u;
         return got;
+    };
+    auto release_use = [&](uint32_t u) {
+        if (tid == 0) fetch_use(u + 2);
     };
     auto wait_mma = [&]() -> bool {
         const bool got = tc::mbar_wait(bar_m, ph_m);
@@ -506,8 +518,10 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         return __syncthreads_and(mine) != 0;
     };
 
-    // Per-row inputs (network parameters and upstream gradient) of a tile;
-    // those of the next tile are loaded while the current one is processed.
+    // Per-row inputs (network parameters and upstream gradient) of a tile:
+    // the row ids two tiles ahead and the inputs of the next tile are loaded
+    // while the current one is processed, so no load waits on another load
+    // inside a tile.
     struct RowIn {
         Pe6Params q;
         float up[4];
@@ -515,17 +529,21 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         int pidx;
         bool valid;
     };
-    auto load_row = [&](int64_t tl) -> RowIn {
-        RowIn r;
+    auto load_act = [&](int64_t tl) -> int64_t {
         const int64_t row = tl * TC_ROWS + t;
-        r.valid = tl < n_tiles && row < n_rows;
+        return (tl < n_tiles && row < n_rows) ? (int64_t)active[row] : (int64_t)-1;
+    };
+    auto load_row = [&](int64_t mr) -> RowIn {
+        RowIn r;
+        r.valid = mr >= 0;
         r.pidx = 0;
         r.m = 0;
         if (r.valid) {
-            const int64_t mr = active[row];
             r.m = mr;
             r.pidx = pair_lookup(s_off, pairs, n_pairs, mr);
-            r.q = load_pe6_params(sc, pairs[r.pidx].g_begin + (mr - pairs[r.pidx].item_offset), mr);
+            const int gb = n_pairs <= TC_MAX_SMEM_PAIRS ? s_gb[r.pidx] : pairs[r.pidx].g_begin;
+            const int64_t io = n_pairs <= TC_MAX_SMEM_PAIRS ? s_off[r.pidx] : pairs[r.pidx].item_offset;
+            r.q = load_pe6_params(sc, gb + (mr - io), mr);
             const float4 u = *reinterpret_cast<const float4*>(dout + dstride * mr);
             r.up[0] = u.x;
             r.up[1] = u.y;
@@ -534,14 +552,17 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         }
         return r;
     };
-    RowIn cur = load_row(blockIdx.x);
+    RowIn cur = load_row(load_act(blockIdx.x));
+    int64_t act1 = load_act((int64_t)blockIdx.x + gridDim.x);
     float dmu_a[3] = {0.f, 0.f, 0.f};     // Fourier part of dL/dmu (frequencies 0..2, warpgroup 0)
+    const uint32_t ones = tc::smem_u32(smem + T.offOnes);
 
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int64_t m = cur.m;
         const bool valid = cur.valid;
         const int pidx = cur.pidx;
-        const RowIn nxt = load_row(tile + gridDim.x);
+        const int64_t act2 = load_act(tile + 2 * (int64_t)gridDim.x);
+        const RowIn nxt = load_row(act1);
         // H_0: network input, split between the warpgroups: columns [0, 18)
         // (frequencies 0..2) on warpgroup 0, [18, 64) on warpgroup 1.
         if (wg == 0) {
@@ -572,18 +593,18 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             const int K = G.kin(l), Np = G.np(l);
             bool mine = begin_use();
             ++use;
-            if (tid == 0) {
+            if (tid < 32) {
                 const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Np, false, false);
-                const uint32_t a0 = tc::smem_u32(smem + G.off(l));
-                const uint32_t b0 = tc::smem_u32(smem + (((use - 1) & 1) ? T.offW[1] : T.offW[0]));
                 const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-                for (int k = 0; k < K / 16; ++k)
-                    tc::mma_bf16(tmem, tc::make_desc(a0 + k * 256, 128, sbo), tc::make_desc(b0 + k * 256, 128, sbo),
-                                 idesc, k > 0 ? 1u : 0u);
-                tc::mma_commit(bar_m);
+                const tc::Desc2 da = tc::desc2(tc::smem_u32(smem + G.off(l)), 128, sbo);
+                const tc::Desc2 dw = tc::desc2(((use - 1) & 1) ? wslot1 : wslot0, 128, sbo);
+#pragma unroll
+                for (int k = 0; k < TC_MAXW / 16; ++k)
+                    if (k < K / 16) tc::mma_bf16_w(tmem, da, k * 256, dw, k * 256, idesc, k > 0 ? 1u : 0u, lane);
+                tc::mma_commit_w(bar_m, lane);
             }
-            __syncwarp();
             mine = wait_mma() && mine;
+            release_use(use - 1);
             const float* bl = sbias + G.bias(l);
             if (l < L - 1) {
                 const int N = 128;
@@ -654,41 +675,46 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             const uint32_t w_addr = tc::smem_u32(smem + (((use - 1) & 1) ? T.offW[1] : T.offW[0]));
             const uint32_t w_sr = (uint32_t)(Kin / 8) * 128u;    // weight image: rows = outputs, C = Kin
             const int halves = Kin > 64 ? 2 : 1;
-            if (tid == 0) {
+            if (tid < 32) {
                 // per-tile or accumulated weight gradient, K' = 128 rows
+                const tc::Desc2 dzm = tc::desc2(dz_addr, dz_sr, 128);    // dZ, MN-major (K = rows)
+                const tc::Desc2 hm = tc::desc2(h_addr, h_sr, 128);       // H_l, MN-major (K = rows)
                 if (l >= 1 && l <= L - 2) {
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin, true, true);
+#pragma unroll
                     for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16(tmem + G.colw(l), tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
-                                     tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128), idesc,
-                                     (any_tile || k > 0) ? 1u : 0u);
+                        tc::mma_bf16_w(tmem + G.colw(l), dzm, k * 2 * dz_sr, hm, k * 2 * h_sr, idesc,
+                                       (any_tile || k > 0) ? 1u : 0u, lane);
                 } else if (last) {      // dW_{L-1}^T = H_{L-1}^T dZ_L  -> [Kin x 16]
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, true);
+#pragma unroll
                     for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16(tmem + 64, tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128),
-                                     tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128), idesc, k > 0 ? 1u : 0u);
+                        tc::mma_bf16_w(tmem + 64, hm, k * 2 * h_sr, dzm, k * 2 * dz_sr, idesc, k > 0 ? 1u : 0u, lane);
                 } else {                // l == 0: dW_0 = dZ_1^T H_0 -> [w1 x Kin]
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin, true, true);
+#pragma unroll
                     for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16(tmem + 64, tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
-                                     tc::make_desc(h_addr + k * 2 * h_sr, h_sr, 128), idesc, k > 0 ? 1u : 0u);
+                        tc::mma_bf16_w(tmem + 64, dzm, k * 2 * dz_sr, hm, k * 2 * h_sr, idesc, k > 0 ? 1u : 0u, lane);
                 }
                 if (!last && l >= 1) {  // db_l = dZ_{l+1}^T 1 -> [Nout x 16]
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
-                    const uint32_t ones = tc::smem_u32(smem + T.offOnes);
+                    const tc::Desc2 on = tc::desc2(ones, 128, (TC_ROWS / 8) * 128);
+#pragma unroll
                     for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16(tmem + 64, tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
-                                     tc::make_desc(ones + k * 256, 128, (TC_ROWS / 8) * 128), idesc, k > 0 ? 1u : 0u);
+                        tc::mma_bf16_w(tmem + 64, dzm, k * 2 * dz_sr, on, k * 256, idesc, k > 0 ? 1u : 0u, lane);
                 }
                 // dH_l, first half: [128 x min(64, Kin)] = dZ_{l+1} W_l
                 const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin > 64 ? 64 : Kin, false, true);
-                for (int k = 0; k < Nout / 16; ++k)
-                    tc::mma_bf16(tmem, tc::make_desc(dz_addr + k * 256, 128, dz_sr),
-                                 tc::make_desc(w_addr + k * 2 * w_sr, w_sr, 128), idesc, k > 0 ? 1u : 0u);
-                tc::mma_commit(bar_m);
+                const tc::Desc2 dzk = tc::desc2(dz_addr, 128, dz_sr);    // dZ, K-major (K = outputs)
+                const tc::Desc2 wm = tc::desc2(w_addr, w_sr, 128);       // W_l, MN-major (K = outputs)
+#pragma unroll
+                for (int k = 0; k < TC_MAXW / 16; ++k)
+                    if (k < Nout / 16)
+                        tc::mma_bf16_w(tmem, dzk, k * 256, wm, k * 2 * w_sr, idesc, k > 0 ? 1u : 0u, lane);
+                tc::mma_commit_w(bar_m, lane);
             }
-            __syncwarp();
             mine = wait_mma() && mine;
+            if (halves == 1) release_use(use - 1);
             // epilogue after the first dH half
             if (last) {
                 if (wg == 0) {
@@ -713,17 +739,19 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 if (h == 1) {
                     if (halves == 1) break;
                     mine = sync_all(mine);
-                    if (tid == 0) {
+                    if (tid < 32) {
                         tc::fence_after();
                         const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 64, false, true);
-                        for (int k = 0; k < Nout / 16; ++k)
-                            tc::mma_bf16(tmem, tc::make_desc(dz_addr + k * 256, 128, dz_sr),
-                                         tc::make_desc(w_addr + 8 * 128 + k * 2 * w_sr, w_sr, 128), idesc,
-                                         k > 0 ? 1u : 0u);
-                        tc::mma_commit(bar_m);
+                        const tc::Desc2 dzk = tc::desc2(dz_addr, 128, dz_sr);
+                        const tc::Desc2 wm = tc::desc2(w_addr + 8 * 128, w_sr, 128);
+#pragma unroll
+                        for (int k = 0; k < TC_MAXW / 16; ++k)
+                            if (k < Nout / 16)
+                                tc::mma_bf16_w(tmem, dzk, k * 256, wm, k * 2 * w_sr, idesc, k > 0 ? 1u : 0u, lane);
+                        tc::mma_commit_w(bar_m, lane);
                     }
-                    __syncwarp();
                     mine = wait_mma() && mine;
+                    release_use(use - 1);
                 }
                 const int cbase = 64 * h;
                 const int ncols = Kin - cbase < 64 ? Kin - cbase : 64;
@@ -775,15 +803,16 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                         dx_items[SSSGS_DX * m + k] = s_dx[k * TC_ROWS + t] + (k < 3 ? dmu_a[k] : 0.f);
                     // columns 7..13 (no q, log_s inputs) stay as cleared
                 }
-                if (tid == 0) {
+                if (tid < 32) {
+                    tc::fence_after();
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
-                    const uint32_t ones = tc::smem_u32(smem + T.offOnes);
+                    const tc::Desc2 dzm = tc::desc2(dz_addr, dz_sr, 128);
+                    const tc::Desc2 on = tc::desc2(ones, 128, (TC_ROWS / 8) * 128);
+#pragma unroll
                     for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16(tmem, tc::make_desc(dz_addr + k * 2 * dz_sr, dz_sr, 128),
-                                     tc::make_desc(ones + k * 256, 128, (TC_ROWS / 8) * 128), idesc, k > 0 ? 1u : 0u);
-                    tc::mma_commit(bar_m);
+                        tc::mma_bf16_w(tmem, dzm, k * 2 * dz_sr, on, k * 256, idesc, k > 0 ? 1u : 0u, lane);
+                    tc::mma_commit_w(bar_m, lane);
                 }
-                __syncwarp();
                 mine = wait_mma() && mine;
                 if (wg == 0) {
                     float v[16];
@@ -796,7 +825,11 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         }
         any_tile = true;
         cur = nxt;
+        act1 = act2;
     }
+    // copies still in flight after a failed wait: let them land (bounded)
+    if (tid == 0)
+        for (uint32_t u = use; u < fetched; ++u) tc::mbar_wait((u & 1) ? bar_w1 : bar_w0, (u >> 1) & 1u);
     if (!ok) {
         if (tid == 0 && status) atomicOr(status, SSSGS_STATUS_TIMEOUT);
     } else if (any_tile) {

@@ -91,14 +91,6 @@ __device__ __forceinline__ float pb(const MlpDev& net, int l, int n) {
 
 __device__ __forceinline__ float lrelu(float v) { return v > 0.f ? v : kLReluSlope * v; }
 
-// Instruction descriptor and operand descriptors.
-__device__ __forceinline__ uint64_t kmaj(uint32_t addr, int C) {      // K along C, rows along M/N
-    return tc::make_desc(addr, 128, (uint32_t)(C / 8) * 128u);
-}
-__device__ __forceinline__ uint64_t mnmaj(uint32_t addr, int C) {     // M/N along C, K along rows
-    return tc::make_desc(addr, (uint32_t)(C / 8) * 128u, 128);
-}
-
 // Forward (BWD = false: rows are the items, writes out) or backward (BWD =
 // true: rows are the active items, recompute + back-propagate, gradients).
 template <bool BWD>
@@ -172,27 +164,36 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
         named_sync(1 + wg, PT);
         return s_fail[wg] == 0;
     };
+    // Issued from the lane group's first warp (t < 32), lane 0 executing:
     // D(work) = A(kin(l)) W_l^T
     auto mma_fwd = [&](int l) {
         const int K = kin(l);
         const uint32_t idesc = tc::idesc_bf16(PR, nout(l), false, false);
-        const uint32_t a = tc::smem_u32((lane + act_off(l))), w = tc::smem_u32(smem + PSmem::W(l));
-        for (int k = 0; k < K / 16; ++k) tc::mma_bf16(work, kmaj(a + k * 256, K), kmaj(w + k * 256, K), idesc, k > 0 ? 1u : 0u);
+        const tc::Desc2 a = tc::desc2(tc::smem_u32(lane + act_off(l)), 128, (uint32_t)(K / 8) * 128u);
+        const tc::Desc2 w = tc::desc2(tc::smem_u32(smem + PSmem::W(l)), 128, (uint32_t)(K / 8) * 128u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < K / 16) tc::mma_bf16_w(work, a, k * 256, w, k * 256, idesc, k > 0 ? 1u : 0u, t);
     };
     // dW_l += dZ^T H_l, db_l += dZ^T 1, D(work) = dZ W_l (dZ in sDZ, C = 64)
     auto mma_bwd = [&](int l) {
         const int K = kin(l), No = nout(l);
-        const uint32_t dz = tc::smem_u32(sDZ), h = tc::smem_u32((lane + act_off(l)));
+        const uint32_t dz = tc::smem_u32(sDZ), h = tc::smem_u32(lane + act_off(l));
         const uint32_t ones = tc::smem_u32(smem + PSmem::ONES), w = tc::smem_u32(smem + PSmem::W(l));
         const uint32_t hsr = (uint32_t)(K / 8) * 128u;
         const uint32_t idw = tc::idesc_bf16(PR, K, true, true), idb = tc::idesc_bf16(PR, 16, true, false);
+        const tc::Desc2 dzm = tc::desc2(dz, 8 * 128, 128), hm = tc::desc2(h, hsr, 128);
+        const tc::Desc2 on = tc::desc2(ones, 128, (PR / 8) * 128);
+#pragma unroll
         for (int k = 0; k < PR / 16; ++k) {
-            tc::mma_bf16(tmem + acc_w(l), mnmaj(dz + k * 2048, 64), mnmaj(h + k * 2 * hsr, K), idw, 1u);
-            tc::mma_bf16(tmem + acc_b(l), mnmaj(dz + k * 2048, 64), kmaj(ones + k * 256, PR), idb, 1u);
+            tc::mma_bf16_w(tmem + acc_w(l), dzm, k * 2048, hm, k * 2 * hsr, idw, 1u, t);
+            tc::mma_bf16_w(tmem + acc_b(l), dzm, k * 2048, on, k * 256, idb, 1u, t);
         }
         const uint32_t idh = tc::idesc_bf16(PR, K, false, true);
-        for (int k = 0; k < No / 16; ++k)
-            tc::mma_bf16(work, kmaj(dz + k * 256, 64), mnmaj(w + k * 2 * hsr, K), idh, k > 0 ? 1u : 0u);
+        const tc::Desc2 dzk = tc::desc2(dz, 128, 8 * 128), wm = tc::desc2(w, hsr, 128);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < No / 16) tc::mma_bf16_w(work, dzk, k * 256, wm, k * 2 * hsr, idh, k > 0 ? 1u : 0u, t);
     };
 
     for (int64_t tile = PLANES * (int64_t)blockIdx.x + wg; tile < n_tiles && ok;
@@ -219,12 +220,11 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
         // ---- forward
         float ls[3] = {0.f, 0.f, 0.f}, zi = 0.f;
         for (int l = 0; l < NCH && ok; ++l) {
-            if (t == 0) {
+            if (t < 32) {
                 tc::fence_after();
                 mma_fwd(l);
-                tc::mma_commit(bar);
+                tc::mma_commit_w(bar, t);
             }
-            __syncwarp();
             round_wait();
             if (s_fail[wg] == 0) {
                 const float* bl = sbias + PSmem::BIAS_OFF(l);
@@ -274,12 +274,11 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
         }
         // ---- backward, chain layer 4 down to 0
         for (int l = NCH - 1; BWD && l >= 0 && ok; --l) {
-            if (t == 0) {
+            if (t < 32) {
                 tc::fence_after();
                 mma_bwd(l);
-                tc::mma_commit(bar);
+                tc::mma_commit_w(bar, t);
             }
-            __syncwarp();
             round_wait();
             if (s_fail[wg] == 0) {
                 const int K = kin(l);   // width of dH_l

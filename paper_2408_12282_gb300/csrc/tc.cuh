@@ -107,6 +107,45 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// A shared-memory matrix descriptor as its two 32-bit words (fields as in
+// make_desc). Stepping an operand by a byte offset is one 32-bit add to the
+// start-address field (bits 0-13, address >> 4): shared-memory addresses stay
+// below 256 KB, so the field never carries into the next one.
+struct Desc2 {
+    uint32_t lo, hi;
+};
+__device__ __forceinline__ Desc2 desc2(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return Desc2{((saddr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16), ((sbo >> 4) & 0x3FFFu) | (1u << 14)};
+}
+
+// D(tmem) (+)= A(smem) * B(smem)^T issued from a converged warp: every lane
+// evaluates the warp-uniform operands and lane 0 alone executes the MMA.
+// a_step / b_step are byte offsets added to the operands' start addresses.
+__device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, Desc2 a, uint32_t a_step, Desc2 b, uint32_t b_step,
+                                           uint32_t idesc, uint32_t accumulate, uint32_t lane) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t.reg .b64 da, db;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "setp.eq.u32 e, %7, 0;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a.lo + (a_step >> 4)), "r"(a.hi), "r"(b.lo + (b_step >> 4)), "r"(b.hi), "r"(idesc), "r"(accumulate),
+        "r"(lane)
+        : "memory");
+}
+
+// tcgen05.commit from lane 0 of a converged warp (the lane that issued the
+// warp's MMAs through mma_bf16_w).
+__device__ __forceinline__ void mma_commit_w(uint32_t bar, uint32_t lane) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "setp.eq.u32 e, %1, 0;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(bar),
+        "r"(lane)
+        : "memory");
+}
+
 // Arrive on `bar` when all tcgen05 operations issued so far by this thread complete.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
