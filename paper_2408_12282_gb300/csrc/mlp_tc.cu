@@ -174,9 +174,7 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
                         float v[64];
                         tc::tmem_ld64(lane_base + c0, v);
 #pragma unroll
-                        for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) store8_bf16(sA, t, c0 + 8 * q, N, v + 8 * q);
+                        for (int q = 0; q < 8; ++q) store8_bias_relu(sA, t, c0 + 8 * q, N, v + 8 * q, bl + c0 + 8 * q);
                     }
                 } else {
                     float v[16];
@@ -613,17 +611,15 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                     float v[64];
                     tc::tmem_ld64(tmem + lane_off + c0, v);
 #pragma unroll
-                    for (int j = 0; j < 64; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) store8_bf16(smem + G.off(l + 1), t, c0 + 8 * q, N, v + 8 * q);
+                    for (int q = 0; q < 8; ++q)
+                        store8_bias_relu(smem + G.off(l + 1), t, c0 + 8 * q, N, v + 8 * q, bl + c0 + 8 * q);
                 } else {
                     for (int c0 = wg * (N / 2); c0 < (wg + 1) * (N / 2); c0 += 32) {
                         float v[32];
                         tc::tmem_ld32(tmem + lane_off + c0, v);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bl[c0 + j], 0.f);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) store8_bf16(smem + G.off(l + 1), t, c0 + 8 * q, N, v + 8 * q);
+                        for (int q = 0; q < 4; ++q)
+                            store8_bias_relu(smem + G.off(l + 1), t, c0 + 8 * q, N, v + 8 * q, bl + c0 + 8 * q);
                     }
                 }
             } else if (wg == 0) {
@@ -764,16 +760,12 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                         for (int q = 0; q < 4; ++q) {
                             const int c = cbase + c0 + 8 * q;
                             const uint4 hq = load8_packed(hb, t, c, Kin);
-                            float o8[8];
-                            o8[0] = tc::bf16_lo(hq.x) > 0.f ? v[8 * q + 0] : 0.f;
-                            o8[1] = tc::bf16_hi(hq.x) > 0.f ? v[8 * q + 1] : 0.f;
-                            o8[2] = tc::bf16_lo(hq.y) > 0.f ? v[8 * q + 2] : 0.f;
-                            o8[3] = tc::bf16_hi(hq.y) > 0.f ? v[8 * q + 3] : 0.f;
-                            o8[4] = tc::bf16_lo(hq.z) > 0.f ? v[8 * q + 4] : 0.f;
-                            o8[5] = tc::bf16_hi(hq.z) > 0.f ? v[8 * q + 5] : 0.f;
-                            o8[6] = tc::bf16_lo(hq.w) > 0.f ? v[8 * q + 6] : 0.f;
-                            o8[7] = tc::bf16_hi(hq.w) > 0.f ? v[8 * q + 7] : 0.f;
-                            store8_bf16(hb, t, c, Kin, o8);
+                            uint4 o;
+                            o.x = tc::pack_bf16_mask(v[8 * q + 0], v[8 * q + 1], hq.x);
+                            o.y = tc::pack_bf16_mask(v[8 * q + 2], v[8 * q + 3], hq.y);
+                            o.z = tc::pack_bf16_mask(v[8 * q + 4], v[8 * q + 5], hq.z);
+                            o.w = tc::pack_bf16_mask(v[8 * q + 6], v[8 * q + 7], hq.w);
+                            store8_packed(hb, t, c, Kin, o);
                         }
                     }
                 } else {

@@ -50,6 +50,24 @@ __device__ __forceinline__ uint4 load8_packed(const uint8_t* base, int r, int c,
     return *reinterpret_cast<const uint4*>(base + tc::blk_offset(r, c, C));
 }
 
+// Hidden-layer epilogue of 8 consecutive columns: ReLU(v + bias) rounded to
+// BF16 and stored at (r, c..c+7). The bias adds are paired FP32 additions
+// (each rounded as the scalar one); bias8 is 16-byte aligned.
+__device__ __forceinline__ void store8_bias_relu(uint8_t* base, int r, int c, int C, const float* v,
+                                                 const float* bias8) {
+    const float4 b0 = *reinterpret_cast<const float4*>(bias8), b1 = *reinterpret_cast<const float4*>(bias8 + 4);
+    const float2 s0 = __fadd2_rn(make_float2(v[0], v[1]), make_float2(b0.x, b0.y));
+    const float2 s1 = __fadd2_rn(make_float2(v[2], v[3]), make_float2(b0.z, b0.w));
+    const float2 s2 = __fadd2_rn(make_float2(v[4], v[5]), make_float2(b1.x, b1.y));
+    const float2 s3 = __fadd2_rn(make_float2(v[6], v[7]), make_float2(b1.z, b1.w));
+    uint4 q;
+    q.x = tc::pack_bf16_relu(s0.x, s0.y);
+    q.y = tc::pack_bf16_relu(s1.x, s1.y);
+    q.z = tc::pack_bf16_relu(s2.x, s2.y);
+    q.w = tc::pack_bf16_relu(s3.x, s3.y);
+    store8_packed(base, r, c, C, q);
+}
+
 // Write n TMEM columns [col, col + n) of this warp's 32 lanes with zeros
 // (n a multiple of 32); the whole warp calls it.
 __device__ __forceinline__ void tmem_zero(uint32_t taddr, int n) {

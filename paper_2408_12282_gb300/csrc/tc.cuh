@@ -215,6 +215,24 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// ReLU(a), ReLU(b) rounded to BF16 (nearest even), packed with a in the low
+// half: one conversion with the clamp built in. Its zeros can differ from
+// rounding fmaxf(x, 0) only in sign, which no product or comparison sees.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
+// BF16 roundings of (a, b), packed, each kept where the matching half of the
+// packed BF16 pair h is > 0 and 0 elsewhere: the same bits as rounding
+// (h > 0 ? x : 0).
+__device__ __forceinline__ uint32_t pack_bf16_mask(float a, float b, uint32_t h) {
+    __nv_bfloat162 hv;
+    *reinterpret_cast<uint32_t*>(&hv) = h;
+    return pack_bf16(a, b) & __hgt2_mask(hv, __float2bfloat162_rn(0.f));
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
