@@ -660,6 +660,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         for (int l = L - 1; l >= 0 && ok; --l) {
             const int Kin = G.kin(l);
             const bool last = (l == L - 1);
+            const bool hidden = l >= 1 && l <= L - 2;
             const int Nout = last ? 16 : 128;        // dZ_{l+1} columns (padded for the last layer)
             const uint8_t* dzbuf = last ? sDZL : smem + G.off(l + 1);
             const uint32_t dz_addr = tc::smem_u32(dzbuf);
@@ -670,12 +671,17 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             ++use;
             const uint32_t w_addr = tc::smem_u32(smem + (((use - 1) & 1) ? T.offW[1] : T.offW[0]));
             const uint32_t w_sr = (uint32_t)(Kin / 8) * 128u;    // weight image: rows = outputs, C = Kin
-            const int halves = Kin > 64 ? 2 : 1;
+            // dH_l in one 128-column round on the hidden layers (their bias
+            // gradients wait for the tile's last round, so TMEM columns
+            // [0, 128) are free); the last layer (dW^T at columns [64, 80))
+            // takes two 64-column halves, layer 0 has 64 columns
+            const int halves = (!hidden && Kin > 64) ? 2 : 1;
+            const int ncols_round = hidden ? 128 : (Kin > 64 ? 64 : Kin);
             if (tid < 32) {
                 // per-tile or accumulated weight gradient, K' = 128 rows
                 const tc::Desc2 dzm = tc::desc2(dz_addr, dz_sr, 128);    // dZ, MN-major (K = rows)
                 const tc::Desc2 hm = tc::desc2(h_addr, h_sr, 128);       // H_l, MN-major (K = rows)
-                if (l >= 1 && l <= L - 2) {
+                if (hidden) {
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin, true, true);
 #pragma unroll
                     for (int k = 0; k < TC_ROWS / 16; ++k)
@@ -692,15 +698,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                     for (int k = 0; k < TC_ROWS / 16; ++k)
                         tc::mma_bf16_w(tmem + 64, dzm, k * 2 * dz_sr, hm, k * 2 * h_sr, idesc, k > 0 ? 1u : 0u, lane);
                 }
-                if (!last && l >= 1) {  // db_l = dZ_{l+1}^T 1 -> [Nout x 16]
-                    const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
-                    const tc::Desc2 on = tc::desc2(ones, 128, (TC_ROWS / 8) * 128);
-#pragma unroll
-                    for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16_w(tmem + 64, dzm, k * 2 * dz_sr, on, k * 256, idesc, k > 0 ? 1u : 0u, lane);
-                }
-                // dH_l, first half: [128 x min(64, Kin)] = dZ_{l+1} W_l
-                const uint32_t idesc = tc::idesc_bf16(TC_ROWS, Kin > 64 ? 64 : Kin, false, true);
+                // dH_l (hidden: all 128 columns; else the first half): dZ_{l+1} W_l
+                const uint32_t idesc = tc::idesc_bf16(TC_ROWS, ncols_round, false, true);
                 const tc::Desc2 dzk = tc::desc2(dz_addr, 128, dz_sr);    // dZ, K-major (K = outputs)
                 const tc::Desc2 wm = tc::desc2(w_addr, w_sr, 128);       // W_l, MN-major (K = outputs)
 #pragma unroll
@@ -711,7 +710,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             }
             mine = wait_mma() && mine;
             if (halves == 1) release_use(use - 1);
-            // epilogue after the first dH half
+            // epilogue of the per-tile weight gradients
             if (last) {
                 if (wg == 0) {
                     float v[16];
@@ -724,12 +723,6 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 tc::tmem_ld32(tmem + lane_off + 64 + 32 * wg, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) acc0[j] += v[j];
-            } else if (wg == 0) {
-                float v[16];
-                tc::tmem_ld16(tmem + lane_off + 64, v);
-#pragma unroll
-                for (int j = 0; j < SSSGS_MAX_LAYERS; ++j)
-                    if (j == l) dbacc[j] += v[0];
             }
             for (int h = 0; h < 2; ++h) {
                 if (h == 1) {
@@ -750,12 +743,13 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                     release_use(use - 1);
                 }
                 const int cbase = 64 * h;
-                const int ncols = Kin - cbase < 64 ? Kin - cbase : 64;
                 if (l > 0) {
-                    for (int c0 = 32 * wg; c0 < ncols; c0 += 64) {
+                    // dZ_l = bf16(dH_l * [H_l > 0]) in place over H_l; warpgroup wg
+                    // takes 32-column chunks wg, wg + 2, ... of this round's columns
+                    uint8_t* hb = smem + G.off(l);
+                    for (int c0 = 32 * wg; c0 < ncols_round; c0 += 64) {
                         float v[32];
                         tc::tmem_ld32(tmem + lane_off + c0, v);
-                        uint8_t* hb = smem + G.off(l);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int c = cbase + c0 + 8 * q;
@@ -788,28 +782,37 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 }
             }
             mine = sync_all(mine);
-            if (l == 0) {   // db_0 = dZ_1^T 1 (its TMEM columns were busy above)
+            if (l == 0) {
                 if (wg == 0 && valid) {   // combine the two halves of the input gradient
 #pragma unroll
                     for (int k = 0; k < 7; ++k)
                         dx_items[SSSGS_DX * m + k] = s_dx[k * TC_ROWS + t] + (k < 3 ? dmu_a[k] : 0.f);
                     // columns 7..13 (no q, log_s inputs) stay as cleared
                 }
+                // the tile's bias gradients of layers 0 .. L-2 in one round:
+                // db_j = dZ_{j+1}^T 1 (dZ_{j+1} stays where H_{j+1} was) into
+                // TMEM columns [16 j, 16 j + 16)
                 if (tid < 32) {
                     tc::fence_after();
                     const uint32_t idesc = tc::idesc_bf16(TC_ROWS, 16, true, false);
-                    const tc::Desc2 dzm = tc::desc2(dz_addr, dz_sr, 128);
                     const tc::Desc2 on = tc::desc2(ones, 128, (TC_ROWS / 8) * 128);
+                    for (int j = 0; j <= L - 2; ++j) {
+                        const tc::Desc2 dzm = tc::desc2(tc::smem_u32(smem + G.off(j + 1)), 2048, 128);
 #pragma unroll
-                    for (int k = 0; k < TC_ROWS / 16; ++k)
-                        tc::mma_bf16_w(tmem, dzm, k * 2 * dz_sr, on, k * 256, idesc, k > 0 ? 1u : 0u, lane);
+                        for (int k = 0; k < TC_ROWS / 16; ++k)
+                            tc::mma_bf16_w(tmem + 16 * j, dzm, k * 2 * 2048, on, k * 256, idesc, k > 0 ? 1u : 0u, lane);
+                    }
                     tc::mma_commit_w(bar_m, lane);
                 }
                 mine = wait_mma() && mine;
                 if (wg == 0) {
-                    float v[16];
-                    tc::tmem_ld16(tmem + lane_off, v);
-                    dbacc[0] += v[0];
+#pragma unroll
+                    for (int j = 0; j < SSSGS_MAX_LAYERS - 1; ++j)
+                        if (j <= L - 2) {
+                            float v[16];
+                            tc::tmem_ld16(tmem + lane_off + 16 * j, v);
+                            dbacc[j] += v[0];
+                        }
                 }
                 mine = sync_all(mine);
             }
