@@ -520,20 +520,23 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
     // the row ids two tiles ahead and the inputs of the next tile are loaded
     // while the current one is processed, so no load waits on another load
     // inside a tile.
+    // Item ids fit 32 bits (the host checks n < 2^32); NO_ROW marks a
+    // padding row past the list.
+    constexpr uint32_t NO_ROW = 0xFFFFFFFFu;
     struct RowIn {
         Pe6Params q;
         float up[4];
-        int64_t m;
+        uint32_t m;
         int pidx;
         bool valid;
     };
-    auto load_act = [&](int64_t tl) -> int64_t {
+    auto load_act = [&](int64_t tl) -> uint32_t {
         const int64_t row = tl * TC_ROWS + t;
-        return (tl < n_tiles && row < n_rows) ? (int64_t)active[row] : (int64_t)-1;
+        return (tl < n_tiles && row < n_rows) ? active[row] : NO_ROW;
     };
-    auto load_row = [&](int64_t mr) -> RowIn {
+    auto load_row = [&](uint32_t mr) -> RowIn {
         RowIn r;
-        r.valid = mr >= 0;
+        r.valid = mr != NO_ROW;
         r.pidx = 0;
         r.m = 0;
         if (r.valid) {
@@ -541,8 +544,8 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             r.pidx = pair_lookup(s_off, pairs, n_pairs, mr);
             const int gb = n_pairs <= TC_MAX_SMEM_PAIRS ? s_gb[r.pidx] : pairs[r.pidx].g_begin;
             const int64_t io = n_pairs <= TC_MAX_SMEM_PAIRS ? s_off[r.pidx] : pairs[r.pidx].item_offset;
-            r.q = load_pe6_params(sc, gb + (mr - io), mr);
-            const float4 u = *reinterpret_cast<const float4*>(dout + dstride * mr);
+            r.q = load_pe6_params(sc, gb + ((int64_t)mr - io), mr);
+            const float4 u = *reinterpret_cast<const float4*>(dout + dstride * (int64_t)mr);
             r.up[0] = u.x;
             r.up[1] = u.y;
             r.up[2] = u.z;
@@ -551,23 +554,18 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
         return r;
     };
     RowIn cur = load_row(load_act(blockIdx.x));
-    int64_t act1 = load_act((int64_t)blockIdx.x + gridDim.x);
+    uint32_t act1 = load_act((int64_t)blockIdx.x + gridDim.x);
     float dmu_a[3] = {0.f, 0.f, 0.f};     // Fourier part of dL/dmu (frequencies 0..2, warpgroup 0)
     const uint32_t ones = tc::smem_u32(smem + T.offOnes);
 
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t m = cur.m;
-        const bool valid = cur.valid;
-        const int pidx = cur.pidx;
-        const int64_t act2 = load_act(tile + 2 * (int64_t)gridDim.x);
-        const RowIn nxt = load_row(act1);
-        // H_0: network input, split between the warpgroups: columns [0, 18)
-        // (frequencies 0..2) on warpgroup 0, [18, 64) on warpgroup 1.
+    // H_0 of a tile: the network input, split between the warpgroups: columns
+    // [0, 18) (frequencies 0..2) on warpgroup 0, [18, 64) on warpgroup 1.
+    auto build_h0 = [&](const RowIn& r) {
         if (wg == 0) {
             float x[18];
 #pragma unroll
             for (int k = 0; k < 18; ++k) x[k] = 0.f;
-            if (valid) pe6_fourier<0, 3>(cur.q.mu, x);
+            if (r.valid) pe6_fourier<0, 3>(r.q.mu, x);
             store8_bf16(smem + G.off(0), t, 0, 64, x);
             store8_bf16(smem + G.off(0), t, 8, 64, x + 8);
             store1_bf16(smem + G.off(0), t, 16, 64, x[16]);
@@ -576,16 +574,29 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
             float x[46];
 #pragma unroll
             for (int k = 0; k < 46; ++k) x[k] = 0.f;
-            if (valid) {
-                pe6_fourier<3, 6>(cur.q.mu, x);
-                pe6_direct(pairs[pidx], cur.q.mu, cur.q.n, cur.q.v, x + 18);
+            if (r.valid) {
+                pe6_fourier<3, 6>(r.q.mu, x);
+                pe6_direct(pairs[r.pidx], r.q.mu, r.q.n, r.q.v, x + 18);
             }
 #pragma unroll
             for (int c = 18; c < 24; ++c) store1_bf16(smem + G.off(0), t, c, 64, x[c - 18]);
 #pragma unroll
             for (int q = 0; q < 5; ++q) store8_bf16(smem + G.off(0), t, 24 + 8 * q, 64, x + 6 + 8 * q);
         }
+    };
+    // the first tile's input; every later tile's is built during the previous
+    // tile's bias round (H_0 is free once layer 0's MMAs are done)
+    if ((int64_t)blockIdx.x < n_tiles) {
+        build_h0(cur);
         ok = sync_all(true);
+    }
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t m = (int64_t)cur.m;
+        const bool valid = cur.valid;
+        const int pidx = cur.pidx;
+        const uint32_t act2 = load_act(tile + 2 * (int64_t)gridDim.x);
+        const RowIn nxt = load_row(act1);
         // ---------------- forward recompute
         for (int l = 0; l < L && ok; ++l) {
             const int K = G.kin(l), Np = G.np(l);
@@ -804,6 +815,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                     }
                     tc::mma_commit_w(bar_m, lane);
                 }
+                if (tile + gridDim.x < n_tiles) build_h0(nxt);   // next tile's input, under the bias MMAs
                 mine = wait_mma() && mine;
                 if (wg == 0) {
 #pragma unroll
