@@ -89,7 +89,6 @@ __device__ __forceinline__ float pb(const MlpDev& net, int l, int n) {
     return n == 0 ? net.b[4][0] : 0.f;
 }
 
-__device__ __forceinline__ float lrelu(float v) { return v > 0.f ? v : kLReluSlope * v; }
 
 // Forward (BWD = false: rows are the items, writes out) or backward (BWD =
 // true: rows are the active items, recompute + back-propagate, gradients).
@@ -232,16 +231,14 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
                     float v[64];
                     tc::tmem_ld64(work_l, v);
 #pragma unroll
-                    for (int j = 0; j < 64; ++j) v[j] = lrelu(v[j] + bl[j]);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) store8_bf16((lane + act_off(1)), t, 8 * q, 64, v + 8 * q);
+                    for (int q = 0; q < 8; ++q)
+                        store8_bias_lrelu(lane + act_off(1), t, 8 * q, 64, v + 8 * q, bl + 8 * q, kLReluSlope);
                 } else if (l < 4) {
                     float v[32];
                     tc::tmem_ld32(work_l, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = lrelu(v[j] + bl[j]);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) store8_bf16((lane + act_off(l + 1)), t, 8 * q, 32, v + 8 * q);
+                    for (int q = 0; q < 4; ++q)
+                        store8_bias_lrelu(lane + act_off(l + 1), t, 8 * q, 32, v + 8 * q, bl + 8 * q, kLReluSlope);
                     if (l == 3) {   // SSS head: logits in columns 32..34
                         float h[16];
                         tc::tmem_ld16(work_l + 32, h);
@@ -290,12 +287,12 @@ __global__ void __launch_bounds__(PLANES * PT, 1) k_mlp_paper_tc(MlpDev net, con
                     for (int c0 = 0; c0 < 64; c0 += 8) {
                         if (c0 >= K) break;
                         const uint4 hq = load8_packed((lane + act_off(l)), t, c0, K);
-                        const float hv[8] = {tc::bf16_lo(hq.x), tc::bf16_hi(hq.x), tc::bf16_lo(hq.y), tc::bf16_hi(hq.y),
-                                             tc::bf16_lo(hq.z), tc::bf16_hi(hq.z), tc::bf16_lo(hq.w), tc::bf16_hi(hq.w)};
-                        float o[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) o[j] = hv[j] > 0.f ? v[c0 + j] : kLReluSlope * v[c0 + j];
-                        store8_bf16(sDZ, t, c0, 64, o);
+                        uint4 o;
+                        o.x = tc::pack_bf16_leaky(v[c0 + 0], v[c0 + 1], hq.x, kLReluSlope);
+                        o.y = tc::pack_bf16_leaky(v[c0 + 2], v[c0 + 3], hq.y, kLReluSlope);
+                        o.z = tc::pack_bf16_leaky(v[c0 + 4], v[c0 + 5], hq.z, kLReluSlope);
+                        o.w = tc::pack_bf16_leaky(v[c0 + 6], v[c0 + 7], hq.w, kLReluSlope);
+                        store8_packed(sDZ, t, c0, 64, o);
                     }
                     if (l == 4) {   // the layer-3 output also carries the SSS logits' dZ
                         const float d8[8] = {ls[0], ls[1], ls[2], 0.f, 0.f, 0.f, 0.f, 0.f};

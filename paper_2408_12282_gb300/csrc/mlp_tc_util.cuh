@@ -68,6 +68,25 @@ __device__ __forceinline__ void store8_bias_relu(uint8_t* base, int r, int c, in
     store8_packed(base, r, c, C, q);
 }
 
+// The same with Leaky-ReLU: max(x, slope x) for slope < 1 equals
+// (x > 0 ? x : slope x) bit for bit, taken on paired FP32 products.
+__device__ __forceinline__ void store8_bias_lrelu(uint8_t* base, int r, int c, int C, const float* v,
+                                                  const float* bias8, float slope) {
+    const float4 b0 = *reinterpret_cast<const float4*>(bias8), b1 = *reinterpret_cast<const float4*>(bias8 + 4);
+    const float2 sl = make_float2(slope, slope);
+    const float2 s[4] = {__fadd2_rn(make_float2(v[0], v[1]), make_float2(b0.x, b0.y)),
+                         __fadd2_rn(make_float2(v[2], v[3]), make_float2(b0.z, b0.w)),
+                         __fadd2_rn(make_float2(v[4], v[5]), make_float2(b1.x, b1.y)),
+                         __fadd2_rn(make_float2(v[6], v[7]), make_float2(b1.z, b1.w))};
+    uint32_t q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __fmul2_rn(s[k], sl);
+        q[k] = tc::pack_bf16(fmaxf(s[k].x, t.x), fmaxf(s[k].y, t.y));
+    }
+    store8_packed(base, r, c, C, make_uint4(q[0], q[1], q[2], q[3]));
+}
+
 // Write n TMEM columns [col, col + n) of this warp's 32 lanes with zeros
 // (n a multiple of 32); the whole warp calls it.
 __device__ __forceinline__ void tmem_zero(uint32_t taddr, int n) {

@@ -233,6 +233,17 @@ __device__ __forceinline__ uint32_t pack_bf16_mask(float a, float b, uint32_t h)
     return pack_bf16(a, b) & __hgt2_mask(hv, __float2bfloat162_rn(0.f));
 }
 
+// Leaky-ReLU derivative applied to a packed pair: the BF16 roundings of
+// (a, b) where the matching half of the packed BF16 pair h is > 0, of
+// (slope a, slope b) elsewhere (the same bits as rounding h > 0 ? x : slope x).
+__device__ __forceinline__ uint32_t pack_bf16_leaky(float a, float b, uint32_t h, float slope) {
+    __nv_bfloat162 hv;
+    *reinterpret_cast<uint32_t*>(&hv) = h;
+    const uint32_t m = __hgt2_mask(hv, __float2bfloat162_rn(0.f));
+    const float2 s = __fmul2_rn(make_float2(a, b), make_float2(slope, slope));
+    return (pack_bf16(a, b) & m) | (pack_bf16(s.x, s.y) & ~m);
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
