@@ -205,18 +205,22 @@ __global__ void __launch_bounds__(TC_FWD_LANES * TC_THREADS, 1) k_mlp_fwd_tc(Mlp
 
 // ---------------------------------------------------------------- backward
 //
-// Per 128-row tile: rebuild the input H_0, recompute the forward keeping every
+// Per 128-row tile: recompute the forward from the input H_0 keeping every
 // layer input H_l (BF16) in shared memory, form the head gradient dZ_L, then
-// for l = L-1 .. 0 (one elected thread issues, all warps run epilogues):
+// for l = L-1 .. 0 (lane 0 of warp 0 issues, all warps run epilogues):
 //   dW_l (+)= dZ_{l+1}^T H_l   hidden layers: accumulated across tiles in TMEM
 //                              first/last layer: per tile, summed in registers
-//   db_l (+)= dZ_{l+1}^T 1     (MMA against a ones operand)
-//   dH_l  = dZ_{l+1} W_l       (two 64-column halves), then
+//   dH_l  = dZ_{l+1} W_l       (hidden layers in one 128-column round, the
+//                              last layer in two 64-column halves), then
 //   dZ_l  = bf16(dH_l * [H_l > 0]) written in place over H_l; dH_0 is the
 //   network-input gradient, mapped to (d mu, d n, d v) per item.
+// A last round forms every bias gradient db_l (+)= dZ_{l+1}^T 1 (MMAs against
+// a ones operand; dZ_{l+1} stays in place of H_{l+1} until then) while the
+// next tile's H_0 is built.
 // Weight images (BF16, operand layout) stream from global memory with
-// cp.async.bulk into two shared-memory slots, one layer ahead.
-// TMEM columns: [0, 64) dH half / recompute, [64, 128) per-tile dW/db,
+// cp.async.bulk into two shared-memory slots, two uses ahead.
+// TMEM columns: [0, 128) recompute and dH, [64, 128) the per-tile dW of the
+// first and last layers (with a 64-wide dH), [0, 16 (L-1)) the bias round,
 // [128, 512) the hidden layers' dW accumulators.
 
 struct TcBwdLayout {
