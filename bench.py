@@ -307,8 +307,8 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # otherwise null.
 TRAFFIC_SOURCES = ("raster.cu", "raster_common.cuh", "common.cuh")
 KERNEL_TRAFFIC = {
-    "render_bwd": ("f829334662678eee74bb0ac5e19a2a12ff8acc0095cf97c5939759fd7a46b3c0", 108.34e6),
-    "render_fwd": ("f829334662678eee74bb0ac5e19a2a12ff8acc0095cf97c5939759fd7a46b3c0", 83.43e6),
+    "render_bwd": ("44bf3ed7952819584a2266ec8b961f8bbf2ed8ac7e39a6d083084784cac7165a", 108.33e6),
+    "render_fwd": ("44bf3ed7952819584a2266ec8b961f8bbf2ed8ac7e39a6d083084784cac7165a", 81.70e6),
 }
 
 
