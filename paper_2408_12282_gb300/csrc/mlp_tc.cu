@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(2 * TC_THREADS, 1) k_mlp_bwd_tc(MlpDev net, Tc
                 const int cbase = 64 * h;
                 if (l > 0) {
                     // dZ_l = bf16(dH_l * [H_l > 0]) in place over H_l; warpgroup wg
-                    // takes 32-column chunks wg, wg + 2, ... of this round's columns
+                    // takes 32-column chunks wg, wg + 2, ... of the columns this MMA pass formed
                     uint8_t* hb = smem + G.off(l);
                     for (int c0 = 32 * wg; c0 < ncols_round; c0 += 64) {
                         float v[32];
