@@ -25,16 +25,6 @@ __device__ __forceinline__ uint32_t blk_offset(int r, int c, int C) {
     return (uint32_t)((r >> 3) * (C >> 3) * 128 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
 
-// Shared-memory matrix descriptor (no swizzle, descriptor version 1).
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
 // Instruction descriptor of kind::f16 with BF16 A/B, FP32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major, bool b_mn_major) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((b_mn_major ? 1u : 0u) << 16) |
@@ -96,21 +86,11 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// D(tmem) (+)= A(smem) * B(smem)^T, one instruction (K = 16 for BF16).
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// A shared-memory matrix descriptor as its two 32-bit words (fields as in
-// make_desc). Stepping an operand by a byte offset is one 32-bit add to the
-// start-address field (bits 0-13, address >> 4): shared-memory addresses stay
-// below 256 KB, so the field never carries into the next one.
+// Shared-memory matrix descriptor (no swizzle, descriptor version 1) as its
+// two 32-bit words: bits 0-13 start address >> 4, 16-29 leading byte offset
+// >> 4, 32-45 stride byte offset >> 4, bit 46 the version. Stepping an operand
+// by a byte offset is one 32-bit add to the start-address field: shared-memory
+// addresses stay below 256 KB, so the field never carries into the next one.
 struct Desc2 {
     uint32_t lo, hi;
 };
@@ -136,7 +116,8 @@ __device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, Desc2 a, uint32_t a_
 }
 
 // tcgen05.commit from lane 0 of a converged warp (the lane that issued the
-// warp's MMAs through mma_bf16_w).
+// warp's MMAs through mma_bf16_w): the mbarrier arrives once every tcgen05
+// operation that lane issued so far has completed.
 __device__ __forceinline__ void mma_commit_w(uint32_t bar, uint32_t lane) {
     asm volatile(
         "{\n\t.reg .pred e;\n\t"
@@ -144,12 +125,6 @@ __device__ __forceinline__ void mma_commit_w(uint32_t bar, uint32_t lane) {
         "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(bar),
         "r"(lane)
         : "memory");
-}
-
-// Arrive on `bar` when all tcgen05 operations issued so far by this thread complete.
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
